@@ -1,0 +1,234 @@
+"""ctypes binding of the CPU FP64 oracle (af_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, __graft_entry__.smoke() and the
+benchmark's CPU-baseline / reference arm are the only users.  The product
+(paper_2506_04857_gb300) never imports this package.
+
+States are lists of four float64 arrays [8, nyp, nxp] (cell averages, x-face,
+y-face and corner point values; see af_inputs for the layout).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import List, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "af_oracle.cpp")
+_BUILD = os.path.join(_HERE, "_build")
+_LIBS = {}
+_LOCK = threading.Lock()
+
+NSTATS = 11
+STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
+              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
+PHASES = ["dt", "pointdata", "center", "point_ho", "point_pp", "sensor_phi", "sensor_theta", "face", "cell_src",
+          "cell_update", "cell_final", "rk"]
+KINDS = ["add", "mul", "div", "sqrt", "exp", "cmp"]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
+                ("y1", C.c_double), ("cfl", C.c_double), ("kappa", C.c_double), ("bc", C.c_int),
+                ("pp_on", C.c_int), ("src_cell_on", C.c_int), ("src_point_on", C.c_int)]
+
+
+def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, cfl=None) -> Params:
+    return Params(pb.gamma, pb.x0, pb.x1, pb.y0, pb.y1, pb.cfl if cfl is None else cfl,
+                  pb.kappa if kappa is None else kappa, pb.bc, int(pp_on), int(src_cell_on), int(src_point_on))
+
+
+def build(force: bool = False) -> None:
+    """Compile the oracle (plain and counting builds) with g++."""
+    os.makedirs(_BUILD, exist_ok=True)
+    jobs = [("liboracle.so", ["-fopenmp"]), ("liboracle_count.so", ["-DAF_ORACLE_COUNT"])]
+    procs = []
+    for name, extra in jobs:
+        out = os.path.join(_BUILD, name)
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        tmp = out + ".tmp%d" % os.getpid()
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", *extra, "-o", tmp, _SRC]
+        procs.append((subprocess.Popen(cmd), tmp, out))
+    for p, tmp, out in procs:
+        if p.wait() != 0:
+            raise RuntimeError("oracle build failed")
+        os.replace(tmp, out)
+
+
+def _lib(count: bool = False):
+    key = "count" if count else "plain"
+    with _LOCK:
+        if key not in _LIBS:
+            build()
+            lib = C.CDLL(os.path.join(_BUILD, "liboracle_count.so" if count else "liboracle.so"))
+            pp = C.POINTER(C.POINTER(C.c_double))
+            dp = C.POINTER(C.c_double)
+            lib.or_dt.restype = C.c_double
+            lib.or_dt.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp]
+            lib.or_stage.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double, C.c_double, C.c_double,
+                                     pp, C.POINTER(C.c_longlong)]
+            lib.or_step.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, C.c_double, dp, C.POINTER(C.c_longlong)]
+            lib.or_rhs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp]
+            lib.or_flux.argtypes = [C.c_int, dp, C.c_double, dp]
+            lib.or_pressure.restype = C.c_double
+            lib.or_pressure.argtypes = [dp, C.c_double]
+            lib.or_fast_speed.restype = C.c_double
+            lib.or_fast_speed.argtypes = [C.c_int, dp, C.c_double]
+            lib.or_spectral_radius.restype = C.c_double
+            lib.or_spectral_radius.argtypes = [C.c_int, dp, C.c_double]
+            lib.or_llf_flux.restype = C.c_double
+            lib.or_llf_flux.argtypes = [C.c_int, dp, dp, C.c_double, dp]
+            lib.or_center_value.argtypes = [dp, dp, dp, dp]
+            lib.or_fd.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, dp]
+            lib.or_flux_limiter.restype = C.c_int
+            lib.or_flux_limiter.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, dp, C.POINTER(C.c_int)]
+            lib.or_scaling_limiter.argtypes = [dp, dp, C.c_double, dp, dp]
+            lib.or_sensor_phi.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
+            lib.or_counts.restype = C.c_int
+            lib.or_counts.argtypes = [C.POINTER(C.c_longlong), C.c_int]
+            _LIBS[key] = lib
+        return _LIBS[key]
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptrs(U: List[np.ndarray]):
+    arr = (C.POINTER(C.c_double) * 4)(*[_dp(u) for u in U])
+    return arr
+
+
+def _check(U, nx, ny, bc):
+    from af_inputs import class_extents
+    ext = class_extents(nx, ny, bc)
+    out = []
+    for c in range(4):
+        a = np.ascontiguousarray(U[c], dtype=np.float64)
+        if a.shape != (8, ext[c][1], ext[c][0]):
+            raise ValueError("class %d has shape %s, expected %s" % (c, a.shape, (8, ext[c][1], ext[c][0])))
+        out.append(a)
+    return out
+
+
+def _empty(nx, ny, bc):
+    from af_inputs import class_extents
+    return [np.zeros((8, e[1], e[0])) for e in class_extents(nx, ny, bc)]
+
+
+def dt(pb, U, count=False, **kw) -> float:
+    P = params_for(pb, **kw)
+    U = _check(U, pb.nx, pb.ny, pb.bc)
+    return _lib(count).or_dt(C.byref(P), pb.nx, pb.ny, _ptrs(U))
+
+
+def stage(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, count=False, **kw):
+    P = params_for(pb, **kw)
+    Un = _check(Un, pb.nx, pb.ny, pb.bc)
+    Us = _check(Us, pb.nx, pb.ny, pb.bc)
+    out = _empty(pb.nx, pb.ny, pb.bc)
+    st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
+    _lib(count).or_stage(C.byref(P), pb.nx, pb.ny, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
+                         st.ctypes.data_as(C.POINTER(C.c_longlong)))
+    return out
+
+
+def step(pb, U, dt_in: float = 0.0, stats: Optional[np.ndarray] = None, count=False, **kw):
+    """One SSP-RK3 step; returns (new state, dt used)."""
+    P = params_for(pb, **kw)
+    V = [a.copy() for a in _check(U, pb.nx, pb.ny, pb.bc)]
+    st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
+    d = C.c_double(0.0)
+    _lib(count).or_step(C.byref(P), pb.nx, pb.ny, _ptrs(V), dt_in, C.byref(d),
+                        st.ctypes.data_as(C.POINTER(C.c_longlong)))
+    return V, d.value
+
+
+def rhs(pb, U, **kw):
+    P = params_for(pb, **kw)
+    U = _check(U, pb.nx, pb.ny, pb.bc)
+    out = _empty(pb.nx, pb.ny, pb.bc)
+    _lib().or_rhs(C.byref(P), pb.nx, pb.ny, _ptrs(U), _ptrs(out))
+    return out
+
+
+def flux(l: int, U, gamma: float) -> np.ndarray:
+    u = np.ascontiguousarray(U, dtype=np.float64)
+    F = np.zeros(8)
+    _lib().or_flux(l, _dp(u), gamma, _dp(F))
+    return F
+
+
+def pressure(U, gamma: float) -> float:
+    return _lib().or_pressure(_dp(np.ascontiguousarray(U, dtype=np.float64)), gamma)
+
+
+def fast_speed(l: int, U, gamma: float) -> float:
+    return _lib().or_fast_speed(l, _dp(np.ascontiguousarray(U, dtype=np.float64)), gamma)
+
+
+def spectral_radius(l: int, U, gamma: float) -> float:
+    return _lib().or_spectral_radius(l, _dp(np.ascontiguousarray(U, dtype=np.float64)), gamma)
+
+
+def llf_flux(l: int, U, V, gamma: float):
+    F = np.zeros(8)
+    a = _lib().or_llf_flux(l, _dp(np.ascontiguousarray(U, dtype=np.float64)),
+                           _dp(np.ascontiguousarray(V, dtype=np.float64)), gamma, _dp(F))
+    return F, a
+
+
+def center_value(avg, faces, corners) -> np.ndarray:
+    out = np.zeros(8)
+    _lib().or_center_value(_dp(np.ascontiguousarray(avg, dtype=np.float64)),
+                           _dp(np.ascontiguousarray(faces, dtype=np.float64)),
+                           _dp(np.ascontiguousarray(corners, dtype=np.float64)), _dp(out))
+    return out
+
+
+def fd(a, b, c, h) -> np.ndarray:
+    out = np.zeros(3)
+    _lib().or_fd(a, b, c, h, _dp(out))
+    return out
+
+
+def flux_limiter(lim1, H, eps_rho, eps_p, gamma):
+    lam = np.zeros(4)
+    it = C.c_int(0)
+    solves = _lib().or_flux_limiter(_dp(np.ascontiguousarray(lim1, dtype=np.float64)),
+                                    _dp(np.ascontiguousarray(H, dtype=np.float64)), eps_rho, eps_p, gamma,
+                                    _dp(lam), C.byref(it))
+    return lam, solves, it.value
+
+
+def scaling_limiter(UH, UL, gamma):
+    out = np.zeros(8)
+    th = np.zeros(2)
+    _lib().or_scaling_limiter(_dp(np.ascontiguousarray(UH, dtype=np.float64)),
+                              _dp(np.ascontiguousarray(UL, dtype=np.float64)), gamma, _dp(out), _dp(th))
+    return out, th
+
+
+def sensor_phi(c, e, w, n, s, gamma, dx, dy) -> np.ndarray:
+    """phi_1 (x), phi_1 (y), phi_2, phi_3 of one cell from five cell averages."""
+    out = np.zeros(4)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (c, e, w, n, s)]
+    _lib().or_sensor_phi(*[_dp(a) for a in arrs], gamma, dx, dy, _dp(out))
+    return out
+
+
+def counts(reset: bool = True) -> np.ndarray:
+    """Operation counts [phase, kind] of the counting build since the last reset."""
+    out = np.zeros(len(PHASES) * len(KINDS), dtype=np.int64)
+    _lib(count=True).or_counts(out.ctypes.data_as(C.POINTER(C.c_longlong)), int(reset))
+    return out.reshape(len(PHASES), len(KINDS))
+
+
+def flops(cnt: np.ndarray) -> np.ndarray:
+    """Flops per phase (add, mul, div, sqrt, exp each count one)."""
+    return cnt[:, :5].sum(axis=1)
