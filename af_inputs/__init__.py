@@ -210,14 +210,17 @@ def blast(n: int = 2048, low_beta: bool = True, kappa: float = 1.0) -> Problem:
 
 
 def rotor(n: int = 400, kappa: float = 2.0) -> Problem:
-    """Second rotor problem (Example 4.5), periodic [0,1]^2, gamma = 5/3."""
+    """Second rotor problem (Example 4.5), periodic [0,1]^2, gamma = 5/3.
+
+    The taper is read as f = (r1 - r)/(r1 - r0), which makes the state continuous
+    at r0 and r1; the printed (r1 - r)/(r - r0) is singular at r = r0."""
     r0, r1 = 0.1, 0.115
     b1 = 2.5 / math.sqrt(4.0 * math.pi)
 
     def prim(x, y):
         dx_, dy_ = x - 0.5, y - 0.5
         r = np.sqrt(dx_ * dx_ + dy_ * dy_)
-        f = np.where(r > r0, (r1 - r) / np.maximum(r - r0, 1e-300), 1.0)
+        f = (r1 - r) / (r1 - r0)
         inside = r < r0
         mid = (r >= r0) & (r < r1)
         rho = np.where(inside, 10.0, np.where(mid, 1.0 + 9.0 * f, 1.0))

@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the PP Active Flux MHD stage (arXiv:2506.04857) on GB300.
+
+Metric: FP64 cell-stage updates per second (one cell-stage = one cell's 32
+unknowns -- its average and its x-face, y-face and corner point values --
+advanced through one SSP-RK3 stage with all limiters), whole job.
+
+Default workload: the low-beta blast on a 2048 x 2048 outflow grid
+(gamma = 1.4, p = 1000 inside r < 0.1 else 0.1, |B| = 100/sqrt(4 pi) along
+the diagonal, kappa = 1, CFL 0.2), synthetic initial data (af_inputs).  A step
+is one SSP-RK3 step: dt reduction plus three limited stages.  One state is
+1.07 GB, far larger than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--workload blast2048|ot512|vortex64]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+Under torchrun (N > 1) each rank advances its own copy of the workload (the
+path has no exchange between independent runs): weak scaling, max-over-ranks
+time.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import af_inputs as ai  # noqa: E402
+
+WORKLOADS = {
+    "blast2048": ("low-beta blast 2048x2048 outflow, kappa=1", lambda: ai.blast(2048)),
+    "blast512": ("low-beta blast 512x512 outflow, kappa=1 (profiling size)", lambda: ai.blast(512)),
+    "ot512": ("Orszag-Tang 512x512 periodic, kappa=1", lambda: ai.orszag_tang(512)),
+    "vortex64": ("smooth vortex 64x64 periodic, kappa=0", lambda: ai.vortex(64)),
+}
+
+# Algorithmic FP64 flops per cell-stage of each kernel: the arithmetic of the
+# scheme as the paper writes it, with the PP limiters off (their tests and
+# occasional blends are extra work, not counted), counted by the counting
+# build of the oracle: python -m oracle.count_flops (64x64 grids; +, -, *, /,
+# sqrt, exp, min/max, |.| one flop each).
+ALGO_FLOPS = {
+    "blast_low_beta": {"k_pointdata": 714.9, "k_points": 1294.8, "k_faces": 253.9, "k_cells": 628.0, "k_final": 16.3},
+    "orszag_tang": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 250.0, "k_cells": 628.0, "k_final": 16.0},
+    "vortex": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 234.0, "k_cells": 468.0, "k_final": 16.0},
+}
+# FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
+# instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
+FP64_FLOPS_PER_SM_CYCLE = 4.0
+# Algorithmic bytes per cell-stage: read U^(s) (32 doubles), read U^n on stages
+# 2 and 3, write U^(s+1): (512 + 768 + 768)/3 B.
+ALGO_BYTES_PER_CS = (512.0 + 768.0 + 768.0) / 3.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def window_problem(pb, i0, j0, w):
+    """A w x w window of cells of pb as an outflow sub-problem (for the CPU oracle)."""
+    import dataclasses
+    return dataclasses.replace(pb, nx=w, ny=w, x0=pb.x0 + i0 * pb.dx, x1=pb.x0 + (i0 + w) * pb.dx,
+                               y0=pb.y0 + j0 * pb.dy, y1=pb.y0 + (j0 + w) * pb.dy, bc=ai.OUTFLOW)
+
+
+def cpu_sample_problem(key, pb, w):
+    """The bounded CPU sample of a workload: a w x w window on its most active region."""
+    if key.startswith("blast"):
+        # window straddling the blast front (radius 0.1 = 204.8 cells from the centre)
+        c = pb.nx // 2
+        w = min(w, pb.nx)
+        r = int(round(0.1 / pb.dx))
+        i0, j0 = min(pb.nx - w, c + r - w // 2), c - w // 2
+    else:
+        i0 = j0 = 0
+        w = min(w, pb.nx)
+    sub = window_problem(pb, i0, j0, w) if (w < pb.nx or pb.bc == ai.OUTFLOW) else pb
+    desc = "%dx%d window [%d:%d, %d:%d] of the %dx%d workload as an outflow sub-problem" % (
+        w, w, i0, i0 + w, j0, j0 + w, pb.nx, pb.ny)
+    return sub, desc
+
+
+def threads_used():
+    try:
+        n = int(os.environ.get("OMP_NUM_THREADS", "0"))
+    except ValueError:
+        n = 0
+    return n if n > 0 else len(os.sched_getaffinity(0))
+
+
+def run_oracle_steps(sub, steps, budget_s=None):
+    import oracle
+    U = ai.dofs(sub)
+    t0 = time.perf_counter()
+    done = 0
+    for _ in range(steps):
+        U, _ = oracle.step(sub, U)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(key, pb, budget_s=12.0, w=512):
+    """The oracle, as it stands, timed on the host cores on a bounded sample."""
+    import oracle
+    oracle.build()
+    sub, desc = cpu_sample_problem(key, pb, w)
+    run_oracle_steps(sub, 1)   # warm-up (first-touch, thread pool)
+    n, t = run_oracle_steps(sub, 1000, budget_s=budget_s)
+    cs = sub.nx * sub.ny * 3 * n
+    return {"value": cs / t, "unit": "cell-stage updates/s", "cores": threads_used(), "kind": "oracle",
+            "sample": "%s, %d SSP-RK3 steps in %.1f s" % (desc, n, t)}
+
+
+def reference_arm(args, key, desc, pb):
+    """--impl reference: the CPU oracle on the host cores (the paper ships no code)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sub, sdesc = cpu_sample_problem(key, pb, 128)
+    for _ in range(args.warmup):
+        run_oracle_steps(sub, 1)
+    n, t = run_oracle_steps(sub, args.steps)
+    value = sub.nx * sub.ny * 3 * n / t
+    line = {"metric": "FP64 AF-MHD cell-stage updates/s", "value": value, "unit": "cell-stage updates/s",
+            "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "nx": pb.nx, "ny": pb.ny, "cells": pb.nx * pb.ny, "sample": sdesc},
+            "cpu_baseline": {"value": value, "unit": "cell-stage updates/s", "cores": threads_used(),
+                             "kind": "oracle", "sample": "%s, one SSP-RK3 step per timed step" % sdesc},
+            "e2e": {"value": value, "unit": "cell-stage updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="blast2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    key = args.workload
+    desc, make = WORKLOADS[key]
+    pb = make()
+    if args.impl == "reference":
+        return reference_arm(args, key, desc, pb)
+
+    import torch
+    import paper_2506_04857_gb300 as af
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+
+    U0 = ai.dofs(pb)
+    s = af.Solver(pb.nx, pb.ny, pb.gamma, pb.bc, domain=(pb.x0, pb.x1, pb.y0, pb.y1), cfl=pb.cfl, kappa=pb.kappa,
+                  stream=stream)
+    dev_state = [torch.from_numpy(u).cuda() for u in U0]
+    s.set_state(dev_state)
+    peak_fp64 = af.af_probe_fp64(stream)
+    for _ in range(args.warmup):
+        s.step(dt_out=False)
+    torch.cuda.synchronize()
+
+    # ---------------- timed region: K steps, inputs resident in HBM --------
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.step(dt_out=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ktimes = s.timing(False)
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    rc, cnt = s.status(reset=True)
+    if rc != af.AF_OK:
+        raise SystemExit("libaf reported %s after the timed region" % af.af_last_error(s.ctx))
+    cells = pb.nx * pb.ny
+    units = cells * 3 * args.steps * world
+    value = units / (ms * 1e-3)
+    launches = sum(n for _, n in ktimes.values())
+
+    # ---------------- roofline of the dominant kernel -----------------------
+    flops = ALGO_FLOPS[pb.name]
+    dom = max((k for k in ktimes if k in flops), key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    avg_ms = dom_ms / max(dom_n, 1)
+    achieved = flops[dom] * cells / (avg_ms * 1e-3) * 1e-12
+    kernel_share = {k: round(v[0] / sum(x[0] for x in ktimes.values()), 4) for k, v in ktimes.items() if v[1]}
+    stage_flops = sum(flops.values()) * cells * 3 * args.steps
+    props = torch.cuda.get_device_properties(local)
+    max_mhz = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = FP64_FLOPS_PER_SM_CYCLE * props.multi_processor_count * max_mhz * 1e6 * 1e-12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "derived: 2 DFMA/SM/cycle x %d SMs x %.0f MHz x 2 flops" % (props.multi_processor_count,
+                                                                                         max_mhz),
+                "probe_fp64_tflops": peak_fp64,
+                "algorithmic_flops_per_cell_stage": flops[dom],
+                "step_achieved_tflops": stage_flops / (ms * 1e-3) * 1e-12 / world,
+                "step_frac": stage_flops / (ms * 1e-3) * 1e-12 / world / peak,
+                "hbm_bound_cell_stages_per_s": measured_peaks().get("hbm_gbs", 6775.6) * 1e9 / ALGO_BYTES_PER_CS,
+                "kernel_time_share": kernel_share}
+
+    # ---------------- end to end through the C ABI with host buffers --------
+    host_in = [torch.from_numpy(u).pin_memory() for u in U0]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    bytes_state = sum(u.nbytes for u in U0)
+    s.set_state(host_in)
+    s.step(dt_out=False)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.set_state(host_in)     # H2D from pinned memory, synchronous
+        s.step(dt_out=False)
+        s.get_state(out=[h.numpy() for h in host_out], device=False)   # D2H, synchronous
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": cells * 3 * args.e2e_steps * world / te, "unit": "cell-stage updates/s",
+           "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state, "steps": args.e2e_steps}
+
+    if rank == 0:
+        line = {"metric": "FP64 AF-MHD cell-stage updates/s", "value": value, "unit": "cell-stage updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (analytic initial condition, af_inputs)",
+                "config": {"workload": desc, "nx": pb.nx, "ny": pb.ny, "cells": cells, "gamma": pb.gamma,
+                           "cfl": pb.cfl, "kappa": pb.kappa, "bc": "outflow" if pb.bc == ai.OUTFLOW else "periodic",
+                           "per_rank_replica": world > 1,
+                           "l2": "state 1.07 GB per buffer >> 129 MB L2 (no flush needed)" if key == "blast2048"
+                           else "no L2 flush; state smaller than L2"},
+                "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "clocks": clk,
+                "limiter_counters": cnt}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(key, pb)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * af.h -- C ABI of libaf: one SSP-RK3 step of the positivity-preserving
+ * Active Flux (AF) scheme for 2D ideal MHD with the Godunov-Powell source
+ * term (J. Duan, P. Chandrashekar, C. Klingenberg, arXiv:2506.04857), in FP64
+ * on an NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 1, eq. 2d_mhd_gp): U_t + F1(U)_x + F2(U)_y = -(div B) Psi(U),
+ * U = (rho, rho v1, rho v2, rho v3, B1, B2, B3, E), Psi = (0, B, v, v.B),
+ * perfect gas p = (gamma-1)(E - |rho v|^2/(2 rho) - |B|^2/2), on a uniform
+ * Cartesian grid of nx x ny cells.
+ *
+ * Degrees of freedom (Sec. 2, Fig. 1), in four classes, each stored as a
+ * contiguous FP64 array [8][nyp][nxp] (component, row y, column x; x fastest):
+ *   AF_CLASS_AVG    cell averages          at cell (i,j)               nx x ny
+ *   AF_CLASS_XFACE  x-face point values    at (x0 + i dx, y_j)         nxf x ny
+ *   AF_CLASS_YFACE  y-face point values    at (x_i, y0 + j dy)         nx x nyf
+ *   AF_CLASS_CORNER corner point values    at (x0 + i dx, y0 + j dy)   nxf x nyf
+ * with nxf = nx, nyf = ny for periodic boundaries and nx+1, ny+1 for outflow
+ * (boundary point values are degrees of freedom).  af_sizes returns nxp, nyp.
+ *
+ * Conventions.
+ *   - Return value: AF_OK (0) or a negative AF_E* code; af_last_error gives a
+ *     message.  Nothing aborts the process.
+ *   - The context owns its device memory (three state buffers and the stage
+ *     work arrays, about 260 doubles per cell).  The caller owns every array
+ *     passed in.
+ *   - on_device = 1: pointers are device pointers on the context's device,
+ *     used in stream order on the context's stream (af_set_stream); calls
+ *     return before the GPU work ends.  on_device = 0: host pointers; the call
+ *     synchronises the stream before it returns.
+ *   - Device-side faults of the scheme (a degree of freedom left outside the
+ *     admissible set after every safeguard, a non-finite time step) latch a
+ *     device error word that the next af_status call reports as AF_ENONPHYS.
+ */
+#ifndef AF_H
+#define AF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_ctx af_ctx;
+
+enum { AF_BC_PERIODIC = 0, AF_BC_OUTFLOW = 1 };
+enum {
+  AF_OK = 0,
+  AF_EINVAL = -1,     /* bad argument */
+  AF_ECUDA = -2,      /* CUDA runtime error */
+  AF_ENOMEM = -3,     /* device allocation failed */
+  AF_ENONPHYS = -4,   /* a DoF left the admissible set G, or dt was not finite */
+  AF_EBOUNDS = -5,    /* internal capacity exceeded (round-off repair list) */
+  AF_ETIMEOUT = -6    /* reserved */
+};
+enum { AF_CLASS_AVG = 0, AF_CLASS_XFACE = 1, AF_CLASS_YFACE = 2, AF_CLASS_CORNER = 3 };
+
+/* Counters reported by af_status (cumulative since af_create or the last
+ * af_status call with reset = 1). */
+enum {
+  AF_STAT_SRC_LIMITED = 0,   /* cells with theta_ij < 1 (Sec. 3.2 step (1)) */
+  AF_STAT_LAMBDA_LT1,        /* cells with some Lambda_I < 1 (step (2)) */
+  AF_STAT_FACE_THETA_LT1,    /* faces with theta < 1 (step (3)) */
+  AF_STAT_SENSOR_LT099,      /* faces with theta^s < 0.99 (Sec. 3.4) */
+  AF_STAT_NEWTON_SOLVES,     /* vertex cubics solved by Newton (step (2)) */
+  AF_STAT_NEWTON_MAXIT,      /* largest Newton iteration count (a maximum, not a sum) */
+  AF_STAT_SHRINK,            /* round-off shrink events (Remark 4.1) */
+  AF_STAT_POINT_LIMITED,     /* point values with theta* < 1 or theta** < 1 (Sec. 3.3) */
+  AF_STAT_CFL_VIOLATIONS,    /* cells violating the LLF CFL condition of Lemma 3.1 */
+  AF_STAT_CENTER_LIMITED,    /* cell-centre values modified (Remark 3.2) */
+  AF_STAT_NONADMISSIBLE,     /* DoFs left outside G after every safeguard */
+  AF_NSTAT
+};
+
+typedef struct af_params {
+  double cfl;        /* The shock-sensor blending coefficients theta^s of Sec. 3.4 for the current
+ * state: theta_x at the x-faces, an [ny][nxf] array (class AF_CLASS_XFACE
+ * extents), theta_y at the y-faces, an [nyf][nx] array (AF_CLASS_YFACE
+ * extents).  With kappa = 0 every coefficient is 1. */
+int af_sensor(af_ctx *ctx, double *theta_x, double *theta_y, int on_device);
+
+/* dt = cfl / (max varrho_1/dx + max varrho_2/dy), maxima over all four DoF
+                        classes of U^n (Sec. 2.3 eq. cf; the paper prints no formula).  Default 0.2. */
+  double kappa;      /* shock-sensor strength kappa (Sec. 3.4); 0 gives theta^s = 1.  Default 0. */
+  int pp_on;         /* positivity-preserving limiters of Sec. 3.2-3.3 and Remark 4.1.  Default 1. */
+  int src_cell_on;   /* Godunov-Powell source in the cell-average update (eq. semi_av_src).  Default 1. */
+  int src_point_on;  /* Godunov-Powell source in the point-value update (Sec. 2.3).  Default 1. */
+} af_params;
+
+/* Create a context for an nx x ny grid (nx, ny >= 4), ratio of specific heats
+ * gamma > 1, boundary condition bc (AF_BC_PERIODIC or AF_BC_OUTFLOW; outflow
+ * mirrors the DoFs across the boundary, the paper names the condition only).
+ * Uses the current CUDA device.  The domain defaults to [0,1]^2 and the
+ * parameters to the defaults above.  The state is zero until af_set_state. */
+int af_create(int nx, int ny, double gamma, int bc, af_ctx **out);
+
+/* Domain [x0,x1] x [y0,y1] (x1 > x0, y1 > y0); sets dx = (x1-x0)/nx, dy = (y1-y0)/ny. */
+int af_set_domain(af_ctx *ctx, double x0, double x1, double y0, double y1);
+
+int af_set_params(af_ctx *ctx, const af_params *p);
+int af_get_params(const af_ctx *ctx, af_params *p);
+
+/* The CUDA stream (a cudaStream_t passed as void*; NULL = the legacy default
+ * stream) on which all further work of this context is enqueued. */
+int af_set_stream(af_ctx *ctx, void *stream);
+
+/* Extents of DoF class cls (AF_CLASS_*): *nxp columns, *nyp rows. */
+int af_sizes(const af_ctx *ctx, int cls, int *nxp, int *nyp);
+
+/* Copy the state U^n in (U[cls] is a [8][nyp][nxp] array of conserved
+ * variables).  The state is not validated here; af_status reports a
+ * non-admissible state once a step has run on it. */
+int af_set_state(af_ctx *ctx, const double *const U[4], int on_device);
+
+/* Copy the current state U^n out (same layout). */
+int af_get_state(af_ctx *ctx, double *const U[4], int on_device);
+
+/* The semi-discrete right-hand side L(U^n) of Sec. 2.2 and 2.3 for all four
+ * classes (Simpson fluxes, Powell source on the 3x3 Simpson nodes, LLF flux
+ * vector splitting with the central divergence, cell-centre values limited
+ * as in Remark 3.2), without the shock sensor or the PP limiters, which
+ * depend on dt.  dUdt has the state layout. */
+int af_rhs(af_ctx *ctx, double *const dUdt[4], int on_device);
+
+/* The shock-sensor blending coefficients theta^s of Sec. 3.4 for the current
+ * state: theta_x at the x-faces, an [ny][nxf] array (class AF_CLASS_XFACE
+ * extents), theta_y at the y-faces, an [nyf][nx] array (AF_CLASS_YFACE
+ * extents).  With kappa = 0 every coefficient is 1. */
+int af_sensor(af_ctx *ctx, double *theta_x, double *theta_y, int on_device);
+
+/* dt = cfl / (max varrho_1/dx + max varrho_2/dy) over the DoFs of U^n.  The
+ * value stays on the device for af_stage; it is also written to *dt_out
+ * (host or device pointer) when dt_out is not NULL. */
+int af_dt(af_ctx *ctx, double *dt_out, int on_device);
+
+/* One stage s in {0,1,2} of the SSP-RK3 scheme, written as convex
+ * combinations of limited forward-Euler stages (Sec. 3.1):
+ *   U1 = FE(U^n), U2 = 3/4 U^n + 1/4 FE(U1), U^{n+1} = 1/3 U^n + 2/3 FE(U2),
+ * with FE the forward-Euler update of Sec. 2 limited by Sec. 3.2-3.4.  Stages
+ * must be called in order 0, 1, 2; stage 2 makes U^{n+1} the current state.
+ * dt: the time step (host or device pointer); NULL uses the value of the last
+ * af_dt / af_step. */
+int af_stage(af_ctx *ctx, int s, const double *dt, int on_device);
+
+/* Copy out the result of the most recent stage: U1 after stage 0, U2 after
+ * stage 1, U^{n+1} after stage 2 (same layout as the state). */
+int af_get_stage(af_ctx *ctx, double *const U[4], int on_device);
+
+/* af_dt followed by the three stages.  *dt_used (host or device, may be NULL)
+ * receives the step's dt. */
+int af_step(af_ctx *ctx, double *dt_used, int on_device);
+
+/* Synchronise the stream, copy the AF_NSTAT counters into counters (may be
+ * NULL) and report the device error word: AF_ENONPHYS for a non-admissible
+ * DoF or a non-finite dt, AF_EBOUNDS for an overflowed repair list.  reset = 1
+ * clears counters and error word afterwards. */
+int af_status(af_ctx *ctx, long long *counters, int reset);
+
+/* Kernels of one stage, in the order af_timing reports them. */
+enum { AF_K_POINTDATA = 0, AF_K_DT, AF_K_POINTS, AF_K_FACES, AF_K_CELLS, AF_K_FINAL, AF_K_REPAIR, AF_NKERNEL };
+
+/* Per-kernel device timing for measurement tools.  enable = 1 clears the
+ * record and starts bracketing every kernel launch of this context with a
+ * pair of CUDA events on its stream; enable = 0 stops, synchronises the
+ * stream and writes, per kernel (AF_K_* order), the summed device time in
+ * milliseconds to ms[AF_NKERNEL] and the number of launches to
+ * launches[AF_NKERNEL] (either may be NULL). */
+int af_timing(af_ctx *ctx, int enable, double *ms, long long *launches);
+
+/* Message of the last error on this context ("" when none). */
+const char *af_last_error(const af_ctx *ctx);
+
+/* Free the context and its device memory (NULL is ignored). */
+void af_destroy(af_ctx *ctx);
+
+/* Diagnostic: n results of the FP64 helpers the kernels use, on device
+ * arrays, in stream order: op 0 out = 1/x, op 1 out = x/y, op 2 out = sqrt(x).
+ * Used by the tests to bound their error against the CUDA operators. */
+int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
+
+/* Diagnostic: measured FP64 fused-multiply-add throughput of the current
+ * device (a register-resident DFMA loop over all SMs, timed with CUDA events
+ * on stream), written to *tflops (2 flops per FMA).  Used as the arithmetic
+ * roofline of the kernels, which are bound by the FP64 pipe. */
+int af_probe_fp64(void *stream, double *tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AF_H */

@@ -28,7 +28,7 @@ STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "ne
               "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
 PHASES = ["dt", "pointdata", "center", "point_ho", "point_pp", "sensor_phi", "sensor_theta", "face", "cell_src",
           "cell_update", "cell_final", "rk"]
-KINDS = ["add", "mul", "div", "sqrt", "exp", "cmp"]
+KINDS = ["add", "mul", "div", "sqrt", "exp", "minmax", "cmp"]
 
 
 class Params(C.Structure):
@@ -89,6 +89,7 @@ def _lib(count: bool = False):
             lib.or_flux_limiter.argtypes = [dp, dp, C.c_double, C.c_double, C.c_double, dp, C.POINTER(C.c_int)]
             lib.or_scaling_limiter.argtypes = [dp, dp, C.c_double, dp, dp]
             lib.or_sensor_phi.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
+            lib.or_sensor.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp, dp]
             lib.or_counts.restype = C.c_int
             lib.or_counts.argtypes = [C.POINTER(C.c_longlong), C.c_int]
             _LIBS[key] = lib
@@ -155,6 +156,18 @@ def rhs(pb, U, **kw):
     out = _empty(pb.nx, pb.ny, pb.bc)
     _lib().or_rhs(C.byref(P), pb.nx, pb.ny, _ptrs(U), _ptrs(out))
     return out
+
+
+def sensor(pb, U, **kw):
+    """theta^s at x-faces [ny, nxf] and y-faces [nyf, nx] of the state U."""
+    from af_inputs import class_extents
+    P = params_for(pb, **kw)
+    U = _check(U, pb.nx, pb.ny, pb.bc)
+    ext = class_extents(pb.nx, pb.ny, pb.bc)
+    tx = np.zeros((ext[1][1], ext[1][0]))
+    ty = np.zeros((ext[2][1], ext[2][0]))
+    _lib().or_sensor(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(tx), _dp(ty))
+    return tx, ty
 
 
 def flux(l: int, U, gamma: float) -> np.ndarray:
@@ -230,5 +243,6 @@ def counts(reset: bool = True) -> np.ndarray:
 
 
 def flops(cnt: np.ndarray) -> np.ndarray:
-    """Flops per phase (add, mul, div, sqrt, exp each count one)."""
-    return cnt[:, :5].sum(axis=1)
+    """Flops per phase: +, -, *, /, sqrt, exp, min/max and |.| each count one
+    (comparisons that only steer branches are not counted)."""
+    return cnt[:, :6].sum(axis=1)

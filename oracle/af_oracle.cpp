@@ -49,7 +49,7 @@ enum Phase {
   PH_RK,            // SSP-RK3 convex combination
   NPHASE
 };
-enum Kind { K_ADD = 0, K_MUL, K_DIV, K_SQRT, K_EXP, K_CMP, NKIND };
+enum Kind { K_ADD = 0, K_MUL, K_DIV, K_SQRT, K_EXP, K_MINMAX, K_CMP, NKIND };
 
 #ifdef AF_ORACLE_COUNT
 static long long g_cnt[NPHASE][NKIND];
@@ -76,7 +76,7 @@ static inline bool operator<=(real a, real b) { tick(K_CMP); return a.v <= b.v; 
 static inline bool operator>=(real a, real b) { tick(K_CMP); return a.v >= b.v; }
 static inline real sqrt(real a) { tick(K_SQRT); return std::sqrt(a.v); }
 static inline real exp(real a) { tick(K_EXP); return std::exp(a.v); }
-static inline real fabs(real a) { tick(K_CMP); return std::fabs(a.v); }
+static inline real fabs(real a) { tick(K_MINMAX); return std::fabs(a.v); }
 static inline bool is_finite(real a) { return std::isfinite(a.v); }
 static inline void set_phase(int p) { g_phase = p; }
 #else
@@ -86,8 +86,13 @@ static inline bool is_finite(real a) { return std::isfinite(a); }
 static inline void set_phase(int) {}
 #endif
 
+#ifdef AF_ORACLE_COUNT
+static inline real rmax(real a, real b) { tick(K_MINMAX); return (a.v < b.v) ? b : a; }
+static inline real rmin(real a, real b) { tick(K_MINMAX); return (b.v < a.v) ? b : a; }
+#else
 static inline real rmax(real a, real b) { return (a < b) ? b : a; }
 static inline real rmin(real a, real b) { return (b < a) ? b : a; }
+#endif
 
 // ---------------------------------------------------------------------------
 // Parameters (mirrors the fields the test-suite passes in).
@@ -1193,6 +1198,26 @@ int or_rhs(const or_params *p, int nx, int ny, const double *const *U, double *c
   return 0;
 }
 
+// Shock-sensor coefficients theta^s (Sec. 3.4) of the state U: x-faces
+// [ny][nxf] and y-faces [nyf][nx] (class-1 and class-2 extents).
+int or_sensor(const or_params *p, int nx, int ny, const double *const *U, double *ths_x, double *ths_y) {
+  Ctx C;
+  make_ctx(p, nx, ny, C);
+  State S;
+  load_state(C, U, S);
+  long long st[ST_NSTATS] = {0};
+  Work W;
+  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, S.c[cls], cls);
+  compute_point_data(C, S, W);
+  compute_sensor(C, W);
+  compute_faces(C, W, st);
+  for (int j = 0; j < C.ext[1][1]; ++j)
+    for (int f = 0; f < C.ext[1][0]; ++f) ths_x[(size_t)j * C.ext[1][0] + f] = val(W.fx.at(C, 16, f, j));
+  for (int g = 0; g < C.ext[2][1]; ++g)
+    for (int i = 0; i < C.ext[2][0]; ++i) ths_y[(size_t)g * C.ext[2][0] + i] = val(W.fy.at(C, 16, i, g));
+  return 0;
+}
+
 // ---- pointwise pieces, exported for the unit tests --------------------------
 void or_flux(int l, const double *U, double gamma, double *F) {
   real u[8];
@@ -1287,7 +1312,7 @@ void or_sensor_phi(const double *c, const double *e, const double *w, const doub
 }
 
 // Operation counts per phase since the last reset (counting build only).
-// out[NPHASE][NKIND]: add(+sub), mul, div, sqrt, exp, cmp (comparisons, min/max, |.|).
+// out[NPHASE][NKIND]: add(+sub), mul, div, sqrt, exp, min/max/|.|, comparisons.
 int or_counts(long long *out, int reset) {
 #ifdef AF_ORACLE_COUNT
   for (int p = 0; p < NPHASE; ++p)

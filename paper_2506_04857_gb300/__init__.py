@@ -1,0 +1,387 @@
+"""Python binding of libaf (include/af.h): one SSP-RK3 step of the
+positivity-preserving Active Flux scheme for 2D ideal MHD with the
+Godunov-Powell source term (arXiv:2506.04857), in FP64 on GB300 (sm_103a).
+
+The functions mirror the C ABI one to one and only marshal arguments; every
+step of the scheme runs in the CUDA kernels of libaf.  PyTorch provides device
+memory (tensors) and streams.  There is no CPU fallback: if libaf cannot be
+built or loaded, or no CUDA device is present, the calls raise.
+
+A state is a list of four float64 arrays/tensors [8, nyp, nxp] (cell averages,
+x-face, y-face and corner point values; af_sizes gives the extents).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
+    "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_sensor", "af_dt",
+    "af_stage",
+    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
+]
+
+AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
+AF_OK, AF_EINVAL, AF_ECUDA, AF_ENOMEM, AF_ENONPHYS, AF_EBOUNDS, AF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+AF_NSTAT = 11
+STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
+              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
+_CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
+          AF_EBOUNDS: "AF_EBOUNDS", AF_ETIMEOUT: "AF_ETIMEOUT"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+_LOCK = threading.Lock()
+
+
+class AFError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_CODES.get(code, "AF_E?"), code, msg))
+        self.code = code
+
+
+class af_params(C.Structure):
+    _fields_ = [("cfl", C.c_double), ("kappa", C.c_double), ("pp_on", C.c_int), ("src_cell_on", C.c_int),
+                ("src_point_on", C.c_int)]
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "_build", "libaf.so")
+
+
+def _lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            from . import build as _build
+            path = _build.build()   # no-op when up to date; raises without nvcc
+            lib = C.CDLL(path)
+            vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+            pp = C.POINTER(C.c_void_p)
+            lib.af_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_void_p)]
+            lib.af_set_domain.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
+            lib.af_set_params.argtypes = [vp, C.POINTER(af_params)]
+            lib.af_get_params.argtypes = [vp, C.POINTER(af_params)]
+            lib.af_set_stream.argtypes = [vp, vp]
+            lib.af_sizes.argtypes = [vp, C.c_int, ip, ip]
+            lib.af_set_state.argtypes = [vp, pp, C.c_int]
+            lib.af_get_state.argtypes = [vp, pp, C.c_int]
+            lib.af_rhs.argtypes = [vp, pp, C.c_int]
+            lib.af_dt.argtypes = [vp, vp, C.c_int]
+            lib.af_sensor.argtypes = [vp, vp, vp, C.c_int]
+            lib.af_stage.argtypes = [vp, C.c_int, vp, C.c_int]
+            lib.af_step.argtypes = [vp, vp, C.c_int]
+            lib.af_get_stage.argtypes = [vp, pp, C.c_int]
+            lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+            lib.af_last_error.argtypes = [vp]
+            lib.af_last_error.restype = C.c_char_p
+            lib.af_destroy.argtypes = [vp]
+            lib.af_destroy.restype = None
+            lib.af_math_check.argtypes = [C.c_int, vp, vp, vp, C.c_longlong, vp]
+            lib.af_timing.argtypes = [vp, C.c_int, vp, vp]
+            lib.af_probe_fp64.argtypes = [vp, C.POINTER(C.c_double)]
+            _LIB = lib
+        return _LIB
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise AFError(AF_ECUDA, "no CUDA device: libaf runs on the GPU only")
+    return torch
+
+
+def _check(ctx, rc: int):
+    if rc != AF_OK:
+        msg = af_last_error(ctx) if ctx else ""
+        raise AFError(rc, msg)
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    return (C.c_void_p * 4)(*ptrs)
+
+
+def _is_tensor(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+# ---------------------------------------------------------------------------
+# C ABI mirrors
+# ---------------------------------------------------------------------------
+def af_create(nx: int, ny: int, gamma: float, bc: int = AF_BC_PERIODIC):
+    _torch()
+    h = C.c_void_p()
+    rc = _lib().af_create(int(nx), int(ny), float(gamma), int(bc), C.byref(h))
+    if rc != AF_OK:
+        raise AFError(rc, "af_create(%d, %d, %g, %d) failed" % (nx, ny, gamma, bc))
+    return h
+
+
+def af_set_domain(ctx, x0: float, x1: float, y0: float, y1: float) -> None:
+    _check(ctx, _lib().af_set_domain(ctx, x0, x1, y0, y1))
+
+
+def af_set_params(ctx, cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True, src_cell_on: bool = True,
+                  src_point_on: bool = True) -> None:
+    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on))
+    _check(ctx, _lib().af_set_params(ctx, C.byref(p)))
+
+
+def af_get_params(ctx) -> dict:
+    p = af_params()
+    _check(ctx, _lib().af_get_params(ctx, C.byref(p)))
+    return {"cfl": p.cfl, "kappa": p.kappa, "pp_on": bool(p.pp_on), "src_cell_on": bool(p.src_cell_on),
+            "src_point_on": bool(p.src_point_on)}
+
+
+def af_set_stream(ctx, stream=None) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None (legacy default stream)."""
+    if stream is None:
+        handle = None
+    elif hasattr(stream, "cuda_stream"):
+        handle = stream.cuda_stream
+    else:
+        handle = int(stream)
+    _check(ctx, _lib().af_set_stream(ctx, handle))
+
+
+def af_sizes(ctx, cls: int):
+    a, b = C.c_int(), C.c_int()
+    _check(ctx, _lib().af_sizes(ctx, cls, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def _shapes(ctx):
+    return [(8, af_sizes(ctx, c)[1], af_sizes(ctx, c)[0]) for c in range(4)]
+
+
+def _marshal_in(ctx, U):
+    """Pointers of a state given as CUDA tensors (on_device = 1) or host arrays (0)."""
+    shapes = _shapes(ctx)
+    if len(U) != 4:
+        raise ValueError("a state has four DoF classes")
+    if all(_is_tensor(u) and u.is_cuda for u in U):
+        torch = _torch()
+        keep = []
+        for u, s in zip(U, shapes):
+            if tuple(u.shape) != s or u.dtype != torch.float64:
+                raise ValueError("class tensor must be float64 %s, got %s %s" % (s, u.dtype, tuple(u.shape)))
+            keep.append(u.contiguous())
+        return _ptr_array([k.data_ptr() for k in keep]), 1, keep
+    keep = []
+    for u, s in zip(U, shapes):
+        a = u.detach().cpu().numpy() if _is_tensor(u) else np.asarray(u)
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        if a.shape != s:
+            raise ValueError("class array must be %s, got %s" % (s, a.shape))
+        keep.append(a)
+    return _ptr_array([k.ctypes.data for k in keep]), 0, keep
+
+
+def af_set_state(ctx, U) -> None:
+    ptrs, dev, keep = _marshal_in(ctx, U)
+    _check(ctx, _lib().af_set_state(ctx, ptrs, dev))
+    del keep
+
+
+def _outputs(ctx, out, device: bool):
+    shapes = _shapes(ctx)
+    if out is None:
+        if device:
+            torch = _torch()
+            out = [torch.empty(s, dtype=torch.float64, device="cuda") for s in shapes]
+        else:
+            out = [np.empty(s) for s in shapes]
+    on_dev = int(_is_tensor(out[0]) and out[0].is_cuda)
+    ptrs = _ptr_array([o.data_ptr() if on_dev else o.ctypes.data for o in out])
+    return out, ptrs, on_dev
+
+
+def af_get_state(ctx, out=None, device: bool = True):
+    out, ptrs, dev = _outputs(ctx, out, device)
+    _check(ctx, _lib().af_get_state(ctx, ptrs, dev))
+    return out
+
+
+def af_get_stage(ctx, out=None, device: bool = True):
+    """The result of the most recent stage (U1, U2 or U^{n+1})."""
+    out, ptrs, dev = _outputs(ctx, out, device)
+    _check(ctx, _lib().af_get_stage(ctx, ptrs, dev))
+    return out
+
+
+def af_rhs(ctx, out=None, device: bool = True):
+    out, ptrs, dev = _outputs(ctx, out, device)
+    _check(ctx, _lib().af_rhs(ctx, ptrs, dev))
+    return out
+
+
+def af_sensor(ctx, device: bool = True):
+    """theta^s at the x-faces [ny, nxf] and y-faces [nyf, nx] of the current state."""
+    (nxf, ny), (nx, nyf) = af_sizes(ctx, 1), af_sizes(ctx, 2)
+    if device:
+        torch = _torch()
+        tx = torch.empty((ny, nxf), dtype=torch.float64, device="cuda")
+        ty = torch.empty((nyf, nx), dtype=torch.float64, device="cuda")
+        _check(ctx, _lib().af_sensor(ctx, tx.data_ptr(), ty.data_ptr(), 1))
+    else:
+        tx, ty = np.empty((ny, nxf)), np.empty((nyf, nx))
+        _check(ctx, _lib().af_sensor(ctx, tx.ctypes.data, ty.ctypes.data, 0))
+    return tx, ty
+
+
+def af_dt(ctx, out=None) -> Optional[float]:
+    """dt of the current state.  out: None (returns a float, synchronises) or a
+    one-element CUDA float64 tensor that receives dt in stream order."""
+    if out is None:
+        v = C.c_double()
+        _check(ctx, _lib().af_dt(ctx, C.cast(C.byref(v), C.c_void_p), 0))
+        return v.value
+    _check(ctx, _lib().af_dt(ctx, out.data_ptr(), 1))
+    return None
+
+
+def af_stage(ctx, s: int, dt=None) -> None:
+    """dt: None (value from the last af_dt/af_step), a float, or a CUDA float64 tensor."""
+    if dt is None:
+        _check(ctx, _lib().af_stage(ctx, s, None, 0))
+    elif _is_tensor(dt) and dt.is_cuda:
+        _check(ctx, _lib().af_stage(ctx, s, dt.data_ptr(), 1))
+    else:
+        v = C.c_double(float(dt))
+        _check(ctx, _lib().af_stage(ctx, s, C.cast(C.byref(v), C.c_void_p), 0))
+
+
+def af_step(ctx, dt_out=None) -> Optional[float]:
+    """One SSP-RK3 step.  dt_out: None (returns dt as a float, synchronises),
+    False (returns nothing, no synchronisation) or a CUDA float64 tensor."""
+    if dt_out is False:
+        _check(ctx, _lib().af_step(ctx, None, 0))
+        return None
+    if dt_out is None:
+        v = C.c_double()
+        _check(ctx, _lib().af_step(ctx, C.cast(C.byref(v), C.c_void_p), 0))
+        return v.value
+    _check(ctx, _lib().af_step(ctx, dt_out.data_ptr(), 1))
+    return None
+
+
+def af_status(ctx, reset: bool = False):
+    """(return code, counters as a dict) after synchronising the stream."""
+    cnt = (C.c_longlong * AF_NSTAT)()
+    rc = _lib().af_status(ctx, cnt, int(reset))
+    return rc, dict(zip(STAT_NAMES, [int(v) for v in cnt]))
+
+
+KERNEL_NAMES = ["k_pointdata", "k_dt", "k_points", "k_faces", "k_cells", "k_final", "k_repair"]
+
+
+def af_timing(ctx, enable: bool):
+    """enable=True starts per-kernel event timing; enable=False stops it and
+    returns {kernel: (total ms, launches)}."""
+    if enable:
+        _check(ctx, _lib().af_timing(ctx, 1, None, None))
+        return None
+    ms = (C.c_double * len(KERNEL_NAMES))()
+    n = (C.c_longlong * len(KERNEL_NAMES))()
+    _check(ctx, _lib().af_timing(ctx, 0, C.cast(ms, C.c_void_p), C.cast(n, C.c_void_p)))
+    return {k: (ms[i], int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+
+def af_probe_fp64(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    v = C.c_double()
+    rc = _lib().af_probe_fp64(handle, C.byref(v))
+    if rc != AF_OK:
+        raise AFError(rc, "af_probe_fp64 failed")
+    return v.value
+
+
+def af_last_error(ctx) -> str:
+    r = _lib().af_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def af_destroy(ctx) -> None:
+    if ctx:
+        _lib().af_destroy(ctx)
+
+
+def af_math_check(op: int, x, y, out, stream=None) -> None:
+    handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = _lib().af_math_check(op, x.data_ptr(), None if y is None else y.data_ptr(), out.data_ptr(), x.numel(), handle)
+    if rc != AF_OK:
+        raise AFError(rc, "af_math_check failed")
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class Solver:
+    """Owns one libaf context.  Example:
+
+        s = Solver(512, 512, 5/3, AF_BC_PERIODIC, domain=(0, 2*pi, 0, 2*pi), kappa=1.0)
+        s.set_state(U0)          # four float64 arrays/tensors
+        dt = s.step()
+        U = s.get_state()        # CUDA tensors
+    """
+
+    def __init__(self, nx: int, ny: int, gamma: float, bc: int = AF_BC_PERIODIC, domain=(0.0, 1.0, 0.0, 1.0),
+                 cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True, src_cell_on: bool = True,
+                 src_point_on: bool = True, stream=None):
+        self.ctx = af_create(nx, ny, gamma, bc)
+        self.nx, self.ny, self.bc = nx, ny, bc
+        af_set_domain(self.ctx, *domain)
+        af_set_params(self.ctx, cfl, kappa, pp_on, src_cell_on, src_point_on)
+        if stream is not None:
+            af_set_stream(self.ctx, stream)
+
+    def sizes(self):
+        return [af_sizes(self.ctx, c) for c in range(4)]
+
+    def set_state(self, U):
+        af_set_state(self.ctx, U)
+
+    def get_state(self, out=None, device: bool = True):
+        return af_get_state(self.ctx, out, device)
+
+    def get_stage(self, out=None, device: bool = True):
+        return af_get_stage(self.ctx, out, device)
+
+    def rhs(self, out=None, device: bool = True):
+        return af_rhs(self.ctx, out, device)
+
+    def dt(self, out=None):
+        return af_dt(self.ctx, out)
+
+    def sensor(self, device: bool = True):
+        return af_sensor(self.ctx, device)
+
+    def stage(self, s: int, dt=None):
+        af_stage(self.ctx, s, dt)
+
+    def step(self, dt_out=None):
+        return af_step(self.ctx, dt_out)
+
+    def status(self, reset: bool = False):
+        return af_status(self.ctx, reset)
+
+    def timing(self, enable: bool):
+        return af_timing(self.ctx, enable)
+
+    def close(self):
+        if self.ctx:
+            af_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,456 @@
+// af_api.cu -- host side of libaf: context, device memory, stage sequencing.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/af.h"
+#include "af_internal.h"
+
+struct af_ctx {
+  int device;
+  int nx, ny, bc;
+  double gamma, x0, x1, y0, y1;
+  af_params prm;
+  cudaStream_t stream;
+  AfGrid g;
+  double *state[3];       // three state buffers, 32 arrays each (4 classes x 8)
+  size_t class_off[4];    // offset of each class inside a state buffer
+  size_t state_len;       // doubles per state buffer
+  int cur;                // buffer holding U^n
+  int next_stage;         // 0, 1, 2
+  int last_out;           // buffer written by the most recent stage
+  double *work;           // all stage work arrays
+  AfScalars *sc;
+  AfStatus *st;
+  AfDev dev;              // work-array pointers (state pointers set per stage)
+  // per-kernel event timing (af_timing)
+  int timing;
+  int nev;                // event pairs in use
+  int evcap;
+  cudaEvent_t *ev;        // 2 * evcap events
+  unsigned char *evk;     // kernel id of each pair
+  char msg[512];
+};
+
+namespace {
+
+int fail(af_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+int cuda_check(af_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return AF_OK;
+  return fail(c, AF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(expr, what)                            \
+  do {                                            \
+    int rc_ = cuda_check(c, (expr), (what));      \
+    if (rc_) return rc_;                          \
+  } while (0)
+
+void refresh_grid(af_ctx *c) {
+  AfGrid &g = c->g;
+  g.nx = c->nx;
+  g.ny = c->ny;
+  g.bc = c->bc;
+  g.nxa = c->bc == AF_BC_OUTFLOW ? c->nx + 1 : c->nx;
+  g.nya = c->bc == AF_BC_OUTFLOW ? c->ny + 1 : c->ny;
+  const int fx = g.nxa, fy = g.nya;
+  g.ex[0] = c->nx; g.ey[0] = c->ny;
+  g.ex[1] = fx;    g.ey[1] = c->ny;
+  g.ex[2] = c->nx; g.ey[2] = fy;
+  g.ex[3] = fx;    g.ey[3] = fy;
+  g.dx = (c->x1 - c->x0) / c->nx;
+  g.dy = (c->y1 - c->y0) / c->ny;
+  g.gamma = c->gamma;
+  g.gm1 = c->gamma - 1.0;
+  g.kappa = c->prm.kappa;
+  g.cfl = c->prm.cfl;
+  g.c13 = 1e-13 / (c->gamma - 1.0);
+  g.pp_on = c->prm.pp_on;
+  g.src_cell_on = c->prm.src_cell_on;
+  g.src_point_on = c->prm.src_point_on;
+}
+
+const double *cls_ptr(const af_ctx *c, int buf, int cls) { return c->state[buf] + c->class_off[cls]; }
+double *cls_ptr_mut(af_ctx *c, int buf, int cls) { return c->state[buf] + c->class_off[cls]; }
+size_t cls_len(const af_ctx *c, int cls) { return (size_t)8 * c->g.ex[cls] * c->g.ey[cls]; }
+
+int copy_state(af_ctx *c, int buf, const double *const U[4], int on_device, bool to_ctx, double *const Uo[4]) {
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_ctx ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+  for (int cls = 0; cls < 4; ++cls) {
+    const size_t bytes = cls_len(c, cls) * sizeof(double);
+    if (to_ctx) {
+      if (!U[cls]) return fail(c, AF_EINVAL, "state class %d is NULL", cls);
+      CK(cudaMemcpyAsync(cls_ptr_mut(c, buf, cls), U[cls], bytes, k, c->stream), "copy state in");
+    } else {
+      if (!Uo[cls]) return fail(c, AF_EINVAL, "state class %d is NULL", cls);
+      CK(cudaMemcpyAsync(Uo[cls], cls_ptr(c, buf, cls), bytes, k, c->stream), "copy state out");
+    }
+  }
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return AF_OK;
+}
+
+void bind_states(af_ctx *c, int bn, int bs, int bo) {
+  for (int cls = 0; cls < 4; ++cls) {
+    c->dev.un[cls] = cls_ptr(c, bn, cls);
+    c->dev.us[cls] = cls_ptr(c, bs, cls);
+    c->dev.uo[cls] = cls_ptr_mut(c, bo, cls);
+  }
+}
+
+// Event pair around one launch when timing is on (events are created lazily in chunks).
+bool timing_begin(af_ctx *c, int kernel) {
+  if (!c->timing) return false;
+  if (c->nev == c->evcap) {
+    const int cap = c->evcap ? 2 * c->evcap : 256;
+    cudaEvent_t *ev = (cudaEvent_t *)realloc(c->ev, sizeof(cudaEvent_t) * 2 * cap);
+    unsigned char *evk = (unsigned char *)realloc(c->evk, cap);
+    if (!ev || !evk) {
+      if (ev) c->ev = ev;
+      if (evk) c->evk = evk;
+      return false;
+    }
+    c->ev = ev;
+    c->evk = evk;
+    for (int k = 2 * c->evcap; k < 2 * cap; ++k) cudaEventCreate(&c->ev[k]);
+    c->evcap = cap;
+  }
+  c->evk[c->nev] = (unsigned char)kernel;
+  cudaEventRecord(c->ev[2 * c->nev], c->stream);
+  return true;
+}
+void timing_end(af_ctx *c, bool on) {
+  if (!on) return;
+  cudaEventRecord(c->ev[2 * c->nev + 1], c->stream);
+  c->nev++;
+}
+#define TIMED(kernel, call)                    \
+  do {                                         \
+    bool on_ = timing_begin(c, (kernel));      \
+    call;                                      \
+    timing_end(c, on_);                        \
+  } while (0)
+
+// One stage: P1..P5 on the bound buffers.
+void run_stage(af_ctx *c, double a, double b, int reduce_dt) {
+  TIMED(AF_K_POINTDATA, af_launch_pointdata(c->dev, c->g, reduce_dt, c->stream));
+  if (reduce_dt) TIMED(AF_K_DT, af_launch_dt(c->dev, c->g, c->stream));
+  TIMED(AF_K_POINTS, af_launch_points(c->dev, c->g, a, b, 0, c->stream));
+  TIMED(AF_K_FACES, af_launch_faces(c->dev, c->g, 0, c->stream));
+  TIMED(AF_K_CELLS, af_launch_cells(c->dev, c->g, a, b, 0, c->stream));
+  if (c->g.pp_on) {
+    TIMED(AF_K_FINAL, af_launch_final(c->dev, c->g, a, b, c->stream));
+    TIMED(AF_K_REPAIR, af_launch_repair(c->dev, c->g, a, b, c->stream));
+  }
+}
+
+const double RK_A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
+const double RK_B[3] = {1.0, 1.0 / 4.0, 2.0 / 3.0};
+
+int set_dt(af_ctx *c, const double *dt, int on_device) {
+  if (!dt) return AF_OK;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (!on_device && !(*dt > 0.0)) return fail(c, AF_EINVAL, "dt must be positive");
+  CK(cudaMemcpyAsync(&c->sc->dt, dt, sizeof(double), k, c->stream), "set dt");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return AF_OK;
+}
+
+int stage_impl(af_ctx *c, int s, int reduce_dt) {
+  const int n = c->cur, b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+  if (s == 0) bind_states(c, n, n, b1);
+  else if (s == 1) bind_states(c, n, b1, b2);
+  else bind_states(c, n, b2, b1);
+  run_stage(c, RK_A[s], RK_B[s], reduce_dt);
+  CK(cudaGetLastError(), "stage launch");
+  c->last_out = s == 1 ? b2 : b1;
+  if (s == 2) c->cur = b1;
+  c->next_stage = (s + 1) % 3;
+  return AF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
+  if (!out) return AF_EINVAL;
+  *out = nullptr;
+  if (nx < 4 || ny < 4 || !(gamma > 1.0) || (bc != AF_BC_PERIODIC && bc != AF_BC_OUTFLOW)) return AF_EINVAL;
+  af_ctx *c = new (std::nothrow) af_ctx();
+  if (!c) return AF_ENOMEM;
+  c->nx = nx;
+  c->ny = ny;
+  c->bc = bc;
+  c->gamma = gamma;
+  c->x0 = 0.0; c->x1 = 1.0; c->y0 = 0.0; c->y1 = 1.0;
+  c->prm.cfl = 0.2;
+  c->prm.kappa = 0.0;
+  c->prm.pp_on = 1;
+  c->prm.src_cell_on = 1;
+  c->prm.src_point_on = 1;
+  c->stream = nullptr;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return AF_ECUDA;
+  }
+  refresh_grid(c);
+  size_t off = 0;
+  for (int cls = 0; cls < 4; ++cls) {
+    c->class_off[cls] = off;
+    off += cls_len(c, cls);
+  }
+  c->state_len = off;
+  const size_t PS = (size_t)c->g.nxa * c->g.nya;
+  const size_t nwork = PS * (AF_NQA + 4 * AF_NQP + 8 + 4 + 2 * AF_NQF + 4 + 8 + 2);
+  int rc = AF_OK;
+  for (int b = 0; b < 3; ++b) {
+    if (cudaMalloc(&c->state[b], off * sizeof(double)) != cudaSuccess) rc = AF_ENOMEM;
+    else if (cudaMemset(c->state[b], 0, off * sizeof(double)) != cudaSuccess) rc = AF_ECUDA;
+  }
+  if (!rc && cudaMalloc(&c->work, nwork * sizeof(double)) != cudaSuccess) rc = AF_ENOMEM;
+  if (!rc && cudaMemset(c->work, 0, nwork * sizeof(double)) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaMalloc(&c->sc, sizeof(AfScalars)) != cudaSuccess) rc = AF_ENOMEM;
+  if (!rc && cudaMalloc(&c->st, sizeof(AfStatus)) != cudaSuccess) rc = AF_ENOMEM;
+  if (!rc && cudaMemset(c->sc, 0, sizeof(AfScalars)) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaMemset(c->st, 0, sizeof(AfStatus)) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = AF_ECUDA;
+  if (rc) {
+    cudaGetLastError();
+    af_destroy(c);
+    return rc;
+  }
+  double *w = c->work;
+  c->dev.pd[0] = w; w += AF_NQA * PS;
+  for (int k = 1; k <= 4; ++k) { c->dev.pd[k] = w; w += AF_NQP * PS; }
+  c->dev.uc = w; w += 8 * PS;
+  c->dev.phi = w; w += 4 * PS;
+  c->dev.fx = w; w += AF_NQF * PS;
+  c->dev.fy = w; w += AF_NQF * PS;
+  c->dev.lam = w; w += 4 * PS;
+  c->dev.lim1 = w; w += 8 * PS;
+  c->dev.thx = w; w += PS;
+  c->dev.thy = w; w += PS;
+  c->dev.sc = c->sc;
+  c->dev.st = c->st;
+  c->cur = 0;
+  c->next_stage = 0;
+  c->msg[0] = 0;
+  *out = c;
+  return AF_OK;
+}
+
+int af_set_domain(af_ctx *c, double x0, double x1, double y0, double y1) {
+  if (!c) return AF_EINVAL;
+  if (!(x1 > x0) || !(y1 > y0)) return fail(c, AF_EINVAL, "empty domain");
+  c->x0 = x0; c->x1 = x1; c->y0 = y0; c->y1 = y1;
+  refresh_grid(c);
+  return AF_OK;
+}
+
+int af_set_params(af_ctx *c, const af_params *p) {
+  if (!c || !p) return AF_EINVAL;
+  if (!(p->cfl > 0.0) || !(p->kappa >= 0.0)) return fail(c, AF_EINVAL, "cfl must be > 0 and kappa >= 0");
+  c->prm = *p;
+  refresh_grid(c);
+  return AF_OK;
+}
+
+int af_get_params(const af_ctx *c, af_params *p) {
+  if (!c || !p) return AF_EINVAL;
+  *p = c->prm;
+  return AF_OK;
+}
+
+int af_set_stream(af_ctx *c, void *stream) {
+  if (!c) return AF_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return AF_OK;
+}
+
+int af_sizes(const af_ctx *c, int cls, int *nxp, int *nyp) {
+  if (!c || cls < 0 || cls > 3 || !nxp || !nyp) return AF_EINVAL;
+  *nxp = c->g.ex[cls];
+  *nyp = c->g.ey[cls];
+  return AF_OK;
+}
+
+int af_set_state(af_ctx *c, const double *const U[4], int on_device) {
+  if (!c || !U) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  c->next_stage = 0;
+  return copy_state(c, c->cur, U, on_device, true, nullptr);
+}
+
+int af_get_state(af_ctx *c, double *const U[4], int on_device) {
+  if (!c || !U) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  return copy_state(c, c->cur, nullptr, on_device, false, U);
+}
+
+int af_rhs(af_ctx *c, double *const dUdt[4], int on_device) {
+  if (!c || !dUdt) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  const int scratch = (c->cur + 1) % 3;
+  bind_states(c, c->cur, c->cur, scratch);
+  af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  af_launch_points(c->dev, c->g, 0.0, 1.0, 1, c->stream);
+  af_launch_faces(c->dev, c->g, 1, c->stream);
+  af_launch_cells(c->dev, c->g, 0.0, 1.0, 1, c->stream);
+  CK(cudaGetLastError(), "rhs launch");
+  c->next_stage = 0;
+  return copy_state(c, scratch, nullptr, on_device, false, dUdt);
+}
+
+int af_sensor(af_ctx *c, double *theta_x, double *theta_y, int on_device) {
+  if (!c || !theta_x || !theta_y) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  bind_states(c, c->cur, c->cur, (c->cur + 1) % 3);
+  af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  af_launch_points(c->dev, c->g, 0.0, 1.0, 2, c->stream);
+  af_launch_faces(c->dev, c->g, 2, c->stream);
+  CK(cudaGetLastError(), "sensor launch");
+  const size_t PS = (size_t)c->g.nxa * c->g.nya;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const AfGrid &g = c->g;
+  CK(cudaMemcpy2DAsync(theta_x, g.ex[1] * sizeof(double), c->dev.fx + QF_TS * PS, g.nxa * sizeof(double),
+                       g.ex[1] * sizeof(double), g.ey[1], k, c->stream), "copy theta_x");
+  CK(cudaMemcpy2DAsync(theta_y, g.ex[2] * sizeof(double), c->dev.fy + QF_TS * PS, g.nxa * sizeof(double),
+                       g.ex[2] * sizeof(double), g.ey[2], k, c->stream), "copy theta_y");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  c->next_stage = 0;
+  return AF_OK;
+}
+
+int af_dt(af_ctx *c, double *dt_out, int on_device) {
+  if (!c) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  bind_states(c, c->cur, c->cur, (c->cur + 1) % 3);
+  af_launch_pointdata(c->dev, c->g, 1, c->stream);
+  af_launch_dt(c->dev, c->g, c->stream);
+  CK(cudaGetLastError(), "dt launch");
+  if (dt_out) {
+    CK(cudaMemcpyAsync(dt_out, &c->sc->dt, sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy dt");
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  return AF_OK;
+}
+
+int af_stage(af_ctx *c, int s, const double *dt, int on_device) {
+  if (!c || s < 0 || s > 2) return AF_EINVAL;
+  if (s != c->next_stage) return fail(c, AF_EINVAL, "stage %d called, stage %d expected", s, c->next_stage);
+  CK(cudaSetDevice(c->device), "set device");
+  int rc = set_dt(c, dt, on_device);
+  if (rc) return rc;
+  return stage_impl(c, s, 0);
+}
+
+int af_get_stage(af_ctx *c, double *const U[4], int on_device) {
+  if (!c || !U) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  return copy_state(c, c->last_out, nullptr, on_device, false, U);
+}
+
+int af_step(af_ctx *c, double *dt_used, int on_device) {
+  if (!c) return AF_EINVAL;
+  if (c->next_stage != 0) return fail(c, AF_EINVAL, "af_step called in the middle of a step (stage %d next)", c->next_stage);
+  CK(cudaSetDevice(c->device), "set device");
+  int rc = stage_impl(c, 0, 1);
+  if (!rc) rc = stage_impl(c, 1, 0);
+  if (!rc) rc = stage_impl(c, 2, 0);
+  if (rc) return rc;
+  if (dt_used) {
+    CK(cudaMemcpyAsync(dt_used, &c->sc->dt, sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy dt");
+    if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  return AF_OK;
+}
+
+int af_status(af_ctx *c, long long *counters, int reset) {
+  if (!c) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
+  AfStatus h;
+  CK(cudaMemcpy(&h, c->st, offsetof(AfStatus, repair), cudaMemcpyDeviceToHost), "read status");
+  if (counters)
+    for (int k = 0; k < AF_NSTAT; ++k) counters[k] = (long long)h.cnt[k];
+  if (reset) CK(cudaMemset(c->st, 0, sizeof(AfStatus)), "reset status");
+  if (h.err & AFE_REPAIR_OVERFLOW) return fail(c, AF_EBOUNDS, "round-off repair list overflowed (%d cells)", AF_MAX_REPAIR);
+  if (h.err & (AFE_NONADMISSIBLE | AFE_NONFINITE_DT))
+    return fail(c, AF_ENONPHYS, "%s", (h.err & AFE_NONFINITE_DT) ? "time step not finite/positive" : "non-admissible state");
+  return AF_OK;
+}
+
+int af_timing(af_ctx *c, int enable, double *ms, long long *launches) {
+  if (!c) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  if (enable) {
+    c->nev = 0;
+    c->timing = 1;
+    return AF_OK;
+  }
+  c->timing = 0;
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
+  double acc[AF_NKERNEL] = {0};
+  long long cnt[AF_NKERNEL] = {0};
+  for (int p = 0; p < c->nev; ++p) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, c->ev[2 * p], c->ev[2 * p + 1]), "event time");
+    acc[c->evk[p]] += t;
+    cnt[c->evk[p]]++;
+  }
+  for (int k = 0; k < AF_NKERNEL; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  c->nev = 0;
+  return AF_OK;
+}
+
+const char *af_last_error(const af_ctx *c) { return c ? c->msg : "null context"; }
+
+void af_destroy(af_ctx *c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  for (int b = 0; b < 3; ++b)
+    if (c->state[b]) cudaFree(c->state[b]);
+  if (c->work) cudaFree(c->work);
+  if (c->sc) cudaFree(c->sc);
+  if (c->st) cudaFree(c->st);
+  for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);
+  free(c->ev);
+  free(c->evk);
+  delete c;
+}
+
+int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream) {
+  if (op < 0 || op > 2 || !x || !out || (op == 1 && !y) || n < 0) return AF_EINVAL;
+  af_launch_math_check(op, x, y, out, n, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ECUDA;
+}
+
+int af_probe_fp64(void *stream, double *tflops) {
+  if (!tflops) return AF_EINVAL;
+  double f = 0.0;
+  const float ms = af_run_fp64_probe((cudaStream_t)stream, &f);
+  if (ms <= 0.f || cudaGetLastError() != cudaSuccess) return AF_ECUDA;
+  *tflops = f * 1e-12;
+  return AF_OK;
+}
+
+}  // extern "C"

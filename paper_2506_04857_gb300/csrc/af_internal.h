@@ -1,0 +1,84 @@
+// af_internal.h -- device-side data structures shared by the kernels and the
+// host API of libaf (not part of the public C ABI).
+//
+// Layout in HBM (all FP64, structure of arrays):
+//   state class c (0 average, 1 x-face, 2 y-face, 3 corner): [8][ey[c]][ex[c]]
+//   point data of class c and of the cell centres (c = 4): [NQ][nya][nxa]
+//   cell-centre values [8][nya][nxa], sensor [4][nya][nxa],
+//   face data [NQF][nya][nxa] for x-faces and for y-faces,
+//   Lambda [4][nya][nxa], Lim1 [8][nya][nxa], face theta [nya][nxa] (x and y).
+// nxa = nx (+1 for outflow), nya = ny (+1 for outflow).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define AF_NQP 20   // per point value: F1 (7), F2 (7), varrho_1, varrho_2, v (3), v.B
+#define AF_NQA 21   // per cell average: F1 (7), F2 (7), c_f1, c_f2, v (3), p_t, sqrt(rho)
+#define AF_NQF 18   // per face: F^LLF (8), G = theta^s (F - F^LLF) (8), theta^s, alpha^LLF
+#define AF_NSTAT 11
+#define AF_MAX_REPAIR 4096
+
+// F1 is stored without its B1 component (identically 0), F2 without B2.
+enum { QP_F1 = 0, QP_F2 = 7, QP_SR1 = 14, QP_SR2 = 15, QP_V1 = 16, QP_V2 = 17, QP_V3 = 18, QP_VB = 19 };
+enum { QA_F1 = 0, QA_F2 = 7, QA_CF1 = 14, QA_CF2 = 15, QA_V1 = 16, QA_V2 = 17, QA_V3 = 18, QA_PT = 19, QA_SRHO = 20 };
+enum { QF_FLLF = 0, QF_G = 8, QF_TS = 16, QF_AL = 17 };
+
+// counters (same meaning and order as the af_status counters in af.h)
+enum {
+  ST_SRC_LIMITED = 0, ST_LAMBDA_LT1, ST_FACE_THETA_LT1, ST_SENSOR_LT099, ST_NEWTON_SOLVES, ST_NEWTON_MAXIT,
+  ST_SHRINK, ST_POINT_LIMITED, ST_CFL_VIOLATIONS, ST_CENTER_LIMITED, ST_NONADMISSIBLE
+};
+
+// device error bits
+enum { AFE_NONADMISSIBLE = 1, AFE_REPAIR_OVERFLOW = 2, AFE_NONFINITE_DT = 4 };
+
+struct AfGrid {
+  int nx, ny, bc;          // cells; 0 periodic, 1 outflow
+  int nxa, nya;            // extents of the per-index work arrays
+  int ex[4], ey[4];        // extents of the four DoF classes
+  double dx, dy;
+  double gamma, gm1;
+  double kappa, cfl;
+  double c13;              // 1e-13 / (gamma - 1)
+  int pp_on, src_cell_on, src_point_on;
+};
+
+// Device-resident per-step scalars: dt stays on the device so that a whole
+// step can be captured in a CUDA graph.
+struct AfScalars {
+  double dt;
+  unsigned long long smax[2];   // running max of varrho_1, varrho_2 (bit patterns of non-negative doubles)
+  int pad[4];
+};
+
+struct AfStatus {
+  unsigned long long cnt[16];
+  int err;
+  int nrepair;
+  int repair[AF_MAX_REPAIR];
+};
+
+struct AfDev {
+  const double *un[4];    // U^n
+  const double *us[4];    // stage input U^(s)
+  double *uo[4];          // stage output
+  double *pd[5];          // point data, classes 0..3 and cell centres (4)
+  double *uc;             // limited cell-centre values
+  double *phi;            // phi_1x, phi_1y, phi_2, phi_3
+  double *fx, *fy;        // face data
+  double *lam, *lim1;     // Lambda_{L,R,D,U}, U^{Lim,1}
+  double *thx, *thy;      // unique face coefficients (read back by the repair pass)
+  AfScalars *sc;
+  AfStatus *st;
+};
+
+// kernel launchers (af_kernels.cu)
+void af_launch_pointdata(const AfDev &d, const AfGrid &g, int reduce_dt, cudaStream_t s);
+void af_launch_dt(const AfDev &d, const AfGrid &g, cudaStream_t s);
+void af_launch_points(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s);
+void af_launch_faces(const AfDev &d, const AfGrid &g, int mode, cudaStream_t s);
+void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s);
+void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
+void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
+float af_run_fp64_probe(cudaStream_t s, double *flops);
+void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s);
