@@ -176,6 +176,34 @@ void af_destroy(af_ctx *ctx);
  * Used by the tests to bound their error against the CUDA operators. */
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
 
+/* af_rhs without any device allocation, for callers that cannot allocate
+ * device memory on their hot path (a host framework that owns all device
+ * memory through its own pool, a real-time loop where cudaMalloc -- which can
+ * block, synchronise the device or fail under memory pressure -- is not
+ * allowed).  The paper has no counterpart: this is an interface of the
+ * library, not a step of the method.
+ *
+ * Computes the same semi-discrete right-hand side as af_rhs (both Powell
+ * source terms on) for the state U on an nx x ny grid of [x0,x1] x [y0,y1]
+ * with ratio of specific heats gamma and boundary condition bc.  U[cls] and
+ * dUdt[cls] are device arrays on the current device with the [8][nyp][nxp]
+ * layout of af_sizes; stream is a cudaStream_t (NULL: legacy default stream);
+ * the call is asynchronous in stream order and makes no allocation.
+ *
+ * Scratch: one fixed array in the library's static device memory, which every
+ * GPU that loads the library holds until the process exits, sized for index
+ * grids of at most AF_NOALLOC_MAX_POINTS = (nx, +1 for outflow) x (ny, +1 for
+ * outflow) points; larger grids are rejected with AF_EBOUNDS.  The first call
+ * on a device looks up the array's device address there (once per device);
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; calls that overlap on the GPU race on
+ * it, so serialise them (one stream, one host thread at a time).
+ * Returns AF_OK, AF_EINVAL (bad argument), AF_EBOUNDS (grid too large) or
+ * AF_ECUDA. */
+#define AF_NOALLOC_MAX_POINTS 4225
+int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, double x1, double y0, double y1,
+                   const double *const U[4], double *const dUdt[4], void *stream);
+
 /* Diagnostic: measured FP64 fused-multiply-add throughput of the current
  * device (a register-resident DFMA loop over all SMs, timed with CUDA events
  * on stream), written to *tflops (2 flops per FMA).  Used as the arithmetic

@@ -23,7 +23,7 @@ __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
     "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_sensor", "af_dt",
     "af_stage",
-    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
+    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
 ]
 
 AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
@@ -85,6 +85,8 @@ def _lib():
             lib.af_math_check.argtypes = [C.c_int, vp, vp, vp, C.c_longlong, vp]
             lib.af_timing.argtypes = [vp, C.c_int, vp, vp]
             lib.af_probe_fp64.argtypes = [vp, C.POINTER(C.c_double)]
+            lib.af_rhs_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
+                                           C.c_double, C.c_double, pp, pp, vp]
             _LIB = lib
         return _LIB
 
@@ -301,6 +303,25 @@ def af_probe_fp64(stream=None) -> float:
     if rc != AF_OK:
         raise AFError(rc, "af_probe_fp64 failed")
     return v.value
+
+
+AF_NOALLOC_MAX_POINTS = 4225
+
+
+def af_rhs_noalloc(nx: int, ny: int, gamma: float, bc: int, domain, U, out, stream=None) -> None:
+    """af_rhs computed in the library's static scratch, with no device allocation.
+
+    For callers that cannot allocate device memory on their hot path.  U and
+    out are lists of four CUDA float64 tensors in the state layout; grids with
+    (nx [+1 outflow]) x (ny [+1 outflow]) > AF_NOALLOC_MAX_POINTS are rejected
+    (AF_EBOUNDS).  Calls share one scratch array: do not overlap them on the GPU."""
+    handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    ins = _ptr_array([u.data_ptr() for u in U])
+    outs = _ptr_array([o.data_ptr() for o in out])
+    rc = _lib().af_rhs_noalloc(int(nx), int(ny), float(gamma), int(bc), *[float(v) for v in domain], ins, outs,
+                               handle)
+    if rc != AF_OK:
+        raise AFError(rc, "af_rhs_noalloc(%d, %d) failed" % (nx, ny))
 
 
 def af_last_error(ctx) -> str:
