@@ -40,6 +40,8 @@ WORKLOADS = {
     "blast512": ("low-beta blast 512x512 outflow, kappa=1 (profiling size)", lambda: ai.blast(512)),
     "ot512": ("Orszag-Tang 512x512 periodic, kappa=1", lambda: ai.orszag_tang(512)),
     "vortex64": ("smooth vortex 64x64 periodic, kappa=0", lambda: ai.vortex(64)),
+    "ensemble256": ("256 seeded Orszag-Tang runs, nx, ny drawn from {64,128,256,512}, kappa=1, one batch",
+                    lambda: ai.orszag_tang(64)),
 }
 
 # Algorithmic FP64 flops per cell-stage of each kernel: the arithmetic of the
@@ -199,6 +201,74 @@ def reference_arm(args, key, desc, pb):
     return 0
 
 
+def ensemble_bench(args, desc):
+    """The batched ensemble against the plain per-run loop on the same GPU."""
+    import torch
+    import paper_2506_04857_gb300 as af
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.Stream()
+    pbs = ai.ot_ensemble(256, seed=0)
+    states = [ai.dofs(p) for p in pbs]
+    cells = sum(p.nx * p.ny for p in pbs)
+    steps = max(3, (args.steps + 2) // 3 * 3)
+    warm = max(3, (args.warmup + 2) // 3 * 3)
+    with torch.cuda.stream(stream):
+        # batched: one persistent launch per pass for all runs, 3-step graph, autotuned tiles
+        b = af.af_batch_create([p.nx for p in pbs], [p.ny for p in pbs], [p.gamma for p in pbs],
+                               [p.bc for p in pbs])
+        af.af_batch_set_stream(b, stream)
+        for r, (p, U) in enumerate(zip(pbs, states)):
+            af.af_batch_set_domain(b, r, p.x0, p.x1, p.y0, p.y1)
+            af.af_batch_set_params(b, r, cfl=p.cfl, kappa=p.kappa)
+            af.af_batch_set_state(b, r, U)
+        choice = af.af_batch_autotune(b, reps=2)
+        af.af_batch_graph(b, True)
+        af.af_batch_step(b, warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        af.af_batch_step(b, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1)
+        rc, cnt = af.af_batch_status(b, reset=True)
+        if rc != af.AF_OK:
+            raise SystemExit("batch: " + af.af_batch_last_error(b))
+        af.af_batch_destroy(b)
+        # plain loop: one af_ctx per run, stepped one after the other on the same stream
+        solvers = []
+        for p, U in zip(pbs, states):
+            sv = af.Solver(p.nx, p.ny, p.gamma, p.bc, domain=(p.x0, p.x1, p.y0, p.y1), cfl=p.cfl, kappa=p.kappa,
+                           stream=stream)
+            sv.set_state(U)
+            solvers.append(sv)
+        for _ in range(warm):
+            for sv in solvers:
+                sv.step(dt_out=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            for sv in solvers:
+                sv.step(dt_out=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1)
+        for sv in solvers:
+            sv.close()
+    v_batch = cells * 3 * steps / (ms_batch * 1e-3)
+    v_loop = cells * 3 * steps / (ms_loop * 1e-3)
+    line = {"metric": "FP64 AF-MHD cell-stage updates/s", "value": v_batch, "unit": "cell-stage updates/s",
+            "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms_batch / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "runs": len(pbs), "cells": cells, "seed": 0},
+            "batched": {"value": v_batch, "autotune": choice, "graph": True, "launches_per_step": 19},
+            "plain_loop": {"value": v_loop, "ms_per_step": ms_loop / steps, "launches_per_step": 19 * len(pbs)},
+            "batched_over_loop": v_batch / v_loop, "limiter_counters": cnt}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +281,8 @@ def main():
     args = ap.parse_args()
     key = args.workload
     desc, make = WORKLOADS[key]
+    if key == "ensemble256" and args.impl == "ours":
+        return ensemble_bench(args, desc)
     pb = make()
     if args.impl == "reference":
         return reference_arm(args, key, desc, pb)

@@ -176,6 +176,38 @@ void af_destroy(af_ctx *ctx);
  * Used by the tests to bound their error against the CUDA operators. */
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
 
+/* ---- Batched ensembles (not in the paper: many independent runs at once) ----
+ * A batch holds nruns independent runs of possibly different sizes, boundary
+ * conditions, gamma, domains and parameters.  Every pass of a stage is one
+ * persistent kernel launch over a (run, tile) work list for all runs, dt is
+ * computed per run, and each run's result is bitwise identical to stepping it
+ * alone with an af_ctx.  Device memory: one arena, about 360 doubles per cell
+ * of every run.  State layout per run: as for af_ctx (af_sizes). */
+typedef struct af_batch af_batch;
+int af_batch_create(int nruns, const int *nx, const int *ny, const double *gamma, const int *bc, af_batch **out);
+int af_batch_set_domain(af_batch *b, int run, double x0, double x1, double y0, double y1);
+int af_batch_set_params(af_batch *b, int run, const af_params *p);
+int af_batch_set_stream(af_batch *b, void *stream);
+int af_batch_set_state(af_batch *b, int run, const double *const U[4], int on_device);
+int af_batch_get_state(af_batch *b, int run, double *const U[4], int on_device);
+/* nsteps SSP-RK3 steps of every run (dt of each run from its own state). */
+int af_batch_step(af_batch *b, int nsteps);
+/* enable = 1: capture a 3-step cycle of the RK loop into a CUDA graph (needs a
+ * non-default stream); af_batch_step then replays it.  enable = 0 drops it.
+ * Changing domains, parameters or the stream drops the graph. */
+int af_batch_graph(af_batch *b, int enable);
+/* Time reps repetitions of stage 0 for each tile shape (threads per tile:
+ * 32x4, 32x8, 64x2, 16x8, 64x4, 128x1) and cap on resident blocks per SM,
+ * keep the fastest.  Stage 0 reads only U^n, so the state does not advance.
+ * choice[4] (may be NULL) = {tile x, tile y, cap, microseconds per stage}. */
+int af_batch_autotune(af_batch *b, int reps, int *choice);
+/* dt used by the last step of one run (synchronises). */
+int af_batch_dt(af_batch *b, int run, double *dt);
+/* Counters summed over runs (newton_maxit: maximum) and the device error word, as af_status. */
+int af_batch_status(af_batch *b, long long *counters, int reset);
+const char *af_batch_last_error(const af_batch *b);
+void af_batch_destroy(af_batch *b);
+
 /* af_rhs without any device allocation, for callers that cannot allocate
  * device memory on their hot path (a host framework that owns all device
  * memory through its own pool, a real-time loop where cudaMalloc -- which can

@@ -23,7 +23,10 @@ __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
     "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_sensor", "af_dt",
     "af_stage",
-    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
+    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
+    "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
+    "af_batch_step", "af_batch_graph", "af_batch_autotune", "af_batch_dt", "af_batch_status", "af_batch_last_error",
+    "af_batch_destroy", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
 ]
 
 AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
@@ -85,6 +88,22 @@ def _lib():
             lib.af_math_check.argtypes = [C.c_int, vp, vp, vp, C.c_longlong, vp]
             lib.af_timing.argtypes = [vp, C.c_int, vp, vp]
             lib.af_probe_fp64.argtypes = [vp, C.POINTER(C.c_double)]
+            ip_ = C.POINTER(C.c_int)
+            lib.af_batch_create.argtypes = [C.c_int, ip_, ip_, dp, ip_, C.POINTER(C.c_void_p)]
+            lib.af_batch_set_domain.argtypes = [vp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double]
+            lib.af_batch_set_params.argtypes = [vp, C.c_int, C.POINTER(af_params)]
+            lib.af_batch_set_stream.argtypes = [vp, vp]
+            lib.af_batch_set_state.argtypes = [vp, C.c_int, pp, C.c_int]
+            lib.af_batch_get_state.argtypes = [vp, C.c_int, pp, C.c_int]
+            lib.af_batch_step.argtypes = [vp, C.c_int]
+            lib.af_batch_graph.argtypes = [vp, C.c_int]
+            lib.af_batch_autotune.argtypes = [vp, C.c_int, ip_]
+            lib.af_batch_dt.argtypes = [vp, C.c_int, dp]
+            lib.af_batch_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+            lib.af_batch_last_error.argtypes = [vp]
+            lib.af_batch_last_error.restype = C.c_char_p
+            lib.af_batch_destroy.argtypes = [vp]
+            lib.af_batch_destroy.restype = None
             lib.af_rhs_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                            C.c_double, C.c_double, pp, pp, vp]
             _LIB = lib
@@ -339,6 +358,96 @@ def af_math_check(op: int, x, y, out, stream=None) -> None:
     rc = _lib().af_math_check(op, x.data_ptr(), None if y is None else y.data_ptr(), out.data_ptr(), x.numel(), handle)
     if rc != AF_OK:
         raise AFError(rc, "af_math_check failed")
+
+
+# ---------------------------------------------------------------------------
+# batched ensembles
+# ---------------------------------------------------------------------------
+def _bcheck(b, rc: int):
+    if rc != AF_OK:
+        r = _lib().af_batch_last_error(b)
+        raise AFError(rc, r.decode() if r else "")
+
+
+def af_batch_create(nx, ny, gamma, bc):
+    """nx, ny, gamma, bc: per-run sequences of equal length."""
+    _torch()
+    n = len(nx)
+    a = (C.c_int * n)(*[int(v) for v in nx])
+    b_ = (C.c_int * n)(*[int(v) for v in ny])
+    g = (C.c_double * n)(*[float(v) for v in gamma])
+    c = (C.c_int * n)(*[int(v) for v in bc])
+    h = C.c_void_p()
+    rc = _lib().af_batch_create(n, a, b_, g, c, C.byref(h))
+    if rc != AF_OK:
+        raise AFError(rc, "af_batch_create(%d runs) failed" % n)
+    return h
+
+
+def af_batch_set_domain(b, run, x0, x1, y0, y1):
+    _bcheck(b, _lib().af_batch_set_domain(b, run, x0, x1, y0, y1))
+
+
+def af_batch_set_params(b, run, cfl=0.2, kappa=0.0, pp_on=True, src_cell_on=True, src_point_on=True):
+    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on))
+    _bcheck(b, _lib().af_batch_set_params(b, run, C.byref(p)))
+
+
+def af_batch_set_stream(b, stream=None):
+    handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _bcheck(b, _lib().af_batch_set_stream(b, handle))
+
+
+def af_batch_set_state(b, run, U):
+    dev = all(_is_tensor(u) and u.is_cuda for u in U)
+    keep = [u.contiguous() if dev else np.ascontiguousarray(u.detach().cpu().numpy() if _is_tensor(u) else u,
+                                                             dtype=np.float64) for u in U]
+    ptrs = _ptr_array([k.data_ptr() if dev else k.ctypes.data for k in keep])
+    _bcheck(b, _lib().af_batch_set_state(b, run, ptrs, int(dev)))
+
+
+def af_batch_get_state(b, run, out):
+    """out: four arrays/tensors of the run's class shapes (CUDA tensors or numpy)."""
+    dev = int(_is_tensor(out[0]) and out[0].is_cuda)
+    ptrs = _ptr_array([o.data_ptr() if dev else o.ctypes.data for o in out])
+    _bcheck(b, _lib().af_batch_get_state(b, run, ptrs, dev))
+    return out
+
+
+def af_batch_step(b, nsteps: int = 1):
+    _bcheck(b, _lib().af_batch_step(b, int(nsteps)))
+
+
+def af_batch_graph(b, enable: bool = True):
+    _bcheck(b, _lib().af_batch_graph(b, int(enable)))
+
+
+def af_batch_autotune(b, reps: int = 3):
+    ch = (C.c_int * 4)()
+    _bcheck(b, _lib().af_batch_autotune(b, int(reps), ch))
+    return {"tile": (ch[0], ch[1]), "blocks_per_sm_cap": ch[2], "us_per_stage": ch[3]}
+
+
+def af_batch_dt(b, run: int) -> float:
+    v = C.c_double()
+    _bcheck(b, _lib().af_batch_dt(b, run, C.byref(v)))
+    return v.value
+
+
+def af_batch_status(b, reset: bool = False):
+    cnt = (C.c_longlong * AF_NSTAT)()
+    rc = _lib().af_batch_status(b, cnt, int(reset))
+    return rc, dict(zip(STAT_NAMES, [int(v) for v in cnt]))
+
+
+def af_batch_last_error(b) -> str:
+    r = _lib().af_batch_last_error(b)
+    return r.decode() if r else ""
+
+
+def af_batch_destroy(b):
+    if b:
+        _lib().af_batch_destroy(b)
 
 
 # ---------------------------------------------------------------------------

@@ -72,6 +72,12 @@ struct AfDev {
   AfStatus *st;
 };
 
+// one member of a batch (af_batch.cu): its work pointers and grid
+struct AfRun {
+  AfDev d;
+  AfGrid g;
+};
+
 // kernel launchers (af_kernels.cu)
 void af_launch_pointdata(const AfDev &d, const AfGrid &g, int reduce_dt, cudaStream_t s);
 void af_launch_dt(const AfDev &d, const AfGrid &g, cudaStream_t s);
@@ -81,4 +87,8 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
+// persistent batched launch of one pass (AF_K_* id) over a (run, i0, j0) tile list
+void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
+                     double a, double b, int reduce_dt, cudaStream_t s);
+int af_batch_occupancy(int pass, dim3 block);   // resident blocks per SM
 void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s);

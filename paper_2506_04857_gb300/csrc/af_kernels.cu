@@ -26,6 +26,7 @@
 // Limiter fast paths: where the paper's limiter provably returns theta = 1
 // (all tested quantities clear 1e-13 by a wide margin) the blend is skipped;
 // everywhere else the full procedure runs.  Results are identical.
+#include "../../include/af.h"
 #include "af_internal.h"
 #include "af_math.cuh"
 
@@ -267,9 +268,7 @@ __device__ __forceinline__ void load8(const SV &v, int i, int j, double *U) {
   for (int k = 0; k < 8; ++k) U[k] = v(i, j, k);
 }
 
-__global__ void __launch_bounds__(128) k_pointdata(AfDev d, AfGrid g, int reduce_dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void b_pointdata(const AfDev &d, const AfGrid &g, const int i, const int j, int reduce_dt) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
   double m1 = 0.0, m2 = 0.0;
@@ -331,8 +330,7 @@ __global__ void __launch_bounds__(128) k_pointdata(AfDev d, AfGrid g, int reduce
 }
 
 // dt = cfl / (max varrho_1 / dx + max varrho_2 / dy) over the four DoF classes of U^n.
-__global__ void k_dt(AfDev d, AfGrid g) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void b_dt(const AfDev &d, const AfGrid &g) {
   const double m1 = __longlong_as_double((long long)d.sc->smax[0]);
   const double m2 = __longlong_as_double((long long)d.sc->smax[1]);
   const double dt = g.cfl / (m1 / g.dx + m2 / g.dy);
@@ -514,9 +512,8 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   phi[3] = ddiv(absd(num), absd(Ub(c_i, c_j, 4) + Ub(c_i, c_j, 5)) + 1e-40);
 }
 
-__global__ void __launch_bounds__(128) k_points(AfDev d, AfGrid g, double a, double b, int mode) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b,
+                                         int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const double dt = mode == 1 ? 1.0 : d.sc->dt;
   const double cx = 0.5 * dt / g.dx, cy = 0.5 * dt / g.dy;   // the FVS lines carry a factor 1/2
@@ -667,9 +664,7 @@ __device__ __forceinline__ void face(const AfDev &d, const AfGrid &g, double *ou
   nsens += ts < 0.99;
 }
 
-__global__ void __launch_bounds__(128) k_faces(AfDev d, AfGrid g, int mode) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const int i, const int j, int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
   const bool llf = mode == 0 && (g.pp_on || g.kappa != 0.0);
@@ -793,9 +788,8 @@ __device__ __noinline__ void cell_limiter_full(const double *Ullf, const double 
   flux_limiter_box(L1, H, eps_rho, eps_p, g.gm1, Lam, nl);
 }
 
-__global__ void __launch_bounds__(128) k_cells(AfDev d, AfGrid g, double a, double b, int mode) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b,
+                                        int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
   int nsrc = 0, nlam = 0, ncfl = 0;
@@ -1032,9 +1026,7 @@ __device__ __forceinline__ void limited_value(const AfDev &d, const AfGrid &g, i
   }
 }
 
-__global__ void __launch_bounds__(128) k_final(AfDev d, AfGrid g, double a, double b) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+__device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b) {
   int nface = 0;
   if (i < g.nx && j < g.ny) {
     const double dt = d.sc->dt;
@@ -1090,8 +1082,7 @@ __device__ void fe_of(const AfDev &d, const AfGrid &g, int i, int j, double dt, 
   limited_value(d, g, i, j, th, dt, fe);
 }
 
-__global__ void k_repair(AfDev d, AfGrid g, double a, double b) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void b_repair(const AfDev &d, const AfGrid &g, double a, double b) {
   int n = d.st->nrepair;
   if (n <= 0) return;
   if (n > AF_MAX_REPAIR) n = AF_MAX_REPAIR;
@@ -1155,6 +1146,75 @@ __global__ void k_repair(AfDev d, AfGrid g, double a, double b) {
   d.st->cnt[ST_NONADMISSIBLE] += nbad;
   if (nbad) d.st->err |= AFE_NONADMISSIBLE;
   d.st->nrepair = 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Kernels: one run (grid over its index points) and a batch of runs (a
+// persistent grid walking a (run, tile) work list; tiles are blockDim-sized).
+// ---------------------------------------------------------------------------
+#define AF_IJ blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y
+#define AF_BATCH_LOOP(call)                                       \
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {       \
+    const int4 w = items[it];                                     \
+    const AfRun *__restrict__ r = runs + w.x;                     \
+    const int i = w.y + threadIdx.x, j = w.z + threadIdx.y;       \
+    call;                                                         \
+  }
+
+__global__ void __launch_bounds__(128) k_pointdata(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                                   int reduce_dt) {
+  b_pointdata(d, g, AF_IJ, reduce_dt);
+}
+__global__ void __launch_bounds__(256) kb_pointdata(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
+                                                    int nitems, int reduce_dt) {
+  AF_BATCH_LOOP(b_pointdata(r->d, r->g, i, j, reduce_dt));
+}
+__global__ void k_dt(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) b_dt(d, g);
+}
+__global__ void kb_dt(const AfRun *__restrict__ runs, int nruns) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nruns) b_dt(runs[t].d, runs[t].g);
+}
+__global__ void __launch_bounds__(128) k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                                double a, double b, int mode) {
+  b_points(d, g, AF_IJ, a, b, mode);
+}
+__global__ void __launch_bounds__(256) kb_points(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
+                                                 int nitems, double a, double b) {
+  AF_BATCH_LOOP(b_points(r->d, r->g, i, j, a, b, 0));
+}
+__global__ void __launch_bounds__(128) k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                               int mode) {
+  b_faces(d, g, AF_IJ, mode);
+}
+__global__ void __launch_bounds__(256) kb_faces(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
+                                                int nitems) {
+  AF_BATCH_LOOP(b_faces(r->d, r->g, i, j, 0));
+}
+__global__ void __launch_bounds__(128) k_cells(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                               double a, double b, int mode) {
+  b_cells(d, g, AF_IJ, a, b, mode);
+}
+__global__ void __launch_bounds__(256) kb_cells(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
+                                                int nitems, double a, double b) {
+  AF_BATCH_LOOP(b_cells(r->d, r->g, i, j, a, b, 0));
+}
+__global__ void __launch_bounds__(128) k_final(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                               double a, double b) {
+  b_final(d, g, AF_IJ, a, b);
+}
+__global__ void __launch_bounds__(256) kb_final(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
+                                                int nitems, double a, double b) {
+  AF_BATCH_LOOP(if (r->g.pp_on) b_final(r->d, r->g, i, j, a, b));
+}
+__global__ void k_repair(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g, double a, double b) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) b_repair(d, g, a, b);
+}
+__global__ void kb_repair(const AfRun *__restrict__ runs, int nruns, double a, double b) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nruns && runs[t].g.pp_on) b_repair(runs[t].d, runs[t].g, a, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -1232,4 +1292,32 @@ float af_run_fp64_probe(cudaStream_t s, double *flops) {
 void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s) {
   if (n <= 0) return;
   k_math_check<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(op, x, y, out, n);
+}
+
+void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
+                     double a, double b, int reduce_dt, cudaStream_t s) {
+  switch (pass) {
+    case AF_K_POINTDATA: kb_pointdata<<<nblocks, block, 0, s>>>(runs, items, nitems, reduce_dt); break;
+    case AF_K_DT: kb_dt<<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns); break;
+    case AF_K_POINTS: kb_points<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
+    case AF_K_FACES: kb_faces<<<nblocks, block, 0, s>>>(runs, items, nitems); break;
+    case AF_K_CELLS: kb_cells<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
+    case AF_K_FINAL: kb_final<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
+    case AF_K_REPAIR: kb_repair<<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns, a, b); break;
+    default: break;
+  }
+}
+
+int af_batch_occupancy(int pass, dim3 block) {
+  int n = 0;
+  const int threads = block.x * block.y;
+  switch (pass) {
+    case AF_K_POINTDATA: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_pointdata, threads, 0); break;
+    case AF_K_POINTS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_points, threads, 0); break;
+    case AF_K_FACES: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_faces, threads, 0); break;
+    case AF_K_CELLS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_cells, threads, 0); break;
+    case AF_K_FINAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_final, threads, 0); break;
+    default: n = 1;
+  }
+  return n > 0 ? n : 1;
 }
