@@ -87,6 +87,12 @@ def _gauss_legendre(n: int):
 
 def dofs(pb: Problem, quad: int = 5) -> List[np.ndarray]:
     """The four DoF classes of pb's initial condition."""
+    return class_values(pb, lambda X, Y: prim_to_cons(pb.prim(X, Y), pb.gamma), quad)
+
+
+def class_values(pb: Problem, fn, quad: int = 5) -> List[np.ndarray]:
+    """The four DoF classes of a field fn(X, Y) -> (8, ...) on pb's grid: cell
+    averages by tensor Gauss-Legendre quadrature, point values exactly."""
     nx, ny = pb.nx, pb.ny
     dx, dy = pb.dx, pb.dy
     ext = class_extents(nx, ny, pb.bc)
@@ -95,18 +101,46 @@ def dofs(pb: Problem, quad: int = 5) -> List[np.ndarray]:
     xf = pb.x0 + np.arange(ext[1][0]) * dx
     yf = pb.y0 + np.arange(ext[2][1]) * dy
     out = []
-    # cell averages: tensor Gauss-Legendre
     xg, wg = _gauss_legendre(quad)
-    acc = np.zeros((8, ny, nx))
+    acc = None
     for a in range(quad):
         for b in range(quad):
             X, Y = np.meshgrid(xc + xg[a] * dx, yc + xg[b] * dy, indexing="xy")
-            acc += wg[a] * wg[b] * prim_to_cons(pb.prim(X, Y), pb.gamma)
+            v = wg[a] * wg[b] * np.asarray(fn(X, Y))
+            acc = v if acc is None else acc + v
     out.append(np.ascontiguousarray(acc))
     for xs, ys in ((xf, yc), (xc, yf), (xf, yf)):
         X, Y = np.meshgrid(xs, ys, indexing="xy")
-        out.append(np.ascontiguousarray(prim_to_cons(pb.prim(X, Y), pb.gamma)))
+        out.append(np.ascontiguousarray(np.asarray(fn(X, Y))))
     return out
+
+
+def smooth_direction(pb: Problem, seed: int, kmax: int = 4) -> List[np.ndarray]:
+    """A seeded smooth direction in state space: every conserved variable is a
+    random Fourier series with wave numbers |k| <= kmax, periodic on pb's
+    domain, taken as DoFs like a state; scaled to unit 2-norm over all DoFs.
+    Used for directional-derivative (finite-difference) checks."""
+    rng = np.random.default_rng(seed)
+    Lx, Ly = pb.x1 - pb.x0, pb.y1 - pb.y0
+    ks = [(a, b) for a in range(-kmax, kmax + 1) for b in range(-kmax, kmax + 1) if a * a + b * b <= kmax * kmax]
+    coef = rng.normal(size=(8, len(ks)))
+    phase = rng.uniform(0.0, 2.0 * math.pi, size=(8, len(ks)))
+    # sum_k c cos(2 pi (a x' + b y') + ph) = Re(Ey^T M Ex) on a tensor grid,
+    # M[b, a] = sum of c e^{i ph} over the modes (a, b)
+    M = np.zeros((8, 2 * kmax + 1, 2 * kmax + 1), dtype=complex)
+    for t, (a, b) in enumerate(ks):
+        M[:, b + kmax, a + kmax] += coef[:, t] * np.exp(1j * phase[:, t])
+    kk = np.arange(-kmax, kmax + 1)
+
+    def fn(X, Y):
+        xs, ys = X[0, :], Y[:, 0]     # class_values evaluates on meshgrids (indexing "xy")
+        Ex = np.exp(2j * math.pi * np.outer(kk, (xs - pb.x0) / Lx))
+        Ey = np.exp(2j * math.pi * np.outer(kk, (ys - pb.y0) / Ly))
+        return np.real(np.matmul(Ey.T, np.matmul(M, Ex)))
+
+    d = class_values(pb, fn)
+    nrm = math.sqrt(sum(float((x * x).sum()) for x in d))
+    return [x / nrm for x in d]
 
 
 def _b(x, v):

@@ -42,6 +42,8 @@ WORKLOADS = {
     "vortex64": ("smooth vortex 64x64 periodic, kappa=0", lambda: ai.vortex(64)),
     "ensemble256": ("256 seeded Orszag-Tang runs, nx, ny drawn from {64,128,256,512}, kappa=1, one batch",
                     lambda: ai.orszag_tang(64)),
+    "adjoint256": ("discrete adjoint: 256x256 perturbed vortex, kappa=0, 200 steps, checkpoints every 20",
+                   lambda: ai.perturbed_vortex(256, seed=0)),
 }
 
 # Algorithmic FP64 flops per cell-stage of each kernel: the arithmetic of the
@@ -269,6 +271,61 @@ def ensemble_bench(args, desc):
     return 0
 
 
+def adjoint_cost(stream, nsteps=200, every=20):
+    """Wall-time ratio backward / forward of the differentiable solve on the
+    adjoint workload: 256x256 perturbed vortex (kappa = 0), 200 SSP-RK3 steps,
+    checkpoints every 20 steps, objective the total magnetic energy.  The
+    backward pass includes the recomputation of every segment from its
+    checkpoint and the stage recomputation inside each adjoint step."""
+    import torch
+    import paper_2506_04857_gb300 as af
+    from paper_2506_04857_gb300.adjoint import af_steps, magnetic_energy
+    pb = ai.perturbed_vortex(256, seed=0)
+    s = af.Solver(pb.nx, pb.ny, pb.gamma, pb.bc, domain=(pb.x0, pb.x1, pb.y0, pb.y1), cfl=pb.cfl, kappa=0.0,
+                  stream=stream)
+    U0 = [torch.from_numpy(u).cuda() for u in ai.dofs(pb)]
+
+    def once(n):
+        X0 = [t.clone().requires_grad_(True) for t in U0]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        out = af_steps(s, X0, n, checkpoint_every=every)
+        ev[1].record(stream)
+        J = magnetic_energy(out, pb.dx, pb.dy, pb.bc)
+        ev[2].record(stream)
+        J.backward()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+
+    once(2 * every)                   # warm-up (first adjoint call allocates its workspace)
+    fwd, bwd = once(nsteps)
+    s.close()
+    return {"workload": "256x256 perturbed MHD vortex (random Fourier |k|<=4, amplitude 1e-3 of rho and B), "
+                        "kappa=0, %d steps, checkpoints every %d steps, objective total magnetic energy" % (nsteps, every),
+            "forward_ms": fwd, "backward_ms": bwd, "forward_ms_per_step": fwd / nsteps,
+            "adjoint_ms_per_step": bwd / nsteps, "ratio": bwd / fwd,
+            "target": "<= 4", "includes": "segment recompute from checkpoints + per-step stage recompute + 3 VJPs"}
+
+
+def adjoint_bench(args, desc):
+    """The adjoint workload alone: its backward / forward wall-time ratio."""
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    stream = torch.cuda.current_stream()
+    r = adjoint_cost(stream, nsteps=args.adjoint_steps)
+    cells = 256 * 256
+    line = {"metric": "adjoint/forward wall-time ratio", "value": r["ratio"], "unit": "x", "n_gpus": 1,
+            "steps": args.adjoint_steps, "warmup": 1, "ms_per_step": r["adjoint_ms_per_step"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "cells": cells, "checkpoint_every": 20},
+            "adjoint": r,
+            "backward_cell_steps_per_s": cells * args.adjoint_steps / (r["backward_ms"] * 1e-3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,11 +335,15 @@ def main():
     ap.add_argument("--workload", default="blast2048", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     key = args.workload
     desc, make = WORKLOADS[key]
     if key == "ensemble256" and args.impl == "ours":
         return ensemble_bench(args, desc)
+    if key == "adjoint256" and args.impl == "ours":
+        return adjoint_bench(args, desc)
     pb = make()
     if args.impl == "reference":
         return reference_arm(args, key, desc, pb)
@@ -397,6 +458,8 @@ def main():
                            else "no L2 flush; state smaller than L2"},
                 "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "clocks": clk,
                 "limiter_counters": cnt}
+        if not args.no_adjoint and world == 1:
+            line["adjoint"] = adjoint_cost(stream)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(key, pb)
         print(json.dumps(line), flush=True)

@@ -144,6 +144,29 @@ int af_stage(af_ctx *ctx, int s, const double *dt, int on_device);
  * stage 1, U^{n+1} after stage 2 (same layout as the state). */
 int af_get_stage(af_ctx *ctx, double *const U[4], int on_device);
 
+/* Discrete adjoint (not in the paper; differentiates its scheme).
+ * af_rhs_vjp: out = (dL/dU)^T v for the semi-discrete operator of af_rhs at
+ * the current state (alpha = max varrho on each FVS line differentiated
+ * through the point that attains it).  v and out have the state layout. */
+int af_rhs_vjp(af_ctx *ctx, const double *const v[4], double *const out[4], int on_device);
+
+/* lam_out = (dU^{n+1}/dU^n)^T lam_in for one SSP-RK3 step from the current
+ * state U^n with the recorded time step *dt (host or device pointer, held
+ * fixed: dt is not differentiated; a host dt must be > 0, a device dt is
+ * taken as recorded).  Stages 0 and 1 are recomputed from U^n, and stage 2
+ * too unless flags has AF_ADJ_RECORDED.  The transpose is that of the branch
+ * on which the shock sensor is off (kappa = 0, else AF_EINVAL) and every
+ * positivity limiter is inactive, where a limited forward-Euler stage equals
+ * U + dt L(U).  If a limiter acts during the recomputed stages the call
+ * returns AF_EINVAL (lam_out then holds no gradient).  AF_ADJ_RECORDED: the
+ * caller has established, from the counters of the forward step (af_status),
+ * that no limiter acted in its last stage, which is then not recomputed.
+ * lam_out may alias lam_in.  The state is not advanced.  The call
+ * synchronises the stream once, at its end. */
+enum { AF_ADJ_RECORDED = 1 };
+int af_adjoint_step(af_ctx *ctx, const double *dt, int dt_on_device, const double *const lam_in[4],
+                    double *const lam_out[4], int on_device, int flags);
+
 /* af_dt followed by the three stages.  *dt_used (host or device, may be NULL)
  * receives the step's dt. */
 int af_step(af_ctx *ctx, double *dt_used, int on_device);

@@ -45,7 +45,8 @@ def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, 
 def build(force: bool = False) -> None:
     """Compile the oracle (plain and counting builds) with g++."""
     os.makedirs(_BUILD, exist_ok=True)
-    jobs = [("liboracle.so", ["-fopenmp"]), ("liboracle_count.so", ["-DAF_ORACLE_COUNT"])]
+    jobs = [("liboracle.so", ["-fopenmp"]), ("liboracle_count.so", ["-DAF_ORACLE_COUNT"]),
+            ("liboracle_cs.so", ["-DAF_ORACLE_COMPLEX"])]
     procs = []
     for name, extra in jobs:
         out = os.path.join(_BUILD, name)
@@ -60,12 +61,13 @@ def build(force: bool = False) -> None:
         os.replace(tmp, out)
 
 
-def _lib(count: bool = False):
-    key = "count" if count else "plain"
+def _lib(count: bool = False, complex_step: bool = False):
+    key = "cs" if complex_step else ("count" if count else "plain")
+    name = {"cs": "liboracle_cs.so", "count": "liboracle_count.so", "plain": "liboracle.so"}[key]
     with _LOCK:
         if key not in _LIBS:
             build()
-            lib = C.CDLL(os.path.join(_BUILD, "liboracle_count.so" if count else "liboracle.so"))
+            lib = C.CDLL(os.path.join(_BUILD, name))
             pp = C.POINTER(C.POINTER(C.c_double))
             dp = C.POINTER(C.c_double)
             lib.or_dt.restype = C.c_double
@@ -90,6 +92,9 @@ def _lib(count: bool = False):
             lib.or_scaling_limiter.argtypes = [dp, dp, C.c_double, dp, dp]
             lib.or_sensor_phi.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
             lib.or_sensor.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp, dp]
+            if key == "cs":
+                lib.or_step_cs.restype = C.c_int
+                lib.or_step_cs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double]
             lib.or_counts.restype = C.c_int
             lib.or_counts.argtypes = [C.POINTER(C.c_longlong), C.c_int]
             _LIBS[key] = lib
@@ -233,6 +238,16 @@ def sensor_phi(c, e, w, n, s, gamma, dx, dy) -> np.ndarray:
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (c, e, w, n, s)]
     _lib().or_sensor_phi(*[_dp(a) for a in arrs], gamma, dx, dy, _dp(out))
     return out
+
+
+def step_complex(pb, U_re, U_im, dt, **kw):
+    """One SSP-RK3 step of the complex state U_re + i U_im with fixed dt
+    (complex-step differentiation).  Returns (re, im, limiter events)."""
+    P = params_for(pb, **kw)
+    re = [a.copy() for a in _check(U_re, pb.nx, pb.ny, pb.bc)]
+    im = [a.copy() for a in _check(U_im, pb.nx, pb.ny, pb.bc)]
+    act = _lib(complex_step=True).or_step_cs(C.byref(P), pb.nx, pb.ny, _ptrs(re), _ptrs(im), dt)
+    return re, im, act
 
 
 def counts(reset: bool = True) -> np.ndarray:

@@ -79,6 +79,45 @@ static inline real exp(real a) { tick(K_EXP); return std::exp(a.v); }
 static inline real fabs(real a) { tick(K_MINMAX); return std::fabs(a.v); }
 static inline bool is_finite(real a) { return std::isfinite(a.v); }
 static inline void set_phase(int p) { g_phase = p; }
+#elif defined(AF_ORACLE_COMPLEX)
+// Complex-step build: a + i b carries the directional derivative b of every
+// quantity along the perturbation of the input; branches (comparisons,
+// min/max, |.|) follow the real part.
+struct Cx {
+  double re, im;
+  Cx() : re(0), im(0) {}
+  Cx(double x) : re(x), im(0) {}
+  Cx(double a, double b) : re(a), im(b) {}
+};
+typedef Cx real;
+static inline double val(real x) { return x.re; }
+static inline real operator+(real a, real b) { return Cx(a.re + b.re, a.im + b.im); }
+static inline real operator-(real a, real b) { return Cx(a.re - b.re, a.im - b.im); }
+static inline real operator*(real a, real b) { return Cx(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static inline real operator/(real a, real b) {
+  const double d = b.re * b.re + b.im * b.im;
+  return Cx((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+static inline real operator-(real a) { return Cx(-a.re, -a.im); }
+static inline real &operator+=(real &a, real b) { a = a + b; return a; }
+static inline real &operator-=(real &a, real b) { a = a - b; return a; }
+static inline bool operator<(real a, real b) { return a.re < b.re; }
+static inline bool operator>(real a, real b) { return a.re > b.re; }
+static inline bool operator<=(real a, real b) { return a.re <= b.re; }
+static inline bool operator>=(real a, real b) { return a.re >= b.re; }
+static inline real sqrt(real a) {
+  // principal square root; for the step size used the imaginary part is tiny
+  const double r = std::sqrt(a.re);
+  if (r == 0.0) return Cx(0.0, 0.0);
+  return Cx(r, a.im / (2.0 * r));
+}
+static inline real exp(real a) {
+  const double e = std::exp(a.re);
+  return Cx(e * std::cos(a.im), e * std::sin(a.im));
+}
+static inline real fabs(real a) { return a.re < 0.0 ? -a : a; }
+static inline bool is_finite(real a) { return std::isfinite(a.re) && std::isfinite(a.im); }
+static inline void set_phase(int) {}
 #else
 typedef double real;
 static inline double val(real x) { return x; }
@@ -1310,6 +1349,46 @@ void or_sensor_phi(const double *c, const double *e, const double *w, const doub
   sensor_phi(d[0], d[1], d[2], d[3], d[4], dx, dy, ph);
   for (int q = 0; q < 4; ++q) phi[q] = val(ph[q]);
 }
+
+#ifdef AF_ORACLE_COMPLEX
+// One SSP-RK3 step of the complex state (re[cls], im[cls]) with the fixed time
+// step dt (complex-step differentiation; dt is not perturbed).
+int or_step_cs(const or_params *p, int nx, int ny, double *const *re, double *const *im, double dt) {
+  Ctx C;
+  make_ctx(p, nx, ny, C);
+  State Sn;
+  Sn.init(C);
+  for (int cls = 0; cls < 4; ++cls) {
+    int ex = C.ext[cls][0], ey = C.ext[cls][1];
+    for (int k = 0; k < 8; ++k)
+      for (int j = 0; j < ey; ++j)
+        for (int i = 0; i < ex; ++i) {
+          const size_t o = ((size_t)k * ey + j) * ex + i;
+          Sn.c[cls].at(C, k, i, j) = Cx(re[cls][o], im[cls][o]);
+        }
+  }
+  long long loc[ST_NSTATS] = {0};
+  State S1, S2, S3;
+  stage(C, Sn, Sn, real(dt), real(0.0), real(1.0), S1, loc);
+  stage(C, Sn, S1, real(dt), real(3.0) / real(4.0), real(1.0) / real(4.0), S2, loc);
+  stage(C, Sn, S2, real(dt), real(1.0) / real(3.0), real(2.0) / real(3.0), S3, loc);
+  for (int cls = 0; cls < 4; ++cls) {
+    int ex = C.ext[cls][0], ey = C.ext[cls][1];
+    for (int k = 0; k < 8; ++k)
+      for (int j = 0; j < ey; ++j)
+        for (int i = 0; i < ex; ++i) {
+          const size_t o = ((size_t)k * ey + j) * ex + i;
+          re[cls][o] = S3.c[cls].at(C, k, i, j).re;
+          im[cls][o] = S3.c[cls].at(C, k, i, j).im;
+        }
+  }
+  // limiter activity (the derivative is that of the branch taken)
+  long long act = 0;
+  for (int k = 0; k < ST_NSTATS; ++k)
+    if (k != ST_NEWTON_MAXIT && k != ST_SENSOR_LT099 && k != ST_CFL_VIOLATIONS) act += loc[k];
+  return (int)act;
+}
+#endif
 
 // Operation counts per phase since the last reset (counting build only).
 // out[NPHASE][NKIND]: add(+sub), mul, div, sqrt, exp, min/max/|.|, comparisons.

@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
-    "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_sensor", "af_dt",
+    "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step", "af_sensor", "af_dt",
     "af_stage",
     "af_step", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
     "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
@@ -32,6 +32,7 @@ __all__ = [
 AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
 AF_OK, AF_EINVAL, AF_ECUDA, AF_ENOMEM, AF_ENONPHYS, AF_EBOUNDS, AF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 AF_NSTAT = 11
+AF_ADJ_RECORDED = 1
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
               "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
 _CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
@@ -80,6 +81,8 @@ def _lib():
             lib.af_stage.argtypes = [vp, C.c_int, vp, C.c_int]
             lib.af_step.argtypes = [vp, vp, C.c_int]
             lib.af_get_stage.argtypes = [vp, pp, C.c_int]
+            lib.af_rhs_vjp.argtypes = [vp, pp, pp, C.c_int]
+            lib.af_adjoint_step.argtypes = [vp, vp, C.c_int, pp, pp, C.c_int, C.c_int]
             lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
             lib.af_last_error.argtypes = [vp]
             lib.af_last_error.restype = C.c_char_p
@@ -233,6 +236,36 @@ def af_get_stage(ctx, out=None, device: bool = True):
     """The result of the most recent stage (U1, U2 or U^{n+1})."""
     out, ptrs, dev = _outputs(ctx, out, device)
     _check(ctx, _lib().af_get_stage(ctx, ptrs, dev))
+    return out
+
+
+def af_rhs_vjp(ctx, v, out=None, device: bool = True):
+    """(dL/dU)^T v at the current state (v: four arrays/tensors in the state layout)."""
+    ptrs, dev, keep = _marshal_in(ctx, v)
+    out, optrs, odev = _outputs(ctx, out, device)
+    if dev != odev:
+        raise ValueError("v and out must both be on the device or both on the host")
+    _check(ctx, _lib().af_rhs_vjp(ctx, ptrs, optrs, dev))
+    del keep
+    return out
+
+
+def af_adjoint_step(ctx, dt, lam, out=None, device: bool = True, recorded: bool = False):
+    """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one step from the current state with time step dt
+    (a float or a one-element CUDA float64 tensor).  recorded=True (AF_ADJ_RECORDED): the caller has
+    checked, from the forward step's counters, that no limiter acted in its last stage."""
+    ptrs, dev, keep = _marshal_in(ctx, lam)
+    out, optrs, odev = _outputs(ctx, out, device)
+    if dev != odev:
+        raise ValueError("lam and out must both be on the device or both on the host")
+    flags = AF_ADJ_RECORDED if recorded else 0
+    if _is_tensor(dt) and dt.is_cuda:
+        rc = _lib().af_adjoint_step(ctx, dt.data_ptr(), 1, ptrs, optrs, dev, flags)
+    else:
+        v = C.c_double(float(dt))
+        rc = _lib().af_adjoint_step(ctx, C.cast(C.byref(v), C.c_void_p), 0, ptrs, optrs, dev, flags)
+    _check(ctx, rc)
+    del keep
     return out
 
 

@@ -1,0 +1,640 @@
+// af_adjoint.cu -- transpose of the linearised semi-discrete operator L(U)
+// (Sec. 2.1-2.3): out = (dL/dU)^T v, in gather form (every output element is
+// written by exactly one thread, no atomics, deterministic).
+//
+// L is the high-order AF right-hand side: LLF flux-vector splitting on the
+// point values (alpha = the largest spectral radius on the 5-point line,
+// differentiated through the point that attains it), central divergence and
+// Powell source for the points, Simpson fluxes and the 3x3 Powell source for
+// the cell averages, and the bi-parabola cell-centre values.  On smooth data
+// with the shock sensor off (kappa = 0) and every positivity limiter inactive,
+// a limited forward-Euler stage is exactly U + dt L(U), so its transpose is
+// v + dt (dL/dU)^T v.
+//
+// Three kernels, after the forward point-data pass at the linearisation state;
+// each runs one grid slice (blockIdx.z) per DoF class, so that every thread
+// does the work of one DoF with compile-time class and direction:
+//   A1 (per output): line coefficients alpha, d(out)/d(alpha) and the argmax,
+//      divergence and its cotangent of each point output; for each cell the
+//      weighted node divergences and their cotangents.
+//   A2 (per DoF): gathers, over every output whose stencil contains the DoF,
+//      the cotangents of the DoF's fluxes F1, F2, spectral radii, Psi and B,
+//      then applies the transposed pointwise Jacobians.  Cell centres too.
+//   A3 (per DoF): distributes the cell-centre cotangents to the DoFs of the
+//      bi-parabola, [36 Ubar - 4 (faces) - (corners)] / 16, and applies the
+//      Runge-Kutta combination of the reverse sweep (AfAdjEpi).
+//
+// A 5-point FVS line of an output with index s holds points with indices
+// s-1, s, s+1 along its direction (after the periodic wrap or the outflow
+// mirror), so a DoF is gathered from the outputs at offsets -1, 0, +1.
+#include "../../include/af.h"
+#include "af_internal.h"
+#include "af_math.cuh"
+#include "af_device.cuh"
+
+using namespace afm;
+
+namespace {
+
+// A1 slots (per index point)
+enum {
+  A_CX_AL = 0, A_CX_GA, A_CX_AM, A_CY_AL, A_CY_GA, A_CY_AM, A_C_DB, A_C_DBB,   // corner
+  A_X_AL, A_X_GA, A_X_AM, A_X_DB, A_X_DBB,                                    // x-face
+  A_Y_AL, A_Y_GA, A_Y_AM, A_Y_DB, A_Y_DBB,                                    // y-face
+  A_WD = 18,      // 9: W_lm div_lm of the cell
+  A_DIVB = 27,    // 9: cotangent of div_lm
+  A_N = 36
+};
+enum { CX = 1, CY = 2, CC = 3, CZ = 4 };   // point classes (x-face, y-face, corner, cell centre)
+
+struct PI {
+  int c, i, j;
+};
+__device__ __forceinline__ bool same(const PI &a, const PI &b) { return a.c == b.c && a.i == b.i && a.j == b.j; }
+
+__constant__ double kCoefF[5] = {1.0, -4.0, 0.0, 4.0, -1.0};   // (F0 - F4) + 4 (F3 - F1)
+__constant__ double kCoefU[5] = {1.0, -4.0, 6.0, -4.0, 1.0};   // (U0 + U4) - 4 (U1 + U3) + 6 U2
+// coefficient of the node value at position l (0,1,2) in the derivative at node lp
+__constant__ double kD1[3][3] = {{-3.0, 4.0, -1.0}, {-1.0, 0.0, 1.0}, {1.0, -4.0, 3.0}};
+
+struct Vec4 {
+  const double *p[4];
+};
+struct OVec4 {
+  double *p[4];
+};
+
+__device__ __forceinline__ bool valid_point(const AfGrid &g, const PI &q) {
+  if (q.c == CZ) return q.i >= 0 && q.i < g.nx && q.j >= 0 && q.j < g.ny;
+  return q.i >= 0 && q.i < g.ex[q.c] && q.j >= 0 && q.j < g.ey[q.c];
+}
+
+// value of component k of point q's state (cell centres from the centre array)
+__device__ __forceinline__ double uval(const AfDev &d, const AfGrid &g, const PI &q, int k) {
+  if (q.c == CZ) return __ldg(d.uc + (size_t)k * g.nxa * g.nya + (size_t)q.j * g.nxa + q.i);
+  return __ldg(d.us[q.c] + (size_t)k * g.ex[q.c] * g.ey[q.c] + (size_t)q.j * g.ex[q.c] + q.i);
+}
+__device__ __forceinline__ double pval(const AfDev &d, const AfGrid &g, const PI &q, int slot) {
+  return __ldg(d.pd[q.c] + (size_t)slot * g.nxa * g.nya + (size_t)q.j * g.nxa + q.i);
+}
+__device__ __forceinline__ double vval(const Vec4 &v, const AfGrid &g, int c, int i, int j, int k) {
+  return __ldg(v.p[c] + (size_t)k * g.ex[c] * g.ey[c] + (size_t)j * g.ex[c] + i);
+}
+__device__ __forceinline__ double aval(const double *a, const AfGrid &g, int i, int j, int slot) {
+  return __ldg(a + (size_t)slot * g.nxa * g.nya + (size_t)j * g.nxa + i);
+}
+
+// The 5-point FVS line of point output (cls, i, j) in direction dir, exactly
+// as the forward point-update kernel builds it.
+__device__ __forceinline__ void fvs_line(const AfGrid &g, int cls, int dir, int i, int j, PI *P) {
+  const int im = mface(i - 1, g.nx, g.bc), ip = mface(i + 1, g.nx, g.bc);
+  const int jm = mface(j - 1, g.ny, g.bc), jp = mface(j + 1, g.ny, g.bc);
+  const int ci0 = mcell(i - 1, g.nx, g.bc), ci1 = mcell(i, g.nx, g.bc);
+  const int cj0 = mcell(j - 1, g.ny, g.bc), cj1 = mcell(j, g.ny, g.bc);
+  if (cls == CC && dir == 0) {
+    P[0] = {CC, im, j}; P[1] = {CY, ci0, j}; P[2] = {CC, i, j}; P[3] = {CY, ci1, j}; P[4] = {CC, ip, j};
+  } else if (cls == CC) {
+    P[0] = {CC, i, jm}; P[1] = {CX, i, cj0}; P[2] = {CC, i, j}; P[3] = {CX, i, cj1}; P[4] = {CC, i, jp};
+  } else if (cls == CX) {
+    P[0] = {CX, im, j}; P[1] = {CZ, ci0, j}; P[2] = {CX, i, j}; P[3] = {CZ, ci1, j}; P[4] = {CX, ip, j};
+  } else {
+    P[0] = {CY, i, jm}; P[1] = {CZ, i, cj0}; P[2] = {CY, i, j}; P[3] = {CZ, i, cj1}; P[4] = {CY, i, jp};
+  }
+}
+
+// the 3x3 Simpson nodes of cell (i, j): N[l + 3 m]
+__device__ __forceinline__ void cell_nodes(const AfGrid &g, int i, int j, PI *N) {
+  const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
+  N[0] = {CC, i, j};  N[1] = {CY, i, j};  N[2] = {CC, ip, j};
+  N[3] = {CX, i, j};  N[4] = {CZ, i, j};  N[5] = {CX, ip, j};
+  N[6] = {CC, i, jp}; N[7] = {CY, i, jp}; N[8] = {CC, ip, jp};
+}
+
+// Psi = (0, B, v, v.B) of point q, component k >= 1
+__device__ __forceinline__ double psi(const AfDev &d, const AfGrid &g, const PI &q, int k) {
+  if (k <= 3) return uval(d, g, q, 3 + k);
+  return pval(d, g, q, QP_V1 + (k - 4));
+}
+
+// ---------------------------------------------------------------------------
+// A1
+// ---------------------------------------------------------------------------
+template <int CLS, int DIR>
+__device__ __forceinline__ void line_coefs(const AfDev &d, const AfGrid &g, const Vec4 &v, int i, int j, double rh,
+                                           double *a, int sal, int sga, int sam) {
+  PI P[5];
+  fvs_line(g, CLS, DIR, i, j, P);
+  constexpr int qsr = DIR == 0 ? QP_SR1 : QP_SR2;
+  double al = pval(d, g, P[0], qsr);
+  int am = 0;
+#pragma unroll
+  for (int p = 1; p < 5; ++p) {
+    const double s = pval(d, g, P[p], qsr);
+    if (s > al) { al = s; am = p; }
+  }
+  double ga = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double up = fma(6.0, uval(d, g, P[2], k),
+                          fma(-4.0, uval(d, g, P[1], k) + uval(d, g, P[3], k), uval(d, g, P[0], k) + uval(d, g, P[4], k)));
+    ga = fma(vval(v, g, CLS, i, j, k), up, ga);
+  }
+  const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
+  a[sal * PS + o] = al;
+  a[sga * PS + o] = -0.5 * rh * ga;
+  a[sam * PS + o] = (double)am;
+}
+
+// (B_l(P0) - B_l(P4)) + 4 (B_l(P3) - B_l(P1)) along the FVS line
+template <int CLS, int DIR>
+__device__ __forceinline__ double line_db(const AfDev &d, const AfGrid &g, int i, int j) {
+  PI P[5];
+  fvs_line(g, CLS, DIR, i, j, P);
+  constexpr int k = 4 + DIR;
+  return fma(4.0, uval(d, g, P[3], k) - uval(d, g, P[1], k), uval(d, g, P[0], k) - uval(d, g, P[4], k));
+}
+
+template <int CLS>
+__device__ __forceinline__ void point_div(const AfDev &d, const AfGrid &g, const Vec4 &v, int i, int j, double rdx,
+                                          double rdy, double *a, int sdb, int sdbb) {
+  double divB;
+  if (CLS == CC) {
+    divB = fma(line_db<CC, 0>(d, g, i, j), 0.5 * rdx, line_db<CC, 1>(d, g, i, j) * (0.5 * rdy));
+  } else if (CLS == CX) {
+    const int jp = mface(j + 1, g.ny, g.bc);
+    const PI lo = {CC, i, j}, hi = {CC, i, jp};
+    divB = fma(line_db<CX, 0>(d, g, i, j), 0.5 * rdx, (uval(d, g, hi, 5) - uval(d, g, lo, 5)) * rdy);
+  } else {
+    const int ip = mface(i + 1, g.nx, g.bc);
+    const PI lo = {CC, i, j}, hi = {CC, ip, j};
+    divB = fma(uval(d, g, hi, 4) - uval(d, g, lo, 4), rdx, line_db<CY, 1>(d, g, i, j) * (0.5 * rdy));
+  }
+  const PI q = {CLS, i, j};
+  double dbb = 0.0;
+  if (g.src_point_on)
+#pragma unroll
+    for (int k = 1; k < 8; ++k) dbb = fma(-vval(v, g, CLS, i, j, k), psi(d, g, q, k), dbb);
+  const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
+  a[sdb * PS + o] = divB;
+  a[sdbb * PS + o] = dbb;
+}
+
+__device__ __forceinline__ void cell_terms(const AfDev &d, const AfGrid &g, const Vec4 &v, int i, int j, double rdx,
+                                           double rdy, double *a) {
+  PI N[9];
+  cell_nodes(g, i, j, N);
+  constexpr double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+  const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
+  double vc[8];
+#pragma unroll
+  for (int k = 1; k < 8; ++k) vc[k] = vval(v, g, 0, i, j, k);
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double dx1 = 0.0, dy2 = 0.0;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        dx1 = fma(kD1[l][t], uval(d, g, N[t + 3 * m], 4), dx1);
+        dy2 = fma(kD1[m][t], uval(d, g, N[l + 3 * t], 5), dy2);
+      }
+      const double W = w1[l] * w1[m];
+      const double div = fma(dx1, rdx, dy2 * rdy);
+      double dd = 0.0;
+      if (g.src_cell_on)
+#pragma unroll
+        for (int k = 1; k < 8; ++k) dd = fma(-vc[k], psi(d, g, N[l + 3 * m], k), dd);
+      a[(A_WD + l + 3 * m) * PS + o] = g.src_cell_on ? W * div : 0.0;
+      a[(A_DIVB + l + 3 * m) * PS + o] = W * dd;
+    }
+}
+
+// blockIdx.z: 0 corners, 1 x-faces, 2 y-faces, 3 cells
+__global__ void __launch_bounds__(128) k_adj1(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                              const __grid_constant__ Vec4 v, double *a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+  switch (blockIdx.z) {
+    case 0:
+      if (i < g.ex[CC] && j < g.ey[CC]) {
+        line_coefs<CC, 0>(d, g, v, i, j, rdx, a, A_CX_AL, A_CX_GA, A_CX_AM);
+        line_coefs<CC, 1>(d, g, v, i, j, rdy, a, A_CY_AL, A_CY_GA, A_CY_AM);
+        point_div<CC>(d, g, v, i, j, rdx, rdy, a, A_C_DB, A_C_DBB);
+      }
+      break;
+    case 1:
+      if (i < g.ex[CX] && j < g.ey[CX]) {
+        line_coefs<CX, 0>(d, g, v, i, j, rdx, a, A_X_AL, A_X_GA, A_X_AM);
+        point_div<CX>(d, g, v, i, j, rdx, rdy, a, A_X_DB, A_X_DBB);
+      }
+      break;
+    case 2:
+      if (i < g.ex[CY] && j < g.ey[CY]) {
+        line_coefs<CY, 1>(d, g, v, i, j, rdy, a, A_Y_AL, A_Y_GA, A_Y_AM);
+        point_div<CY>(d, g, v, i, j, rdx, rdy, a, A_Y_DB, A_Y_DBB);
+      }
+      break;
+    default:
+      if (i < g.nx && j < g.ny) cell_terms(d, g, v, i, j, rdx, rdy, a);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A2
+// ---------------------------------------------------------------------------
+struct Acc {
+  double F[2][8];   // cotangents of F1, F2
+  double sr[2];     // of varrho_1, varrho_2
+  double ps[8];     // of Psi
+  double B[2];      // of B1, B2 through the divergence stencils
+  double U[8];      // direct cotangent of U (the alpha (U0 + U4 - ...) terms)
+};
+
+// output of class oc at offset o (-1..1) from q along dir, mapped into range;
+// false when it does not exist
+__device__ __forceinline__ bool candidate(const AfGrid &g, int oc, int dir, const PI &q, int o, PI &s) {
+  int i = q.i, j = q.j;
+  if (dir == 0) i += o; else j += o;
+  if (g.bc == 0) {
+    i = wrapi(wrapi(i, g.nx), g.nx);
+    j = wrapi(wrapi(j, g.ny), g.ny);
+  }
+  s = {oc, i, j};
+  return s.i >= 0 && s.j >= 0 && s.i < g.ex[oc] && s.j < g.ey[oc];
+}
+
+// FVS lines of outputs of class OC in direction DIR that contain q
+template <int OC, int DIR>
+__device__ __forceinline__ void gather_lines(const AfDev &d, const AfGrid &g, const Vec4 &v, const double *a,
+                                             const PI &q, double rh, Acc &acc) {
+  constexpr int sal = OC == CC ? (DIR == 0 ? A_CX_AL : A_CY_AL) : (OC == CX ? A_X_AL : A_Y_AL);
+  constexpr int sdbb = OC == CC ? A_C_DBB : (OC == CX ? A_X_DBB : A_Y_DBB);
+  const double c = 0.5 * rh;
+#pragma unroll
+  for (int o = -1; o <= 1; ++o) {
+    PI s;
+    if (!candidate(g, OC, DIR, q, o, s)) continue;
+    PI P[5];
+    fvs_line(g, OC, DIR, s.i, s.j, P);
+    double cf = 0.0, cu = 0.0, csr = 0.0;
+    int hits = 0;
+    const int am = (int)aval(a, g, s.i, s.j, sal + 2);
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+      if (same(P[p], q)) {
+        cf += kCoefF[p];
+        cu += kCoefU[p];
+        if (p == am) csr += 1.0;
+        ++hits;
+      }
+    if (!hits) continue;
+    const double al = aval(a, g, s.i, s.j, sal);
+    if (csr != 0.0) acc.sr[DIR] = fma(csr, aval(a, g, s.i, s.j, sal + 1), acc.sr[DIR]);
+    acc.B[DIR] = fma(cf * c, aval(a, g, s.i, s.j, sdbb), acc.B[DIR]);
+    const double cual = cu * al;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double gk = -c * vval(v, g, OC, s.i, s.j, k);
+      if (k != 4 + DIR) acc.F[DIR][k] = fma(cf, gk, acc.F[DIR][k]);
+      acc.U[k] = fma(cual, gk, acc.U[k]);
+    }
+  }
+}
+
+// central differences: y-face outputs (F1 between corners, along x) and
+// x-face outputs (F2 between corners, along y) that use corner q
+template <int DIR>
+__device__ __forceinline__ void gather_central(const AfGrid &g, const Vec4 &v, const double *a, const PI &q,
+                                               double rh, Acc &acc) {
+  constexpr int oc = DIR == 0 ? CY : CX;
+  constexpr int sdbb = DIR == 0 ? A_Y_DBB : A_X_DBB;
+#pragma unroll
+  for (int o = -1; o <= 0; ++o) {
+    PI s;
+    if (!candidate(g, oc, DIR, q, o, s)) continue;
+    PI lo = {CC, s.i, s.j}, hi = lo;
+    if (DIR == 0) hi.i = mface(s.i + 1, g.nx, g.bc); else hi.j = mface(s.j + 1, g.ny, g.bc);
+    const double sgn = (same(hi, q) ? 1.0 : 0.0) - (same(lo, q) ? 1.0 : 0.0);
+    if (sgn == 0.0) continue;
+    // L -= (F(hi) - F(lo))/h, divB += (B(hi) - B(lo))/h
+    acc.B[DIR] = fma(sgn * rh, aval(a, g, s.i, s.j, sdbb), acc.B[DIR]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k != 4 + DIR) acc.F[DIR][k] = fma(-sgn * rh, vval(v, g, oc, s.i, s.j, k), acc.F[DIR][k]);
+  }
+}
+
+// cotangent of the Simpson flux of x-face (fi, fj) (DIR 0) or y-face (DIR 1),
+// times wgt, added to acc: sum over the cells that use it as their
+// left/lower (+) or right/upper (-) face
+template <int DIR>
+__device__ __forceinline__ void face_cot(const AfGrid &g, const Vec4 &v, int fi, int fj, double wgt, double rh,
+                                         Acc &acc) {
+#pragma unroll
+  for (int o = -1; o <= 0; ++o) {
+    int ci = fi, cj = fj;
+    if (DIR == 0) ci += o; else cj += o;
+    if (g.bc == 0) { ci = wrapi(ci, g.nx); cj = wrapi(cj, g.ny); }
+    if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny) continue;
+    double sgn = 0.0;
+    if (DIR == 0) {
+      if (ci == fi && cj == fj) sgn += 1.0;                                   // left face of the cell
+      if (mface(ci + 1, g.nx, g.bc) == fi && cj == fj) sgn -= 1.0;            // right face
+    } else {
+      if (ci == fi && cj == fj) sgn += 1.0;
+      if (mface(cj + 1, g.ny, g.bc) == fj && ci == fi) sgn -= 1.0;
+    }
+    if (sgn == 0.0) continue;
+    const double w = sgn * wgt * rh;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (k != 4 + DIR) acc.F[DIR][k] = fma(w, vval(v, g, 0, ci, cj, k), acc.F[DIR][k]);
+  }
+}
+
+template <int C>
+__device__ __forceinline__ void gather_simpson(const AfGrid &g, const Vec4 &v, const PI &q, double rdx, double rdy,
+                                               Acc &acc) {
+  if constexpr (C == CX) face_cot<0>(g, v, q.i, q.j, 4.0 / 6.0, rdx, acc);   // middle node of its own face
+  if constexpr (C == CY) face_cot<1>(g, v, q.i, q.j, 4.0 / 6.0, rdy, acc);
+  if constexpr (C == CC) {
+    // corner: end node (weight 1/6) of the x-faces below/above and the y-faces left/right
+#pragma unroll
+    for (int o = -1; o <= 0; ++o) {
+      PI s;
+      if (candidate(g, CX, 1, q, o, s)) {
+        const int hj = mface(s.j + 1, g.ny, g.bc);
+        const double wgt = (s.j == q.j ? 1.0 : 0.0) + (hj == q.j ? 1.0 : 0.0);
+        if (wgt != 0.0) face_cot<0>(g, v, s.i, s.j, wgt / 6.0, rdx, acc);
+      }
+      if (candidate(g, CY, 0, q, o, s)) {
+        const int hi = mface(s.i + 1, g.nx, g.bc);
+        const double wgt = (s.i == q.i ? 1.0 : 0.0) + (hi == q.i ? 1.0 : 0.0);
+        if (wgt != 0.0) face_cot<1>(g, v, s.i, s.j, wgt / 6.0, rdy, acc);
+      }
+    }
+  }
+}
+
+// the 3x3 source nodes of the cells that have q as a node (node n = l + 3 m)
+template <int C>
+__device__ __forceinline__ void gather_source(const AfGrid &g, const Vec4 &v, const double *a, const PI &q, double rdx,
+                                              double rdy, Acc &acc) {
+  constexpr int na = C == CC ? 4 : (C == CZ ? 1 : 2);
+  constexpr int nodes[4] = {C == CC ? 0 : (C == CX ? 3 : (C == CY ? 1 : 4)), C == CC ? 2 : (C == CX ? 5 : 7),
+                            6, 8};
+#pragma unroll
+  for (int b = 0; b <= 1; ++b)
+#pragma unroll
+    for (int aa = 0; aa <= 1; ++aa) {
+      if (C == CZ && (aa || b)) continue;
+      if (C == CX && b) continue;    // x-face (i, j) is a node of cells (i-1, j) and (i, j) only
+      if (C == CY && aa) continue;
+      int ci = q.i - aa, cj = q.j - b;
+      if (g.bc == 0) { ci = wrapi(ci, g.nx); cj = wrapi(cj, g.ny); }
+      if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny) continue;
+      PI N[9];
+      cell_nodes(g, ci, cj, N);
+#pragma unroll
+      for (int t = 0; t < na; ++t) {
+        const int n = nodes[t];
+        if (!same(N[n], q)) continue;
+        const int l = n % 3, m = n / 3;
+        const double wd = aval(a, g, ci, cj, A_WD + n);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) acc.ps[k] = fma(-wd, vval(v, g, 0, ci, cj, k), acc.ps[k]);
+        double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          s1 = fma(aval(a, g, ci, cj, A_DIVB + r + 3 * m), kD1[r][l], s1);   // d/dx at node (r, m) uses node (l, m)
+          s2 = fma(aval(a, g, ci, cj, A_DIVB + l + 3 * r), kD1[r][m], s2);   // d/dy at node (l, r) uses node (l, m)
+        }
+        acc.B[0] = fma(s1, rdx, acc.B[0]);
+        acc.B[1] = fma(s2, rdy, acc.B[1]);
+      }
+    }
+}
+
+// Transpose of the point data of one state: F1, F2, varrho_1, varrho_2 and
+// Psi = (0, B, v, v.B) as computed by the forward point-data pass.
+__device__ __forceinline__ void pointwise_transpose(const double *U, const AfGrid &g, const Acc &acc, double *out) {
+  const double rho = U[0], r = rcp(rho);
+  const double m1 = U[1], m2 = U[2], m3 = U[3];
+  const double v1 = m1 * r, v2 = m2 * r, v3 = m3 * r;
+  const double B1 = U[4], B2 = U[5], B3 = U[6], E = U[7];
+  const double BB = B1 * B1 + B2 * B2 + B3 * B3;
+  const double mv = m1 * v1 + m2 * v2 + m3 * v3;
+  const double p = g.gm1 * (E - 0.5 * (mv + BB));
+  const double pt = p + 0.5 * BB;
+  const double vB = v1 * B1 + v2 * B2 + v3 * B3;
+  const double Ept = E + pt;
+  double mb1 = 0, mb2 = 0, mb3 = 0, Bb1 = acc.B[0], Bb2 = acc.B[1], Bb3 = 0, Eb = 0;
+  double vb1 = 0, vb2 = 0, vb3 = 0, ptb = 0, vBb = 0, Eptb = 0, pb = 0;
+  const double *F1 = acc.F[0], *F2 = acc.F[1];
+  // F1
+  mb1 += F1[0];
+  mb1 += F1[1] * v1; vb1 += F1[1] * m1; ptb += F1[1]; Bb1 -= 2.0 * B1 * F1[1];
+  mb1 += F1[2] * v2; vb2 += F1[2] * m1; Bb1 -= F1[2] * B2; Bb2 -= F1[2] * B1;
+  mb1 += F1[3] * v3; vb3 += F1[3] * m1; Bb1 -= F1[3] * B3; Bb3 -= F1[3] * B1;
+  vb1 += F1[5] * B2; Bb2 += F1[5] * v1; Bb1 -= F1[5] * v2; vb2 -= F1[5] * B1;
+  vb1 += F1[6] * B3; Bb3 += F1[6] * v1; Bb1 -= F1[6] * v3; vb3 -= F1[6] * B1;
+  Eptb += F1[7] * v1; vb1 += F1[7] * Ept; Bb1 -= F1[7] * vB; vBb -= F1[7] * B1;
+  // F2
+  mb2 += F2[0];
+  mb1 += F2[1] * v2; vb2 += F2[1] * m1; Bb1 -= F2[1] * B2; Bb2 -= F2[1] * B1;
+  mb2 += F2[2] * v2; vb2 += F2[2] * m2; ptb += F2[2]; Bb2 -= 2.0 * B2 * F2[2];
+  mb2 += F2[3] * v3; vb3 += F2[3] * m2; Bb2 -= F2[3] * B3; Bb3 -= F2[3] * B2;
+  Bb1 += F2[4] * v2; vb2 += F2[4] * B1; vb1 -= F2[4] * B2; Bb2 -= F2[4] * v1;
+  vb2 += F2[6] * B3; Bb3 += F2[6] * v2; Bb2 -= F2[6] * v3; vb3 -= F2[6] * B2;
+  Eptb += F2[7] * v2; vb2 += F2[7] * Ept; Bb2 -= F2[7] * vB; vBb -= F2[7] * B2;
+  // Psi
+  Bb1 += acc.ps[1]; Bb2 += acc.ps[2]; Bb3 += acc.ps[3];
+  vb1 += acc.ps[4]; vb2 += acc.ps[5]; vb3 += acc.ps[6]; vBb += acc.ps[7];
+  // spectral radii varrho_l = |v_l| + c_{f,l}
+  const double c2 = g.gamma * p * r;
+  const double a = BB * r + c2;
+  const double k4 = 4.0 * c2 * r;
+  double ab = 0, c2b = 0, k4b = 0;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const double srb = acc.sr[l];
+    if (srb == 0.0) continue;
+    const double vl = l == 0 ? v1 : v2, Bl = l == 0 ? B1 : B2;
+    if (l == 0) vb1 += vl >= 0.0 ? srb : -srb; else vb2 += vl >= 0.0 ? srb : -srb;
+    double dd = a * a - k4 * Bl * Bl;
+    if (dd < 0.0) dd = 0.0;
+    const double sd = dsqrt(dd);
+    const double s = 0.5 * sd + 0.5 * a;
+    const double cf = dsqrt(s);
+    const double sb = cf > 0.0 ? 0.5 * srb * rcp(cf) : 0.0;
+    ab += 0.5 * sb;
+    const double ddb = sd > 0.0 ? 0.25 * sb * rcp(sd) : 0.0;
+    ab += 2.0 * a * ddb;
+    k4b -= Bl * Bl * ddb;
+    if (l == 0) Bb1 -= 2.0 * k4 * Bl * ddb; else Bb2 -= 2.0 * k4 * Bl * ddb;
+  }
+  double rbar = 0.0;
+  c2b += 4.0 * r * k4b;
+  rbar += 4.0 * c2 * k4b;
+  Bb1 += 2.0 * B1 * r * ab; Bb2 += 2.0 * B2 * r * ab; Bb3 += 2.0 * B3 * r * ab;
+  rbar += BB * ab;
+  c2b += ab;
+  pb += g.gamma * r * c2b;
+  rbar += g.gamma * p * c2b;
+  // Ept = E + pt; vB = v.B; pt = p + BB/2; p = (gamma-1)(E - (mv + BB)/2)
+  Eb += Eptb; ptb += Eptb;
+  vb1 += vBb * B1; vb2 += vBb * B2; vb3 += vBb * B3;
+  Bb1 += vBb * v1; Bb2 += vBb * v2; Bb3 += vBb * v3;
+  pb += ptb;
+  Bb1 += ptb * B1; Bb2 += ptb * B2; Bb3 += ptb * B3;
+  Eb += g.gm1 * pb;
+  const double mvb = -0.5 * g.gm1 * pb;
+  Bb1 -= g.gm1 * pb * B1; Bb2 -= g.gm1 * pb * B2; Bb3 -= g.gm1 * pb * B3;
+  mb1 += mvb * v1; mb2 += mvb * v2; mb3 += mvb * v3;
+  vb1 += mvb * m1; vb2 += mvb * m2; vb3 += mvb * m3;
+  // v_k = m_k r, r = 1/rho
+  mb1 += vb1 * r; mb2 += vb2 * r; mb3 += vb3 * r;
+  rbar += vb1 * m1 + vb2 * m2 + vb3 * m3;
+  out[0] = -r * r * rbar + acc.U[0];
+  out[1] = mb1 + acc.U[1];
+  out[2] = mb2 + acc.U[2];
+  out[3] = mb3 + acc.U[3];
+  out[4] = Bb1 + acc.U[4];
+  out[5] = Bb2 + acc.U[5];
+  out[6] = Bb3 + acc.U[6];
+  out[7] = Eb + acc.U[7];
+}
+
+template <int C>
+__device__ __forceinline__ void adj_point(const AfDev &d, const AfGrid &g, const Vec4 &v, const double *a, int i,
+                                          int j, double rdx, double rdy, double *const *tp, double *zc) {
+  const PI q = {C, i, j};
+  if (!valid_point(g, q)) return;
+  Acc acc;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc.F[0][k] = acc.F[1][k] = acc.ps[k] = acc.U[k] = 0.0;
+  acc.sr[0] = acc.sr[1] = acc.B[0] = acc.B[1] = 0.0;
+  if (C == CC || C == CY) gather_lines<CC, 0>(d, g, v, a, q, rdx, acc);
+  if (C == CC || C == CX) gather_lines<CC, 1>(d, g, v, a, q, rdy, acc);
+  if (C == CX || C == CZ) gather_lines<CX, 0>(d, g, v, a, q, rdx, acc);
+  if (C == CY || C == CZ) gather_lines<CY, 1>(d, g, v, a, q, rdy, acc);
+  if (C == CC) {
+    gather_central<0>(g, v, a, q, rdx, acc);
+    gather_central<1>(g, v, a, q, rdy, acc);
+  }
+  gather_simpson<C>(g, v, q, rdx, rdy, acc);
+  gather_source<C>(g, v, a, q, rdx, rdy, acc);
+  if (C != CZ && g.src_point_on) {   // own Powell term -(div B) Psi
+    constexpr int sdb = C == CC ? A_C_DB : (C == CX ? A_X_DB : A_Y_DB);
+    const double divB = aval(a, g, i, j, sdb);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) acc.ps[k] = fma(-divB, vval(v, g, C, i, j, k), acc.ps[k]);
+  }
+  double U[8], o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) U[k] = uval(d, g, q, k);
+  pointwise_transpose(U, g, acc, o);
+  if (C == CZ) {
+    const size_t PS = (size_t)g.nxa * g.nya, oo = (size_t)j * g.nxa + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) zc[k * PS + oo] = o[k];
+  } else {
+    const size_t cs = (size_t)g.ex[C] * g.ey[C], oo = (size_t)j * g.ex[C] + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tp[C][k * cs + oo] = o[k];
+  }
+}
+
+// blockIdx.z: 0 x-faces, 1 y-faces, 2 corners, 3 cell centres
+__global__ void __launch_bounds__(128) k_adj2(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                              const __grid_constant__ Vec4 v, const double *a,
+                                              const __grid_constant__ OVec4 tp, double *zc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+  switch (blockIdx.z) {
+    case 0: adj_point<CX>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
+    case 1: adj_point<CY>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
+    case 2: adj_point<CC>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
+    default: adj_point<CZ>(d, g, v, a, i, j, rdx, rdy, tp.p, zc);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A3: U_c = 2.25 Ubar - 0.25 (faces) - 0.0625 (corners), then the epilogue
+// ---------------------------------------------------------------------------
+template <int C>
+__device__ __forceinline__ void adj_final(const AfGrid &g, const double *zc, const double *const *tp,
+                                          const AfAdjEpi &e, int i, int j) {
+  if (i >= g.ex[C] || j >= g.ey[C]) return;
+  const size_t PS = (size_t)g.nxa * g.nya;
+  const size_t cs = (size_t)g.ex[C] * g.ey[C], oo = (size_t)j * g.ex[C] + i;
+  double T[8];
+  if (C == 0) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T[k] = 2.25 * __ldg(zc + k * PS + (size_t)j * g.nxa + i);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T[k] = __ldg(tp[C] + k * cs + oo);
+    const PI q = {C, i, j};
+#pragma unroll
+    for (int b = 0; b <= 1; ++b)
+#pragma unroll
+      for (int aa = 0; aa <= 1; ++aa) {
+        if (C == 1 && b) continue;
+        if (C == 2 && aa) continue;
+        int ci = i - aa, cj = j - b;
+        if (g.bc == 0) { ci = wrapi(ci, g.nx); cj = wrapi(cj, g.ny); }
+        if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny) continue;
+        PI N[9];
+        cell_nodes(g, ci, cj, N);
+        double wgt = 0.0;
+#pragma unroll
+        for (int n = 0; n < 9; ++n)
+          if (n != 4 && same(N[n], q)) wgt += (n == 1 || n == 3 || n == 5 || n == 7) ? -0.25 : -0.0625;
+        if (wgt == 0.0) continue;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) T[k] = fma(wgt, __ldg(zc + k * PS + (size_t)cj * g.nxa + ci), T[k]);
+      }
+  }
+  const double bs = e.dt ? e.b * __ldg(e.dt) : e.b;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const size_t o = k * cs + oo;
+    const double vk = e.v[C][o];
+    double r = fma(bs, T[k], e.a * vk);
+    if (e.z1[0]) r = fma(e.c, e.z1[C][o], r);
+    if (e.out2[0]) e.out2[C][o] = fma(e.f, e.z2[C][o], e.e * vk);
+    e.out1[C][o] = r;
+  }
+}
+
+// blockIdx.z: DoF class 0..3
+__global__ void __launch_bounds__(128) k_adj3(const __grid_constant__ AfGrid g, const double *zc,
+                                              const __grid_constant__ OVec4 tp, const __grid_constant__ AfAdjEpi e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  switch (blockIdx.z) {
+    case 0: adj_final<0>(g, zc, tp.p, e, i, j); break;
+    case 1: adj_final<1>(g, zc, tp.p, e, i, j); break;
+    case 2: adj_final<2>(g, zc, tp.p, e, i, j); break;
+    default: adj_final<3>(g, zc, tp.p, e, i, j);
+  }
+}
+
+inline dim3 grid3(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 3) / 4, 4); }
+
+}  // namespace
+
+int af_adj_nslots() { return A_N; }
+
+void af_launch_vjp(const AfDev &d, const AfGrid &g, const AfAdjEpi &e, double *a, double *zc, double *const *tpart,
+                   cudaStream_t s) {
+  Vec4 vv;
+  OVec4 tp;
+  for (int c = 0; c < 4; ++c) {
+    vv.p[c] = e.v[c];
+    tp.p[c] = tpart[c];
+  }
+  k_adj1<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a);
+  k_adj2<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a, tp, zc);
+  k_adj3<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(g, zc, tp, e);
+}

@@ -26,6 +26,11 @@ struct af_ctx {
   AfStatus *st;
   AfDev dev;              // work-array pointers (state pointers set per stage)
   // per-kernel event timing (af_timing)
+  // adjoint workspace (allocated on first use)
+  double *adj;            // af_adj_nslots() + 8 arrays per index point
+  double *abuf;           // 6 state-sized buffers: lambda copies, VJP scratch, extra stage output
+  double *adj_pd;         // two more point-data sets (point data and centre values of U^(0), U^(1))
+  unsigned long long *cnt_pin;   // pinned host copy of the counters before / after a recomputation
   int timing;
   int nev;                // event pairs in use
   int evcap;
@@ -358,6 +363,191 @@ int af_stage(af_ctx *c, int s, const double *dt, int on_device) {
   return stage_impl(c, s, 0);
 }
 
+// ---- adjoint ---------------------------------------------------------------
+namespace {
+// doubles of one point-data set per index point: pd classes 0..4 and the centre values
+constexpr size_t kPdLen = AF_NQA + 4 * AF_NQP + 8;
+
+int ensure_adjoint(af_ctx *c) {
+  if (c->adj) return AF_OK;
+  const size_t PS = (size_t)c->g.nxa * c->g.nya;
+  if (cudaMalloc(&c->adj, sizeof(double) * PS * (af_adj_nslots() + 8)) != cudaSuccess ||
+      cudaMalloc(&c->abuf, sizeof(double) * 6 * c->state_len) != cudaSuccess ||
+      cudaMalloc(&c->adj_pd, sizeof(double) * 2 * kPdLen * PS) != cudaSuccess ||
+      cudaMallocHost(&c->cnt_pin, sizeof(unsigned long long) * 32) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AF_ENOMEM, "adjoint workspace");
+  }
+  return AF_OK;
+}
+double *abuf(af_ctx *c, int k) { return c->abuf + (size_t)k * c->state_len; }
+void class_ptrs(af_ctx *c, double *base, double **out) {
+  for (int cls = 0; cls < 4; ++cls) out[cls] = base + c->class_off[cls];
+}
+// point data (pd[0..4], uc) of set 0 or 1 (adjoint workspace) or 2 (the context's own)
+void bind_pd(af_ctx *c, int set) {
+  const size_t PS = (size_t)c->g.nxa * c->g.nya;
+  double *w = set == 2 ? c->work : c->adj_pd + (size_t)set * kPdLen * PS;
+  c->dev.pd[0] = w; w += AF_NQA * PS;
+  for (int k = 1; k <= 4; ++k) { c->dev.pd[k] = w; w += AF_NQP * PS; }
+  c->dev.uc = w;
+}
+// Transposed operator at the state in buffer `buf` whose point data is in set
+// `set`: the last kernel writes e.out1 (and e.out2), see AfAdjEpi.
+void vjp_at(af_ctx *c, int buf, int set, const AfAdjEpi &e) {
+  bind_pd(c, set);
+  bind_states(c, buf, buf, buf);
+  double *tp[4];
+  class_ptrs(c, abuf(c, 1), tp);
+  const size_t PS = (size_t)c->g.nxa * c->g.nya;
+  af_launch_vjp(c->dev, c->g, e, c->adj, c->adj + (size_t)af_adj_nslots() * PS, tp, c->stream);
+  bind_pd(c, 2);
+}
+AfAdjEpi epi(const double *const v[4], double *const out1[4], double a, double b, const double *dt) {
+  AfAdjEpi e;
+  memset(&e, 0, sizeof(e));
+  for (int cls = 0; cls < 4; ++cls) {
+    e.v[cls] = v[cls];
+    e.out1[cls] = out1[cls];
+  }
+  e.a = a;
+  e.b = b;
+  e.dt = dt;
+  return e;
+}
+int copy_in_buf(af_ctx *c, double *dst, const double *const U[4], int on_device) {
+  for (int cls = 0; cls < 4; ++cls) {
+    if (!U[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+    CK(cudaMemcpyAsync(dst + c->class_off[cls], U[cls], cls_len(c, cls) * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+       "copy in");
+  }
+  return AF_OK;
+}
+int copy_out_buf(af_ctx *c, const double *src, double *const U[4], int on_device) {
+  for (int cls = 0; cls < 4; ++cls) {
+    if (!U[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+    CK(cudaMemcpyAsync(U[cls], src + c->class_off[cls], cls_len(c, cls) * sizeof(double),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream),
+       "copy out");
+  }
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return AF_OK;
+}
+}  // namespace
+
+int af_rhs_vjp(af_ctx *c, const double *const v[4], double *const out[4], int on_device) {
+  if (!c || !v || !out) return AF_EINVAL;
+  for (int cls = 0; cls < 4; ++cls)
+    if (!v[cls] || !out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+  CK(cudaSetDevice(c->device), "set device");
+  int rc = ensure_adjoint(c);
+  if (rc) return rc;
+  const double *vp[4];
+  double *op[4], *in_buf[4], *out_buf[4];
+  class_ptrs(c, abuf(c, 0), in_buf);
+  class_ptrs(c, abuf(c, 2), out_buf);
+  if (!on_device) {
+    rc = copy_in_buf(c, abuf(c, 0), v, 0);
+    if (rc) return rc;
+  }
+  for (int cls = 0; cls < 4; ++cls) {
+    vp[cls] = on_device ? v[cls] : in_buf[cls];
+    op[cls] = on_device ? out[cls] : out_buf[cls];
+  }
+  bind_states(c, c->cur, c->cur, c->cur);
+  af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  vjp_at(c, c->cur, 2, epi(vp, op, 0.0, 1.0, nullptr));
+  CK(cudaGetLastError(), "vjp launch");
+  c->next_stage = 0;
+  if (on_device) return AF_OK;
+  return copy_out_buf(c, abuf(c, 2), out, 0);
+}
+
+int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double *const lam_in[4],
+                    double *const lam_out[4], int on_device, int flags) {
+  if (!c || !dt || !lam_in || !lam_out) return AF_EINVAL;
+  for (int cls = 0; cls < 4; ++cls)
+    if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+  if (flags & ~AF_ADJ_RECORDED) return fail(c, AF_EINVAL, "unknown flags %d", flags);
+  if (c->g.kappa != 0.0)
+    return fail(c, AF_EINVAL, "af_adjoint_step differentiates the scheme with the shock sensor off (kappa = 0)");
+  CK(cudaSetDevice(c->device), "set device");
+  int rc = ensure_adjoint(c);
+  if (!rc) rc = set_dt(c, dt, dt_on_device);
+  if (rc) return rc;
+  const double *dtp = &c->sc->dt;
+  const size_t cnt_bytes = sizeof(unsigned long long) * 16;
+  CK(cudaMemcpyAsync(c->cnt_pin, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
+  // recompute U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1) with the recorded dt, each
+  // stage's point data in its own set; then the point data of U2 (or stage 2
+  // into a spare buffer, to see whether a limiter acts there)
+  const int n = c->cur, b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+  bind_pd(c, 0);
+  bind_states(c, n, n, b1);
+  run_stage(c, RK_A[0], RK_B[0], 0);
+  bind_pd(c, 1);
+  bind_states(c, n, b1, b2);
+  run_stage(c, RK_A[1], RK_B[1], 0);
+  bind_pd(c, 2);
+  if (flags & AF_ADJ_RECORDED) {
+    bind_states(c, b2, b2, b2);
+    af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  } else {
+    bind_states(c, n, b2, b1);
+    for (int cls = 0; cls < 4; ++cls) c->dev.uo[cls] = abuf(c, 5) + c->class_off[cls];
+    run_stage(c, RK_A[2], RK_B[2], 0);
+  }
+  CK(cudaGetLastError(), "stage recompute");
+  CK(cudaMemcpyAsync(c->cnt_pin + 16, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
+  // reverse of U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1), U3 = 1/3 U0 + 2/3 FE(U2), FE(U) = U + dt L(U):
+  //   L2 = 2/3 (L3 + dt T(U2) L3),  L1 = 1/4 (L2 + dt T(U1) L2),  W = 3/4 L2 + 1/3 L3,
+  //   L0 = L1 + dt T(U0) L1 + W,    T(U) = (dL/dU)^T
+  double *L3b[4], *L2[4], *L1[4], *W[4], *L0b[4];
+  class_ptrs(c, abuf(c, 0), L3b);
+  class_ptrs(c, abuf(c, 2), L2);
+  class_ptrs(c, abuf(c, 3), L1);
+  class_ptrs(c, abuf(c, 4), W);
+  class_ptrs(c, abuf(c, 0), L0b);
+  if (!on_device) {
+    rc = copy_in_buf(c, abuf(c, 0), lam_in, 0);
+    if (rc) return rc;
+  }
+  const double *L3[4];
+  double *L0[4];
+  for (int cls = 0; cls < 4; ++cls) {
+    L3[cls] = on_device ? lam_in[cls] : L3b[cls];
+    L0[cls] = on_device ? lam_out[cls] : L0b[cls];
+  }
+  vjp_at(c, b2, 2, epi(L3, L2, 2.0 / 3.0, 2.0 / 3.0, dtp));
+  AfAdjEpi e1 = epi(L2, L1, 0.25, 0.25, dtp);
+  for (int cls = 0; cls < 4; ++cls) {
+    e1.out2[cls] = W[cls];
+    e1.z2[cls] = L3[cls];
+  }
+  e1.e = 0.75;
+  e1.f = 1.0 / 3.0;
+  vjp_at(c, b1, 1, e1);
+  AfAdjEpi e0 = epi(L1, L0, 1.0, 1.0, dtp);
+  for (int cls = 0; cls < 4; ++cls) e0.z1[cls] = W[cls];
+  e0.c = 1.0;
+  vjp_at(c, n, 0, e0);
+  CK(cudaGetLastError(), "adjoint launch");
+  c->next_stage = 0;
+  if (!on_device) {
+    rc = copy_out_buf(c, abuf(c, 0), lam_out, 0);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
+  const int lim[] = {ST_SRC_LIMITED, ST_LAMBDA_LT1, ST_FACE_THETA_LT1, ST_SHRINK, ST_POINT_LIMITED, ST_CENTER_LIMITED,
+                     ST_NONADMISSIBLE};
+  for (int k : lim)
+    if (c->cnt_pin[16 + k] != c->cnt_pin[k])
+      return fail(c, AF_EINVAL, "af_adjoint_step: a limiter was active in this step (counter %d); the transpose "
+                  "covers the branch on which every limiter is inactive", k);
+  return AF_OK;
+}
+
 int af_get_stage(af_ctx *c, double *const U[4], int on_device) {
   if (!c || !U) return AF_EINVAL;
   CK(cudaSetDevice(c->device), "set device");
@@ -432,6 +622,10 @@ void af_destroy(af_ctx *c) {
   if (c->work) cudaFree(c->work);
   if (c->sc) cudaFree(c->sc);
   if (c->st) cudaFree(c->st);
+  if (c->adj) cudaFree(c->adj);
+  if (c->adj_pd) cudaFree(c->adj_pd);
+  if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
+  if (c->abuf) cudaFree(c->abuf);
   for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);
   free(c->ev);
   free(c->evk);

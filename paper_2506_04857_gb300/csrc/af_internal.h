@@ -91,4 +91,23 @@ float af_run_fp64_probe(cudaStream_t s, double *flops);
 void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
                      double a, double b, int reduce_dt, cudaStream_t s);
 int af_batch_occupancy(int pass, dim3 block);   // resident blocks per SM
+// adjoint (af_adjoint.cu).  With T = (dL/dU)^T v at the state bound in d (after
+// the point-data pass on it), the last kernel writes
+//   out1 = a v + b s T + c z1   and, when out2[0] is not NULL,   out2 = e v + f z2,
+// s = *dt (device pointer) or 1 when dt is NULL; every array in state layout
+// (four class pointers).  out1 may alias v; nothing else may alias.
+struct AfAdjEpi {
+  const double *v[4];
+  double *out1[4];
+  const double *z1[4];
+  double *out2[4];
+  const double *z2[4];
+  double a, b, c, e, f;
+  const double *dt;
+};
+// a: af_adj_nslots() work arrays, zc: 8 work arrays (per index point),
+// tpart: a state-sized scratch buffer (four class pointers)
+int af_adj_nslots();
+void af_launch_vjp(const AfDev &d, const AfGrid &g, const AfAdjEpi &e, double *a, double *zc, double *const *tpart,
+                   cudaStream_t s);
 void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s);
