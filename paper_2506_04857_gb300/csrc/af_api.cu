@@ -76,6 +76,8 @@ void refresh_grid(af_ctx *c) {
   g.ex[3] = fx;    g.ey[3] = fy;
   g.dx = (c->x1 - c->x0) / c->nx;
   g.dy = (c->y1 - c->y0) / c->ny;
+  g.rdx = 1.0 / g.dx;
+  g.rdy = 1.0 / g.dy;
   g.gamma = c->gamma;
   g.gm1 = c->gamma - 1.0;
   g.kappa = c->prm.kappa;

@@ -81,6 +81,8 @@ void fill_grid(af_batch *b, int r) {
   g.ex[3] = g.nxa; g.ey[3] = g.nya;
   g.dx = (b->x1[r] - b->x0[r]) / g.nx;
   g.dy = (b->y1[r] - b->y0[r]) / g.ny;
+  g.rdx = 1.0 / g.dx;
+  g.rdy = 1.0 / g.dy;
   g.gamma = b->gamma[r];
   g.gm1 = b->gamma[r] - 1.0;
   g.kappa = b->prm[r].kappa;

@@ -37,6 +37,7 @@ struct AfGrid {
   int nxa, nya;            // extents of the per-index work arrays
   int ex[4], ey[4];        // extents of the four DoF classes
   double dx, dy;
+  double rdx, rdy;         // 1/dx, 1/dy (formed once on the host)
   double gamma, gm1;
   double kappa, cfl;
   double c13;              // 1e-13 / (gamma - 1)

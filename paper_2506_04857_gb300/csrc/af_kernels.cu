@@ -411,10 +411,10 @@ __device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, 
   const double b2r = nb.B[1];
   // Reading: the printed stencils are used literally (fluxes between values
   // half a cell apart are still divided by dx or dy; divergence over 2 dx, 2 dy).
-  const double divB = (b1r - b1l) / (2.0 * g.dx) + (b2r - b2l) / (2.0 * g.dy);
+  const double divB = (b1r - b1l) * (0.5 * g.rdx) + (b2r - b2l) * (0.5 * g.rdy);
   const double Ps[8] = {0.0, me.B[0], me.B[1], me.B[2], me.v[0], me.v[1], me.v[2], me.vB};
   double UL[8];
-  const double cxf = dt / g.dx, cyf = dt / g.dy;
+  const double cxf = dt * g.rdx, cyf = dt * g.rdy;
   for (int k = 0; k < 8; ++k) {
     double u = me.U[k] - cxf * (Fxr[k] - Fxl[k]) - cyf * (Fyr[k] - Fyl[k]);
     if (g.src_point_on) u -= dt * divB * Ps[k];
@@ -457,7 +457,7 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   const double sx = pte + ptw, sy = ptn + pts;
   phi[0] = ddiv(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
   phi[1] = ddiv(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
-  const double hx = 0.5 / g.dx, hy = 0.5 / g.dy;
+  const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double divv = fma(A(e, c_j, QA_V1) - A(w, c_j, QA_V1), hx, (A(c_i, n, QA_V2) - A(c_i, s, QA_V2)) * hy);
   const double curl = fma(A(e, c_j, QA_V2) - A(w, c_j, QA_V2), hx, -(A(c_i, n, QA_V1) - A(c_i, s, QA_V1)) * hy);
   const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
@@ -471,8 +471,8 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
                                          int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const double dt = mode == 1 ? 1.0 : d.sc->dt;
-  const double cx = 0.5 * dt / g.dx, cy = 0.5 * dt / g.dy;   // the FVS lines carry a factor 1/2
-  const double cxc = dt / g.dx, cyc = dt / g.dy;             // central differences
+  const double cx = 0.5 * dt * g.rdx, cy = 0.5 * dt * g.rdy;   // the FVS lines carry a factor 1/2
+  const double cxc = dt * g.rdx, cyc = dt * g.rdy;             // central differences
   int nlim = 0, nshr = 0, nbad = 0;
   if (i < g.nxa && j < g.nya) {
     const int im = mface(i - 1, g.nx, g.bc), ip = mface(i + 1, g.nx, g.bc);
@@ -492,17 +492,17 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
         const PP Py[5] = {pref(d, g, 3, i, jm), pref(d, g, 1, i, cj0), me, pref(d, g, 1, i, cj1), pref(d, g, 3, i, jp)};
         fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx);
         fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy);
-        divB = fma(dBx, 0.5 / g.dx, dBy * (0.5 / g.dy));
+        divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
       } else if (cls == 1) {
         const PP Px[5] = {pref(d, g, 1, im, j), pref(d, g, 4, ci0, j), me, pref(d, g, 4, ci1, j), pref(d, g, 1, ip, j)};
         fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx);
         central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
-        divB = fma(dBx, 0.5 / g.dx, dBy / g.dy);
+        divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
       } else {
         central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
         const PP Py[5] = {pref(d, g, 2, i, jm), pref(d, g, 4, i, cj0), me, pref(d, g, 4, i, cj1), pref(d, g, 2, i, jp)};
         fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy);
-        divB = fma(dBx, 1.0 / g.dx, dBy * (0.5 / g.dy));
+        divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
       }
       if (g.src_point_on) {
         // -(div B) Psi(U), Psi = (0, B, v, v.B)
@@ -765,7 +765,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
       b2[0][0] = C(i, j, 5); b2[1][0] = Y(i, j, 5); b2[2][0] = C(ip, j, 5);
       b2[0][1] = X(i, j, 5); b2[1][1] = ZU(i, j, 5); b2[2][1] = X(ip, j, 5);
       b2[0][2] = C(i, jp, 5); b2[1][2] = Y(i, jp, 5); b2[2][2] = C(ip, jp, 5);
-      const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
+      const double rdx = g.rdx, rdy = g.rdy;
       const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
       double wd[3][3];
 #pragma unroll
@@ -813,7 +813,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
     const SV Ub = sview(d.us[0], g, 0);
     const WV A = wview(d.pd[0], g);
     const WV FX = wview(d.fx, g), FY = wview(d.fy, g);
-    const double cxf = dt / g.dx, cyf = dt / g.dy;
+    const double cxf = dt * g.rdx, cyf = dt * g.rdy;
     double *uo = d.uo[0];
     const size_t cs0 = (size_t)g.nx * g.ny, o0 = (size_t)j * g.nx + i;
     if (mode == 1) {
@@ -822,13 +822,13 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
       for (int k = 0; k < 8; ++k) {
         const double fl = FX(i, j, QF_G + k), fr = FX(ip, j, QF_G + k);
         const double fd = FY(i, j, QF_G + k), fu = FY(i, jp, QF_G + k);
-        uo[k * cs0 + o0] = -(fr - fl) / g.dx - (fu - fd) / g.dy - S[k];
+        uo[k * cs0 + o0] = -(fr - fl) * g.rdx - (fu - fd) * g.rdy - S[k];
       }
     } else {
       // S^LLF = (central div Bbar) Psi(Ubar)
       const int ie = mcell(i + 1, g.nx, g.bc), iw = mcell(i - 1, g.nx, g.bc);
       const int jn = mcell(j + 1, g.ny, g.bc), js = mcell(j - 1, g.ny, g.bc);
-      const double divBb = fma(Ub(ie, j, 4) - Ub(iw, j, 4), 0.5 / g.dx, (Ub(i, jn, 5) - Ub(i, js, 5)) * (0.5 / g.dy));
+      const double divBb = fma(Ub(ie, j, 4) - Ub(iw, j, 4), 0.5 * g.rdx, (Ub(i, jn, 5) - Ub(i, js, 5)) * (0.5 * g.rdy));
       double Ubar[8];
       load8(Ub, i, j, Ubar);
       const double vb1 = A(i, j, QA_V1), vb2 = A(i, j, QA_V2), vb3 = A(i, j, QA_V3);
@@ -872,8 +872,8 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         }
         // Lemma 3.1 CFL condition (diagnostic count only)
         {
-          const double lhs = dt * ((FX(i, j, QF_AL) + FX(ip, j, QF_AL)) / g.dx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) / g.dy +
-                                   fabs(divBb) / A(i, j, QA_SRHO));
+          const double lhs = dt * ((FX(i, j, QF_AL) + FX(ip, j, QF_AL)) * g.rdx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) * g.rdy +
+                                   ddiv(absd(divBb), A(i, j, QA_SRHO)));
           ncfl += lhs > 1.0 + 1e-12;
         }
         const double dtts = dt * tsc;
@@ -964,8 +964,8 @@ __device__ __forceinline__ void limited_value(const AfDev &d, const AfGrid &g, i
                                               double *out) {
   const WV FX = wview(d.fx, g), FY = wview(d.fy, g), L1 = wview(d.lim1, g);
   const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
-  const double cxf = dt / g.dx, cyf = dt / g.dy;
-  const bool ones = th[0] == 1.0 && th[1] == 1.0 && th[2] == 1.0 && th[3] == 1.0;
+  const double cxf = dt * g.rdx, cyf = dt * g.rdy;
+  const bool ones = is_one(th[0]) && is_one(th[1]) && is_one(th[2]) && is_one(th[3]);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
     const double gl = FX(i, j, QF_G + k), gr = FX(ip, j, QF_G + k), gd = FY(i, j, QF_G + k), gu = FY(i, jp, QF_G + k);
@@ -994,20 +994,20 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     const size_t o = (size_t)j * g.nxa + i;
     d.thx[o] = th[0];
     d.thy[o] = th[2];
-    nface += (th[0] < 1.0) + (th[2] < 1.0);
+    nface += lt_one(th[0]) + lt_one(th[2]);
     if (g.bc == 1 && i == g.nx - 1) {
       d.thx[o + 1] = th[1];
-      nface += th[1] < 1.0;
+      nface += lt_one(th[1]);
     }
     if (g.bc == 1 && j == g.ny - 1) {
       d.thy[o + g.nxa] = th[3];
-      nface += th[3] < 1.0;
+      nface += lt_one(th[3]);
     }
     double fe[8];
     limited_value(d, g, i, j, th, dt, fe);
     bool ok = fe[0] > 0.0 && qform(fe, 0.0) > 0.0;   // rho > 0 and p > 0
 #pragma unroll
-    for (int k = 0; k < 8; ++k) ok = ok && isfinite(fe[k]);
+    for (int k = 0; k < 8; ++k) ok = ok && finite_bits(fe[k]);
     if (!ok) {
       const int slot = atomicAdd(&d.st->nrepair, 1);
       if (slot < AF_MAX_REPAIR) d.st->repair[slot] = j * g.nx + i;

@@ -97,6 +97,12 @@ __device__ __forceinline__ double minnn(double a, double b) {
 __device__ __forceinline__ double absd(double a) {
   return __hiloint2double(__double2hiint(a) & 0x7fffffff, __double2loint(a));
 }
+// finite (neither infinite nor NaN), from the exponent bits
+__device__ __forceinline__ bool finite_bits(double a) { return ((hi32(a) >> 20) & 0x7ffu) != 0x7ffu; }
+// a == 1.0 and a < 1.0 for non-negative a, +NaN included (bit-pattern comparisons on the
+// integer pipe)
+__device__ __forceinline__ bool is_one(double a) { return __double_as_longlong(a) == 0x3ff0000000000000LL; }
+__device__ __forceinline__ bool lt_one(double a) { return __double_as_longlong(a) < 0x3ff0000000000000LL; }
 // a < 0 for non-NaN a (negative zero is not negative)
 __device__ __forceinline__ bool isneg(double a) {
   long long x = __double_as_longlong(a);

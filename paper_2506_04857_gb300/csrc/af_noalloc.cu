@@ -83,6 +83,8 @@ extern "C" int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, d
   g.ex[3] = nxa; g.ey[3] = nya;
   g.dx = (x1 - x0) / nx;
   g.dy = (y1 - y0) / ny;
+  g.rdx = 1.0 / g.dx;
+  g.rdy = 1.0 / g.dy;
   g.gamma = gamma;
   g.gm1 = gamma - 1.0;
   g.kappa = 0.0;
