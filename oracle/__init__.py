@@ -92,6 +92,7 @@ def _lib(count: bool = False, complex_step: bool = False):
             lib.or_scaling_limiter.argtypes = [dp, dp, C.c_double, dp, dp]
             lib.or_sensor_phi.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
             lib.or_sensor.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp, dp]
+            lib.or_divb.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp]
             if key == "cs":
                 lib.or_step_cs.restype = C.c_int
                 lib.or_step_cs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double]
@@ -173,6 +174,16 @@ def sensor(pb, U, **kw):
     ty = np.zeros((ext[2][1], ext[2][0]))
     _lib().or_sensor(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(tx), _dp(ty))
     return tx, ty
+
+
+def divb(pb, U, **kw):
+    """(divB_1, divB_2): the two discrete divergence measures of Example 4.4 (node
+    divergences of the bi-parabola; Simpson edge integral of B.n per cell)."""
+    P = params_for(pb, **kw)
+    U = _check(U, pb.nx, pb.ny, pb.bc)
+    out = np.zeros(2)
+    _lib().or_divb(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(out))
+    return float(out[0]), float(out[1])
 
 
 def flux(l: int, U, gamma: float) -> np.ndarray:

@@ -1257,6 +1257,60 @@ int or_sensor(const or_params *p, int nx, int ny, const double *const *U, double
   return 0;
 }
 
+// Example 4.4: the two discrete divergence measures of the state U.
+//   out[0] = sum_ij sum_{l,m} |(div B)_ij^{l,m}| w_l w_m dx dy, the node
+//            divergences of eq. (semi_av_src) (centre node: the limited
+//            centre value, as in the stage);
+//   out[1] = sum_ij |closed integral of B.n over the boundary of cell ij|,
+//            each edge by Simpson's rule: dy/6 ([R] - [L]) + dx/6 ([T] - [B]),
+//            [.] = corner + 4 face centre + corner of B1 (R, L) or B2 (T, B).
+//            Reading: the text defines this measure as the edge integral of
+//            B.n; the printed sum carries a factor dx dy instead of the edge
+//            lengths, which is the same only up to a factor h on a square
+//            mesh, so the edge integral is taken.
+int or_divb(const or_params *p, int nx, int ny, const double *const *U, double *out) {
+  Ctx C;
+  make_ctx(p, nx, ny, C);
+  State S;
+  load_state(C, U, S);
+  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, S.c[cls], cls);
+  Work W;
+  long long st[ST_NSTATS] = {0};
+  compute_centers(C, S, W, st);
+  const real w[3] = {real(1.0) / real(6.0), real(2.0) / real(3.0), real(1.0) / real(6.0)};
+  real d1 = real(0.0), d2 = real(0.0);
+  for (int j = 0; j < C.ny; ++j)
+    for (int i = 0; i < C.nx; ++i) {
+      // node values N[l][m] of B1 (q = 4) and B2 (q = 5), l along x, m along y
+      real b[2][3][3];
+      for (int q = 0; q < 2; ++q) {
+        const int k = 4 + q;
+        b[q][0][0] = S.c[3].at(C, k, i, j);     b[q][1][0] = S.c[2].at(C, k, i, j);     b[q][2][0] = S.c[3].at(C, k, i + 1, j);
+        b[q][0][1] = S.c[1].at(C, k, i, j);     b[q][1][1] = W.Uc.at(C, k, i, j);      b[q][2][1] = S.c[1].at(C, k, i + 1, j);
+        b[q][0][2] = S.c[3].at(C, k, i, j + 1); b[q][1][2] = S.c[2].at(C, k, i, j + 1); b[q][2][2] = S.c[3].at(C, k, i + 1, j + 1);
+      }
+      for (int l = 0; l < 3; ++l)
+        for (int m = 0; m < 3; ++m) {
+          real dB1, dB2;
+          if (l == 0) dB1 = Dminus(b[0][0][m], b[0][1][m], b[0][2][m], C.dx);
+          else if (l == 1) dB1 = Dcen(b[0][0][m], b[0][2][m], C.dx);
+          else dB1 = Dplus(b[0][0][m], b[0][1][m], b[0][2][m], C.dx);
+          if (m == 0) dB2 = Dminus(b[1][l][0], b[1][l][1], b[1][l][2], C.dy);
+          else if (m == 1) dB2 = Dcen(b[1][l][0], b[1][l][2], C.dy);
+          else dB2 = Dplus(b[1][l][0], b[1][l][1], b[1][l][2], C.dy);
+          d1 = d1 + fabs(dB1 + dB2) * w[l] * w[m] * real(C.dx * C.dy);
+        }
+      const real right = b[0][2][0] + real(4.0) * b[0][2][1] + b[0][2][2];
+      const real left = b[0][0][0] + real(4.0) * b[0][0][1] + b[0][0][2];
+      const real top = b[1][0][2] + real(4.0) * b[1][1][2] + b[1][2][2];
+      const real bottom = b[1][0][0] + real(4.0) * b[1][1][0] + b[1][2][0];
+      d2 = d2 + fabs(real(C.dy) * (right - left) + real(C.dx) * (top - bottom)) / real(6.0);
+    }
+  out[0] = val(d1);
+  out[1] = val(d2);
+  return 0;
+}
+
 // ---- pointwise pieces, exported for the unit tests --------------------------
 void or_flux(int l, const double *U, double gamma, double *F) {
   real u[8];

@@ -542,3 +542,45 @@ def test_fvs_alpha_uses_five_point_stencil():
     expect = -0.5 * ((-3 * F(Ub) + 4 * F(uc) - F(pert)) + 2 * alpha * delta) / pb.dx
     got = L[1][:, g0, f0 - 1]
     assert np.allclose(got, expect, rtol=1e-11, atol=1e-11 * np.abs(expect).max())
+
+
+# ---------------------------------------------------------------------------
+# Example 4.4: the two discrete divergence measures (oracle.divb)
+# ---------------------------------------------------------------------------
+def _b_field_problem(B1, B2, nx=12, ny=10, box=(1.0, 2.0, 0.0, 1.0)):
+    """rho = 1, v = 0, p = 1 and the given magnetic field on an outflow box."""
+    def prim(x, y):
+        z = np.zeros(np.shape(x))
+        return (z + 1.0, z, z, z, B1(x, y) + z, B2(x, y) + z, z, z + 1.0)
+    return ai.Problem("bfield", nx, ny, box[0], box[1], box[2], box[3], ai.OUTFLOW, 5.0 / 3.0, prim)
+
+
+def test_divb_closed_forms():
+    # a uniform field has no divergence (the averages carry quadrature rounding,
+    # the point values are exact)
+    pb = _b_field_problem(lambda x, y: 0.3 + 0 * x, lambda x, y: -0.7 + 0 * x)
+    d1, d2 = oracle.divb(pb, ai.dofs(pb))
+    assert d1 <= 1e-13 and d2 == 0.0
+    # B = (x^2, 0) on [1,2]x[0,1]: the bi-parabola and Simpson's rule are exact, and
+    # div B = 2x > 0, so both measures equal its integral (x1^2 - x0^2)(y1 - y0) = 3
+    pb = _b_field_problem(lambda x, y: x * x, lambda x, y: 0 * x)
+    d1, d2 = oracle.divb(pb, ai.dofs(pb))
+    assert d1 == pytest.approx(3.0, rel=1e-13)
+    assert d2 == pytest.approx(3.0, rel=1e-13)
+    # B = (0, y^2) on [0,1]x[1,3] (the y-direction paths): (y1^2 - y0^2)(x1 - x0) = 8
+    pb = _b_field_problem(lambda x, y: 0 * x, lambda x, y: y * y, nx=9, ny=14, box=(0.0, 1.0, 1.0, 3.0))
+    d1, d2 = oracle.divb(pb, ai.dofs(pb))
+    assert d1 == pytest.approx(8.0, rel=1e-13)
+    assert d2 == pytest.approx(8.0, rel=1e-13)
+    # B = ((x - 3/2)^2, 0): div B = 2x - 3 changes sign at a face (nx = 12), both
+    # quadratures are exact on each cell, and the measures are the integral of |div B|, 1/2
+    pb = _b_field_problem(lambda x, y: (x - 1.5) ** 2, lambda x, y: 0 * x)
+    d1, d2 = oracle.divb(pb, ai.dofs(pb))
+    assert d1 == pytest.approx(0.5, rel=1e-12)
+    assert d2 == pytest.approx(0.5, rel=1e-12)
+    # a divergence-free field in Q2, B = curl(x^2 y^2 e_z) = (2 x^2 y, -2 x y^2), on a
+    # mesh with dx != dy: both measures vanish up to rounding
+    pb = _b_field_problem(lambda x, y: 2 * x * x * y, lambda x, y: -2 * x * y * y)
+    assert pb.dx != pb.dy
+    d1, d2 = oracle.divb(pb, ai.dofs(pb))
+    assert d1 <= 1e-12 and d2 <= 1e-12
