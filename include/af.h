@@ -144,6 +144,20 @@ int af_stage(af_ctx *ctx, int s, const double *dt, int on_device);
  * stage 1, U^{n+1} after stage 2 (same layout as the state). */
 int af_get_stage(af_ctx *ctx, double *const U[4], int on_device);
 
+/* The two discrete divergence measures of Example 4.4 for the current state,
+ * written to out[0], out[1] (host or device pointer):
+ *   out[0] = sum over cells and the 3x3 nodes of eq. (semi_av_src) of
+ *            |(div B)^{l,m}| w_l w_m dx dy (centre node: the limited centre
+ *            value, as in a stage);
+ *   out[1] = sum over cells of |Simpson edge integral of B.n| =
+ *            |dy/6 ([R] - [L]) + dx/6 ([T] - [B])|, [.] = corner + 4 face
+ *            centre + corner of B1 (right, left faces) or B2 (top, bottom).
+ * Reading: the text defines the second measure as the edge integral of B.n;
+ * the printed sum carries dx dy instead of the edge lengths.  The sums are
+ * formed in a fixed order (deterministic).  With on_device = 0 the call
+ * synchronises the stream.  Allocates a small workspace on first use. */
+int af_divb(af_ctx *ctx, double *out, int on_device);
+
 /* Discrete adjoint (not in the paper; differentiates its scheme).
  * af_rhs_vjp: out = (dL/dU)^T v for the semi-discrete operator of af_rhs at
  * the current state (alpha = max varrho on each FVS line differentiated

@@ -82,6 +82,7 @@ def _lib():
             lib.af_step.argtypes = [vp, vp, C.c_int]
             lib.af_get_stage.argtypes = [vp, pp, C.c_int]
             lib.af_rhs_vjp.argtypes = [vp, pp, pp, C.c_int]
+            lib.af_divb.argtypes = [vp, vp, C.c_int]
             lib.af_adjoint_step.argtypes = [vp, vp, C.c_int, pp, pp, C.c_int, C.c_int]
             lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
             lib.af_last_error.argtypes = [vp]
@@ -237,6 +238,17 @@ def af_get_stage(ctx, out=None, device: bool = True):
     out, ptrs, dev = _outputs(ctx, out, device)
     _check(ctx, _lib().af_get_stage(ctx, ptrs, dev))
     return out
+
+
+def af_divb(ctx, out=None):
+    """(divB_1, divB_2) of the current state (Example 4.4); with out (a 2-element CUDA float64
+    tensor) the values are written on the device without synchronising."""
+    if out is not None:
+        _check(ctx, _lib().af_divb(ctx, out.data_ptr(), 1))
+        return out
+    res = (C.c_double * 2)()
+    _check(ctx, _lib().af_divb(ctx, C.cast(res, C.c_void_p), 0))
+    return float(res[0]), float(res[1])
 
 
 def af_rhs_vjp(ctx, v, out=None, device: bool = True):
@@ -522,6 +534,9 @@ class Solver:
 
     def dt(self, out=None):
         return af_dt(self.ctx, out)
+
+    def divb(self, out=None):
+        return af_divb(self.ctx, out)
 
     def sensor(self, device: bool = True):
         return af_sensor(self.ctx, device)

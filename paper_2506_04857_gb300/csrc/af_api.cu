@@ -31,6 +31,7 @@ struct af_ctx {
   double *abuf;           // 6 state-sized buffers: lambda copies, VJP scratch, extra stage output
   double *adj_pd;         // two more point-data sets (point data and centre values of U^(0), U^(1))
   unsigned long long *cnt_pin;   // pinned host copy of the counters before / after a recomputation
+  double *divb_buf;       // divergence measures: 2 per block, then the 2 results (allocated on first use)
   int timing;
   int nev;                // event pairs in use
   int evcap;
@@ -550,6 +551,25 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   return AF_OK;
 }
 
+int af_divb(af_ctx *c, double *out, int on_device) {
+  if (!c || !out) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  const int nb = af_divb_nblocks(c->g);
+  if (!c->divb_buf && cudaMalloc(&c->divb_buf, sizeof(double) * (2 * (size_t)nb + 2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AF_ENOMEM, "divergence workspace");
+  }
+  bind_states(c, c->cur, c->cur, c->cur);
+  double *res = c->divb_buf + 2 * (size_t)nb;
+  af_launch_divb(c->dev, c->g, c->divb_buf, res, c->stream);
+  CK(cudaGetLastError(), "divergence launch");
+  CK(cudaMemcpyAsync(out, res, 2 * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream),
+     "copy divergence");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return AF_OK;
+}
+
 int af_get_stage(af_ctx *c, double *const U[4], int on_device) {
   if (!c || !U) return AF_EINVAL;
   CK(cudaSetDevice(c->device), "set device");
@@ -626,6 +646,7 @@ void af_destroy(af_ctx *c) {
   if (c->st) cudaFree(c->st);
   if (c->adj) cudaFree(c->adj);
   if (c->adj_pd) cudaFree(c->adj_pd);
+  if (c->divb_buf) cudaFree(c->divb_buf);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);
   for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);

@@ -88,6 +88,10 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
+// divergence measures of Example 4.4 of the state bound in d.us into out[2]
+// (device); partials: 2 * af_divb_nblocks(g) doubles
+int af_divb_nblocks(const AfGrid &g);
+void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s);
 // persistent batched launch of one pass (AF_K_* id) over a (run, i0, j0) tile list
 void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
                      double a, double b, int reduce_dt, cudaStream_t s);

@@ -223,6 +223,25 @@ __device__ __forceinline__ void load8(const SV &v, int i, int j, double *U) {
   for (int k = 0; k < 8; ++k) U[k] = v(i, j, k);
 }
 
+// Sec. 2.1 centre value [36 Ubar - 4 (faces) - (corners)] / 16 of cell (i, j),
+// limited toward the cell average A by Remark 3.2; true when the limiter acted.
+__device__ __forceinline__ bool centre_value(const AfDev &d, const AfGrid &g, int i, int j, const double *A,
+                                             double *uc) {
+  const SV X = sview(d.us[1], g, 1), Y = sview(d.us[2], g, 2), C = sview(d.us[3], g, 3);
+  const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double faces = (X(i, j, k) + X(ip, j, k)) + (Y(i, j, k) + Y(i, jp, k));
+    const double corners = (C(i, j, k) + C(ip, j, k)) + (C(i, jp, k) + C(ip, jp, k));
+    uc[k] = fma(2.25, A[k], fma(-0.25, faces, -0.0625 * corners));
+  }
+  if (clear_of_floor(uc, g)) return false;
+  double out[8], t1, t2;
+  scaling_limiter(uc, A, g.gm1, out, t1, t2);
+  for (int k = 0; k < 8; ++k) uc[k] = out[k];
+  return t1 < 1.0 || t2 < 1.0;
+}
+
 __device__ __forceinline__ void b_pointdata(const AfDev &d, const AfGrid &g, const int i, const int j, int reduce_dt) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
@@ -245,23 +264,8 @@ __device__ __forceinline__ void b_pointdata(const AfDev &d, const AfGrid &g, con
       point_data(A, g, d.pd[0] + o, PS, true, s1, s2);
       m1 = maxnn(m1, s1);
       m2 = maxnn(m2, s2);
-      // Sec. 2.1 centre value: [36 Ubar - 4 (faces) - (corners)] / 16
-      const SV X = sview(d.us[1], g, 1), Y = sview(d.us[2], g, 2), C = sview(d.us[3], g, 3);
-      const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
       double uc[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const double faces = (X(i, j, k) + X(ip, j, k)) + (Y(i, j, k) + Y(i, jp, k));
-        const double corners = (C(i, j, k) + C(ip, j, k)) + (C(i, jp, k) + C(ip, jp, k));
-        uc[k] = fma(2.25, A[k], fma(-0.25, faces, -0.0625 * corners));
-      }
-      // Remark 3.2: limit toward the cell average
-      if (!clear_of_floor(uc, g)) {
-        double out[8], t1, t2;
-        scaling_limiter(uc, A, g.gm1, out, t1, t2);
-        clim = (t1 < 1.0 || t2 < 1.0);
-        for (int k = 0; k < 8; ++k) uc[k] = out[k];
-      }
+      clim = centre_value(d, g, i, j, A, uc);
 #pragma unroll
       for (int k = 0; k < 8; ++k) d.uc[k * PS + o] = uc[k];
       point_data(uc, g, d.pd[4] + o, PS, false, s1, s2);
@@ -1196,6 +1200,94 @@ __global__ void k_fp64_probe(double *out, int iters) {
   out[t] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// ---------------------------------------------------------------------------
+// Example 4.4: the discrete divergence measures of the state bound in d.us.
+// Per cell: s1 = sum_{l,m} |(div B)^{l,m}| w_l w_m dx dy over the 3x3 nodes of
+// eq. (semi_av_src) (centre node: the limited centre value, as in a stage) and
+// s2 = |dy/6 ([R] - [L]) + dx/6 ([T] - [B])|, the Simpson edge integral of B.n
+// ([.] = corner + 4 face centre + corner).  Each block reduces its cells in a
+// fixed order and writes one partial pair; a one-block pass sums the partials
+// in a fixed order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_divb(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                              double *partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  double s1 = 0.0, s2 = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const SV Ub = sview(d.us[0], g, 0), X = sview(d.us[1], g, 1), Y = sview(d.us[2], g, 2), C = sview(d.us[3], g, 3);
+    const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
+    double A[8], uc[8];
+    load8(Ub, i, j, A);
+    centre_value(d, g, i, j, A, uc);
+    double b1[3][3], b2[3][3];   // [l][m]: l along x, m along y
+    b1[0][0] = C(i, j, 4); b1[1][0] = Y(i, j, 4); b1[2][0] = C(ip, j, 4);
+    b1[0][1] = X(i, j, 4); b1[1][1] = uc[4];      b1[2][1] = X(ip, j, 4);
+    b1[0][2] = C(i, jp, 4); b1[1][2] = Y(i, jp, 4); b1[2][2] = C(ip, jp, 4);
+    b2[0][0] = C(i, j, 5); b2[1][0] = Y(i, j, 5); b2[2][0] = C(ip, j, 5);
+    b2[0][1] = X(i, j, 5); b2[1][1] = uc[5];      b2[2][1] = X(ip, j, 5);
+    b2[0][2] = C(i, jp, 5); b2[1][2] = Y(i, jp, 5); b2[2][2] = C(ip, jp, 5);
+    const double w[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        double dx1, dy2;
+        if (l == 0) dx1 = fma(4.0, b1[1][m], -3.0 * b1[0][m]) - b1[2][m];
+        else if (l == 1) dx1 = b1[2][m] - b1[0][m];
+        else dx1 = fma(3.0, b1[2][m], fma(-4.0, b1[1][m], b1[0][m]));
+        if (m == 0) dy2 = fma(4.0, b2[l][1], -3.0 * b2[l][0]) - b2[l][2];
+        else if (m == 1) dy2 = b2[l][2] - b2[l][0];
+        else dy2 = fma(3.0, b2[l][2], fma(-4.0, b2[l][1], b2[l][0]));
+        s1 = fma(w[l] * w[m], absd(fma(dx1, g.rdx, dy2 * g.rdy)), s1);
+      }
+    s1 *= g.dx * g.dy;
+    const double right = fma(4.0, b1[2][1], b1[2][0] + b1[2][2]), left = fma(4.0, b1[0][1], b1[0][0] + b1[0][2]);
+    const double top = fma(4.0, b2[1][2], b2[0][2] + b2[2][2]), bottom = fma(4.0, b2[1][0], b2[0][0] + b2[2][0]);
+    s2 = absd(fma(g.dy, right - left, g.dx * (top - bottom))) * (1.0 / 6.0);
+  }
+  __shared__ double sh[2][128];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  sh[0][t] = s1;
+  sh[1][t] = s2;
+  __syncthreads();
+  for (int h = 64; h > 0; h >>= 1) {
+    if (t < h) {
+      sh[0][t] += sh[0][t + h];
+      sh[1][t] += sh[1][t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    partials[2 * b] = sh[0][0];
+    partials[2 * b + 1] = sh[1][0];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_divb_sum(const double *partials, int nblocks, double *out) {
+  __shared__ double sh[2][256];
+  const int t = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int k = t; k < nblocks; k += 256) {
+    a += partials[2 * k];
+    b += partials[2 * k + 1];
+  }
+  sh[0][t] = a;
+  sh[1][t] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      sh[0][t] += sh[0][t + h];
+      sh[1][t] += sh[1][t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out[0] = sh[0][0];
+    out[1] = sh[1][0];
+  }
+}
+
 inline dim3 grid2(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 3) / 4); }
 
 }  // namespace
@@ -1204,6 +1296,12 @@ void af_launch_pointdata(const AfDev &d, const AfGrid &g, int reduce_dt, cudaStr
   k_pointdata<<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, reduce_dt);
 }
 void af_launch_dt(const AfDev &d, const AfGrid &g, cudaStream_t s) { k_dt<<<1, 32, 0, s>>>(d, g); }
+int af_divb_nblocks(const AfGrid &g) { const dim3 b = grid2(g.nx, g.ny); return (int)(b.x * b.y); }
+void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s) {
+  const dim3 b = grid2(g.nx, g.ny);
+  k_divb<<<b, dim3(32, 4), 0, s>>>(d, g, partials);
+  k_divb_sum<<<1, 256, 0, s>>>(partials, (int)(b.x * b.y), out);
+}
 void af_launch_points(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s) {
   k_points<<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
 }
