@@ -266,6 +266,27 @@ def rotor(n: int = 400, kappa: float = 2.0) -> Problem:
     return Problem("rotor", n, n, 0.0, 1.0, 0.0, 1.0, PERIODIC, 5.0 / 3.0, prim, kappa=kappa)
 
 
+def shock_cloud(n: int = 400, kappa: float = 1.0) -> Problem:
+    """Shock-cloud interaction (Example 4.7) on [0,1]^2, gamma = 5/3, outflow
+    boundaries.  Reading: the printed state vectors list (rho, v1, v2, v3, p, B1,
+    B2, B3) (as printed in the order (rho, v, B, p) the left pressure would be
+    negative); left of x = 0.6: rho = 3.86859, v = 0, p = 167.345,
+    B = (0, 2.1826182, -2.1826182); right: rho = 1, v = (-11.2536, 0, 0), p = 1,
+    B = (0, 0.56418958, 0.56418958); a cloud rho = 10 of radius 0.15 centred at
+    (0.8, 0.5), in pressure balance with the right state."""
+    def prim(x, y):
+        left = x < 0.6
+        cloud = (x - 0.8) ** 2 + (y - 0.5) ** 2 < 0.15 ** 2
+        rho = np.where(left, 3.86859, np.where(cloud, 10.0, 1.0))
+        v1 = np.where(left, 0.0, -11.2536)
+        p = np.where(left, 167.345, 1.0)
+        b2 = np.where(left, 2.1826182, 0.56418958)
+        b3 = np.where(left, -2.1826182, 0.56418958)
+        return (rho, v1, _b(x, 0.0), _b(x, 0.0), _b(x, 0.0), b2, b3, p)
+
+    return Problem("shock_cloud", n, n, 0.0, 1.0, 0.0, 1.0, OUTFLOW, 5.0 / 3.0, prim, kappa=kappa)
+
+
 def constant(n: int = 16, ny: int | None = None, bc: int = PERIODIC, gamma: float = 5.0 / 3.0,
              w=(1.3, 0.4, -0.7, 0.2, 0.6, -0.3, 0.25, 2.1)) -> Problem:
     """A uniform state (free-stream preservation)."""

@@ -1,6 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Metric (per DoF class and conserved variable): max |gpu - oracle| / max |oracle|
+Metric (per DoF class and conserved variable): max |gpu - oracle| / max |oracle|,
+a momentum or B component measured against the largest component of its vector
 (fields that are identically zero must match to 1e-300).  Tolerances: 1e-12
 after one step, 1e-10 after 100 smooth steps; where the positivity limiters
 branch, states that took the same branch agree to the same 1e-12 and the
@@ -23,17 +24,25 @@ if not torch.cuda.is_available():
 import paper_2506_04857_gb300 as af  # noqa: E402
 
 
+# conserved variables grouped by physical quantity: rho, momentum, B, E
+GROUPS = [(0,), (1, 2, 3), (1, 2, 3), (1, 2, 3), (4, 5, 6), (4, 5, 6), (4, 5, 6), (7,)]
+
+
 def rel_err(A, B):
-    """max over classes/variables of max|a-b| / max|b|."""
+    """max over classes/variables of max|a-b| / max|b|, where a component of
+    the momentum or of B is measured against the largest component of that
+    vector (a component that is only rounding noise, e.g. B1 of the
+    shock-cloud problem, has no scale of its own).  A variable that is
+    identically zero in b must be exactly zero in a."""
     worst = 0.0
     for a, b in zip(A, B):
         a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
         for k in range(8):
-            den = np.abs(b[k]).max()
             num = np.abs(a[k] - b[k]).max()
-            if den == 0.0:
+            if np.abs(b[k]).max() == 0.0:
                 assert num <= 1e-300, (k, num)
                 continue
+            den = max(np.abs(b[q]).max() for q in GROUPS[k])
             worst = max(worst, num / den)
     return worst
 
@@ -157,7 +166,8 @@ def fe_on(pb, Us, dt, **kw):
 LIMITED = {"orszag_tang": lambda: ai.orszag_tang(48),
            "blast": lambda: ai.blast(40),
            "blast_paper": lambda: ai.blast(36, low_beta=False),
-           "rotor": lambda: ai.rotor(40)}
+           "rotor": lambda: ai.rotor(40),
+           "shock_cloud": lambda: ai.shock_cloud(40)}
 
 
 @pytest.mark.parametrize("case", sorted(LIMITED))
@@ -195,7 +205,7 @@ def test_fe_stage_parity_limited(case):
     assert active > 0
 
 
-@pytest.mark.parametrize("case", ["blast", "blast_paper", "rotor"])
+@pytest.mark.parametrize("case", ["blast", "blast_paper", "rotor", "shock_cloud"])
 def test_step_parity_limited_no_sensor(case):
     """With kappa = 0 the PP limiters alone branch; chained steps agree."""
     pb = LIMITED[case]()

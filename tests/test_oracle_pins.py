@@ -360,6 +360,26 @@ def test_positivity_low_beta_blast():
     assert st[oracle.STAT_NAMES.index("newton_maxit")] <= golden()["newton_max_iterations"] + 1
 
 
+@pytest.mark.parametrize("case", ["blast_paper", "shock_cloud"])
+def test_pp_limiting_is_necessary(case):
+    """Examples 4.6 and 4.7 state that the runs stop on negative pressure
+    without the PP limitings: on a 32x32 grid the unlimited scheme leaves the
+    admissible set within the first step, the limited one stays in it."""
+    pb = ai.blast(32, low_beta=False) if case == "blast_paper" else ai.shock_cloud(32)
+
+    def admissible(V):
+        return all(np.isfinite(a).all() and a[0].min() > 0 and pressure_field(a, pb.gamma).min() > 0 for a in V)
+
+    V, _ = oracle.step(pb, ai.dofs(pb), pp_on=False)
+    assert not admissible(V)
+    U = ai.dofs(pb)
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    for _ in range(10):
+        U, _ = oracle.step(pb, U, stats=st)
+        assert admissible(U)
+    assert st[oracle.STAT_NAMES.index("point_limited")] > 0
+
+
 def test_dt_closed_form_constant_state():
     pb = ai.constant(8, 4)
     U = ai.dofs(pb)
