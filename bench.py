@@ -65,6 +65,31 @@ FP64_FLOPS_PER_SM_CYCLE = 4.0
 ALGO_BYTES_PER_CS = (512.0 + 768.0 + 768.0) / 3.0
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest of the ranks' values of x (a job's time is that of its
+    slowest rank); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_runs(cells, rank: int, world: int):
+    """Indices of the ensemble runs that `rank` advances: a greedy
+    longest-processing-time partition by cell count (largest run first, to
+    the least loaded rank; ties by index), the same on every rank."""
+    order = sorted(range(len(cells)), key=lambda r: (-cells[r], r))
+    load = [0] * world
+    owner = [0] * len(cells)
+    for r in order:
+        k = min(range(world), key=lambda q: (load[q], q))
+        owner[r] = k
+        load[k] += cells[r]
+    return [r for r in range(len(cells)) if owner[r] == rank]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -204,13 +229,23 @@ def reference_arm(args, key, desc, pb):
 
 
 def ensemble_bench(args, desc):
-    """The batched ensemble against the plain per-run loop on the same GPU."""
+    """The batched ensemble against the plain per-run loop on the same GPU.
+    Under torchrun the runs are sharded over the ranks (shard_runs; no data
+    exchange) and the job's time is that of the slowest rank."""
     import torch
     import paper_2506_04857_gb300 as af
 
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     stream = torch.cuda.Stream()
-    pbs = ai.ot_ensemble(256, seed=0)
+    every = ai.ot_ensemble(256, seed=0)
+    total_cells = sum(p.nx * p.ny for p in every)
+    pbs = [every[r] for r in shard_runs([p.nx * p.ny for p in every], rank, world)]
     states = [ai.dofs(p) for p in pbs]
     cells = sum(p.nx * p.ny for p in pbs)
     steps = max(3, (args.steps + 2) // 3 * 3)
@@ -233,7 +268,7 @@ def ensemble_bench(args, desc):
         af.af_batch_step(b, steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_batch = e0.elapsed_time(e1)
+        ms_batch = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         rc, cnt = af.af_batch_status(b, reset=True)
         if rc != af.AF_OK:
             raise SystemExit("batch: " + af.af_batch_last_error(b))
@@ -255,19 +290,24 @@ def ensemble_bench(args, desc):
                 sv.step(dt_out=False)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_loop = e0.elapsed_time(e1)
+        ms_loop = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         for sv in solvers:
             sv.close()
-    v_batch = cells * 3 * steps / (ms_batch * 1e-3)
-    v_loop = cells * 3 * steps / (ms_loop * 1e-3)
+    v_batch = total_cells * 3 * steps / (ms_batch * 1e-3)
+    v_loop = total_cells * 3 * steps / (ms_loop * 1e-3)
     line = {"metric": "FP64 AF-MHD cell-stage updates/s", "value": v_batch, "unit": "cell-stage updates/s",
-            "n_gpus": 1, "steps": steps, "warmup": warm, "ms_per_step": ms_batch / steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "runs": len(pbs), "cells": cells, "seed": 0},
+            "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms_batch / steps,
+            "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "runs": len(every), "cells": total_cells, "seed": 0,
+                       "runs_per_rank": len(pbs), "sharding": "runs over ranks, greedy by cells"},
             "batched": {"value": v_batch, "autotune": choice, "graph": True, "launches_per_step": 19},
             "plain_loop": {"value": v_loop, "ms_per_step": ms_loop / steps, "launches_per_step": 19 * len(pbs)},
             "batched_over_loop": v_batch / v_loop, "limiter_counters": cnt}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -386,11 +426,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ktimes = s.timing(False)
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     clk = clocks.stop()
     rc, cnt = s.status(reset=True)
@@ -438,11 +475,7 @@ def main():
         s.step(dt_out=False)
         s.get_state(out=[h.numpy() for h in host_out], device=False)   # D2H, synchronous
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": cells * 3 * args.e2e_steps * world / te, "unit": "cell-stage updates/s",
            "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state, "steps": args.e2e_steps}
 
