@@ -38,6 +38,7 @@ import af_inputs as ai  # noqa: E402
 WORKLOADS = {
     "blast2048": ("low-beta blast 2048x2048 outflow, kappa=1", lambda: ai.blast(2048)),
     "blast512": ("low-beta blast 512x512 outflow, kappa=1 (profiling size)", lambda: ai.blast(512)),
+    "blast1024": ("low-beta blast 1024x1024 outflow, kappa=1 (profiling size)", lambda: ai.blast(1024)),
     "ot512": ("Orszag-Tang 512x512 periodic, kappa=1", lambda: ai.orszag_tang(512)),
     "vortex64": ("smooth vortex 64x64 periodic, kappa=0", lambda: ai.vortex(64)),
     "ensemble256": ("256 seeded Orszag-Tang runs, nx, ny drawn from {64,128,256,512}, kappa=1, one batch",
@@ -60,6 +61,12 @@ ALGO_FLOPS = {
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
 FP64_FLOPS_PER_SM_CYCLE = 4.0
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_points
+# launch per cell, from one ncu capture of the 1024x1024 low-beta blast
+# (1.035 GB read + 0.254 GB written for 1,048,576 cells); the 2048x2048 launch
+# is taken as 4x that (the kernel's traffic is per cell: its own and its
+# neighbours' point data).
+DRAM_BYTES_PER_CELL = {"k_points": 1229.4}
 # Algorithmic bytes per cell-stage: read U^(s) (32 doubles), read U^n on stages
 # 2 and 3, write U^(s+1): (512 + 768 + 768)/3 B.
 ALGO_BYTES_PER_CS = (512.0 + 768.0 + 768.0) / 3.0
@@ -449,8 +456,10 @@ def main():
     props = torch.cuda.get_device_properties(local)
     max_mhz = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
     peak = FP64_FLOPS_PER_SM_CYCLE * props.multi_processor_count * max_mhz * 1e6 * 1e-12
+    traffic = DRAM_BYTES_PER_CELL[dom] * cells if dom in DRAM_BYTES_PER_CELL and pb.name == "blast_low_beta" else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": "ncu capture of the 1024x1024 blast, scaled by cells" if traffic else None,
                 "peak_source": "derived: 2 DFMA/SM/cycle x %d SMs x %.0f MHz x 2 flops" % (props.multi_processor_count,
                                                                                          max_mhz),
                 "probe_fp64_tflops": peak_fp64,
