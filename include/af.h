@@ -71,13 +71,7 @@ enum {
 };
 
 typedef struct af_params {
-  double cfl;        /* The shock-sensor blending coefficients theta^s of Sec. 3.4 for the current
- * state: theta_x at the x-faces, an [ny][nxf] array (class AF_CLASS_XFACE
- * extents), theta_y at the y-faces, an [nyf][nx] array (AF_CLASS_YFACE
- * extents).  With kappa = 0 every coefficient is 1. */
-int af_sensor(af_ctx *ctx, double *theta_x, double *theta_y, int on_device);
-
-/* dt = cfl / (max varrho_1/dx + max varrho_2/dy), maxima over all four DoF
+  double cfl;        /* dt = cfl / (max varrho_1/dx + max varrho_2/dy), maxima over all four DoF
                         classes of U^n (Sec. 2.3 eq. cf; the paper prints no formula).  Default 0.2. */
   double kappa;      /* shock-sensor strength kappa (Sec. 3.4); 0 gives theta^s = 1.  Default 0. */
   int pp_on;         /* positivity-preserving limiters of Sec. 3.2-3.3 and Remark 4.1.  Default 1. */
