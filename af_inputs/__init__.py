@@ -405,3 +405,102 @@ def perturbed_vortex(n: int = 256, seed: int = 0, amp: float = 1e-3, kmax: int =
 
     return Problem("perturbed_vortex", n, n, -half_width, half_width, -half_width, half_width, PERIODIC,
                    base.gamma, prim)
+
+
+# ---------------------------------------------------------------------------
+# 1D problems (Sec. 4, Examples 4.1-4.2): states [averages [8, n], point values [8, nf]]
+# ---------------------------------------------------------------------------
+@dataclasses.dataclass
+class Problem1D:
+    """A 1D test problem on [x0, x1]; prim(x) returns (rho, v1, v2, v3, B1, B2, B3, p)."""
+    name: str
+    n: int
+    x0: float
+    x1: float
+    bc: int
+    gamma: float
+    prim: Callable
+    kappa: float = 0.0
+    cfl: float = 0.2
+    t_end: float = 0.0
+    y0: float = 0.0     # unused; lets the 2D parameter helpers serve 1D problems
+    y1: float = 1.0
+
+    @property
+    def dx(self) -> float:
+        return (self.x1 - self.x0) / self.n
+
+    @property
+    def nf(self) -> int:
+        return self.n if self.bc == PERIODIC else self.n + 1
+
+
+def dofs1(pb: Problem1D, quad: int = 5) -> List[np.ndarray]:
+    """Cell averages (Gauss-Legendre quadrature of the conserved variables) and
+    exact interface point values of pb's initial condition."""
+    xg, wg = _gauss_legendre(quad)
+    xc = pb.x0 + (np.arange(pb.n) + 0.5) * pb.dx
+    acc = None
+    for a in range(quad):
+        v = wg[a] * prim_to_cons(pb.prim(xc + xg[a] * pb.dx), pb.gamma)
+        acc = v if acc is None else acc + v
+    xf = pb.x0 + np.arange(pb.nf) * pb.dx
+    return [np.ascontiguousarray(acc), np.ascontiguousarray(prim_to_cons(pb.prim(xf), pb.gamma))]
+
+
+def _piecewise(left, right, x_split=0.5):
+    def prim(x):
+        x = np.asarray(x, dtype=np.float64)
+        return tuple(np.where(x < x_split, l, r) + 0.0 * x for l, r in zip(left, right))
+    return prim
+
+
+def riemann_rj(n: int = 800, kappa: float = 10.0) -> Problem1D:
+    """Example 4.1, first case: gamma = 2, [0,1], split at 0.5, T = 0.2."""
+    return Problem1D("riemann_rj", n, 0.0, 1.0, OUTFLOW, 2.0,
+                     _piecewise((1.0, 0.0, 0.0, 0.0, 0.75, 1.0, 0.0, 1.0),
+                                (0.125, 0.0, 0.0, 0.0, 0.75, -1.0, 0.0, 0.1)), kappa=kappa, t_end=0.2)
+
+
+def riemann_2(n: int = 800, kappa: float = 50.0) -> Problem1D:
+    """Example 4.1, second case: gamma = 5/3, [0,1], split at 0.5, T = 0.2."""
+    s = math.sqrt(4.0 * math.pi)
+    return Problem1D("riemann_2", n, 0.0, 1.0, OUTFLOW, 5.0 / 3.0,
+                     _piecewise((1.08, 1.2, 0.01, 0.5, 2.0 / s, 3.6 / s, 2.0 / s, 0.95),
+                                (1.0, 0.0, 0.0, 0.0, 2.0 / s, 4.0 / s, 2.0 / s, 1.0)), kappa=kappa, t_end=0.2)
+
+
+def blast1d(n: int = 400, kappa: float = 1.0) -> Problem1D:
+    """A strong 1D blast: the low-beta blast's pressure jump (1000 / 0.1) and field
+    B = (100/sqrt(4 pi)) (1/sqrt 2, 1/sqrt 2, 0), gamma = 1.4, on [-0.5, 0.5] with
+    p = 1000 for |x| < 0.1; outflow.  Positivity test for the 1D limiters."""
+    b = 100.0 / math.sqrt(4.0 * math.pi) / math.sqrt(2.0)
+
+    def prim(x):
+        x = np.asarray(x, dtype=np.float64)
+        z = 0.0 * x
+        return (z + 1.0, z, z, z, z + b, z + b, z, np.where(np.abs(x) < 0.1, 1000.0, 0.1) + z)
+    return Problem1D("blast1d", n, -0.5, 0.5, OUTFLOW, 1.4, prim, kappa=kappa)
+
+
+def entropy_wave1d(n: int = 64, t: float = 0.0, amp: float = 0.2, gamma: float = 5.0 / 3.0) -> Problem1D:
+    """A density wave rho = 1 + amp sin(2 pi (x - t)) carried by uniform v = (1, 0.2, -0.1),
+    B = (0.6, 0.3, 0.1), p = 1 on the periodic [0,1]: an exact solution (shifted by t)."""
+    def prim(x):
+        x = np.asarray(x, dtype=np.float64)
+        z = 0.0 * x
+        return (1.0 + amp * np.sin(2.0 * math.pi * (x - t)), z + 1.0, z + 0.2, z - 0.1, z + 0.6, z + 0.3, z + 0.1,
+                z + 1.0)
+    return Problem1D("entropy_wave1d", n, 0.0, 1.0, PERIODIC, gamma, prim)
+
+
+def mirror1d(U: List[np.ndarray]) -> List[np.ndarray]:
+    """The mirror image x -> -x of a 1D state: reversed order, v1 and B1 negated
+    (the averages reverse; the point values reverse onto the same face set)."""
+    out = []
+    for a in U:
+        b = a[:, ::-1].copy()
+        b[1] = -b[1]
+        b[4] = -b[4]
+        out.append(b)
+    return out

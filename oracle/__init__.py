@@ -93,6 +93,11 @@ def _lib(count: bool = False, complex_step: bool = False):
             lib.or_sensor_phi.argtypes = [dp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
             lib.or_sensor.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp, dp]
             lib.or_divb.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, dp]
+            lib.or1d_dt.restype = C.c_double
+            lib.or1d_dt.argtypes = [C.POINTER(Params), C.c_int, pp]
+            lib.or1d_stage.argtypes = [C.POINTER(Params), C.c_int, pp, pp, C.c_double, C.c_double, C.c_double, pp,
+                                       C.POINTER(C.c_longlong)]
+            lib.or1d_step.argtypes = [C.POINTER(Params), C.c_int, pp, C.c_double, dp, C.POINTER(C.c_longlong)]
             if key == "cs":
                 lib.or_step_cs.restype = C.c_int
                 lib.or_step_cs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double]
@@ -184,6 +189,41 @@ def divb(pb, U, **kw):
     out = np.zeros(2)
     _lib().or_divb(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(out))
     return float(out[0]), float(out[1])
+
+
+# ---- the 1D scheme: states are [averages [8, n], point values [8, nf]] ----------
+def _check1(U, pb):
+    nf = pb.n if pb.bc == 0 else pb.n + 1
+    A = np.ascontiguousarray(U[0], dtype=np.float64)
+    P = np.ascontiguousarray(U[1], dtype=np.float64)
+    if A.shape != (8, pb.n) or P.shape != (8, nf):
+        raise ValueError("1D state must be [8, %d] and [8, %d]" % (pb.n, nf))
+    return [A, P]
+
+
+def dt1(pb, U, **kw) -> float:
+    P = params_for(pb, **kw)
+    return _lib().or1d_dt(C.byref(P), pb.n, _ptrs(_check1(U, pb)))
+
+
+def stage1(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, **kw):
+    P = params_for(pb, **kw)
+    Un, Us = _check1(Un, pb), _check1(Us, pb)
+    out = [np.zeros_like(Un[0]), np.zeros_like(Un[1])]
+    st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
+    _lib().or1d_stage(C.byref(P), pb.n, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
+                      st.ctypes.data_as(C.POINTER(C.c_longlong)))
+    return out
+
+
+def step1(pb, U, dt_in: float = 0.0, stats: Optional[np.ndarray] = None, **kw):
+    """One SSP-RK3 step of the 1D scheme; returns (new state, dt used)."""
+    P = params_for(pb, **kw)
+    V = [a.copy() for a in _check1(U, pb)]
+    st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
+    d = C.c_double(0.0)
+    _lib().or1d_step(C.byref(P), pb.n, _ptrs(V), dt_in, C.byref(d), st.ctypes.data_as(C.POINTER(C.c_longlong)))
+    return V, d.value
 
 
 def flux(l: int, U, gamma: float) -> np.ndarray:

@@ -1174,6 +1174,305 @@ static void rhs(const Ctx &C, State &S, State &out) {
 // ---------------------------------------------------------------------------
 // C ABI used by the test-suite (ctypes).
 // ---------------------------------------------------------------------------
+// ===========================================================================
+// The 1D AF scheme (Sec. 4: the 1D tests use the 1D AF scheme with the LLF
+// FVS and without the Godunov-Powell source).  Reading: the scheme of
+// Sec. 2-3 restricted to one dimension.  Degrees of freedom: cell averages
+// and the point values at the interfaces (point f at x0 + f dx, the left face
+// of cell f).  Per stage:
+//   - centre value of the cell parabola, (6 Ubar - U_L - U_R)/4 (Simpson),
+//     limited as in Remark 3.2;
+//   - point update by the LLF FVS on the line (point f-1, centre f-1,
+//     point f, centre f, point f+1), alpha = max varrho_1 on the line;
+//   - the Sec. 3.3 point limiter, its LLF state from the LLF fluxes between
+//     point f and its neighbouring points f-1, f+1;
+//   - the Sec. 3.4 sensor with every y-difference zero;
+//   - cell averages: the face flux is F1 of the face point value, blended
+//     with the LLF flux between the adjacent averages by theta^s; the flux
+//     limiter of Sec. 3.2 with the two faces L, R (no source, so
+//     U^{Lim,1} = U^LLF), face theta = min of the adjacent Lambda, and the
+//     round-off shrink of Remark 4.1;
+//   - SSP-RK3, dt = cfl dx / max varrho_1 over averages and points.
+// Boundaries as in 2D: periodic, or outflow mirrors across the boundary face.
+// ===========================================================================
+struct Ctx1 {
+  int n, nf, bc;
+  double dx, gamma, cfl, kappa;
+  int pp_on;
+};
+
+static void make_ctx1(const or_params *p, int n, Ctx1 &C) {
+  C.n = n; C.nf = p->bc == 0 ? n : n + 1; C.bc = p->bc;
+  C.dx = (p->x1 - p->x0) / n; C.gamma = p->gamma; C.cfl = p->cfl; C.kappa = p->kappa; C.pp_on = p->pp_on;
+}
+
+// ncomp components on an index range [-G, len + G)
+struct Arr1 {
+  int nc = 0, len = 0;
+  std::vector<real> a;
+  void init(int ncomp, int n) { nc = ncomp; len = n; a.assign((size_t)nc * (n + 2 * G), real(0.0)); }
+  real &at(int k, int i) { return a[(size_t)k * (len + 2 * G) + (size_t)(i + G)]; }
+};
+// kind 0: cell index set (len n), kind 1: point index set (len nf)
+static void ghost_fill1(const Ctx1 &C, Arr1 &A, int kind) {
+  for (int i = -G; i < A.len + G; ++i) {
+    if (i >= 0 && i < A.len) continue;
+    int si = map_idx(i, C.n, kind, C.bc);
+    for (int k = 0; k < A.nc; ++k) A.at(k, i) = A.at(k, si);
+  }
+}
+struct PD1 {
+  int len = 0;
+  std::vector<PD> d;
+  void init(int n) { len = n; d.assign((size_t)(n + 2 * G), PD()); }
+  PD &at(int i) { return d[(size_t)(i + G)]; }
+};
+static void pd_fill1(const Ctx1 &C, Arr1 &U, PD1 &P) {
+  P.init(U.len);
+  for (int i = -G; i < U.len + G; ++i) {
+    real u[8];
+    for (int k = 0; k < 8; ++k) u[k] = U.at(k, i);
+    point_data(u, C.gamma, P.at(i));
+  }
+}
+
+static real compute_dt1(const Ctx1 &C, Arr1 &A, Arr1 &P) {
+  set_phase(PH_DT);
+  real m = real(0.0);
+  Arr1 *S[2] = {&A, &P};
+  for (int c = 0; c < 2; ++c)
+    for (int i = 0; i < S[c]->len; ++i) {
+      real u[8];
+      for (int k = 0; k < 8; ++k) u[k] = S[c]->at(k, i);
+      PD d;
+      point_data(u, C.gamma, d);
+      m = rmax(m, d.sr[0]);
+    }
+  return real(C.cfl) / (m / real(C.dx));
+}
+
+// One limited forward-Euler stage of the 1D scheme and the RK combination
+// out = a Un + b FE(Us) for the averages (A) and the point values (P).
+static void stage1(const Ctx1 &C, Arr1 &An, Arr1 &Pn, Arr1 &As, Arr1 &Ps, real dt, real a, real b, Arr1 &Ao, Arr1 &Po,
+                   long long *st) {
+  const double dx = C.dx;
+  ghost_fill1(C, As, 0);
+  ghost_fill1(C, Ps, 1);
+  set_phase(PH_POINTDATA);
+  PD1 pa, pp, pc;
+  pd_fill1(C, As, pa);
+  pd_fill1(C, Ps, pp);
+  // centre values (Simpson on the cell parabola) + Remark 3.2
+  set_phase(PH_CENTER);
+  Arr1 Uc;
+  Uc.init(8, C.n);
+  for (int i = 0; i < C.n; ++i) {
+    real avg[8], uc[8], out[8], t1, t2;
+    for (int k = 0; k < 8; ++k) {
+      avg[k] = As.at(k, i);
+      uc[k] = (real(6.0) * avg[k] - Ps.at(k, i) - Ps.at(k, i + 1)) / real(4.0);
+    }
+    scaling_limiter(uc, avg, C.gamma, out, t1, t2);
+    if (t1 < real(1.0) || t2 < real(1.0)) st[ST_CENTER_LIMITED]++;
+    for (int k = 0; k < 8; ++k) Uc.at(k, i) = out[k];
+  }
+  ghost_fill1(C, Uc, 0);
+  set_phase(PH_POINTDATA);
+  pd_fill1(C, Uc, pc);
+  // point values: LLF FVS, then the Sec. 3.3 limiter
+  Arr1 PF;
+  PF.init(8, C.nf);
+  for (int f = 0; f < C.nf; ++f) {
+    set_phase(PH_POINT_HO);
+    const PD &me = pp.at(f);
+    const PD *L[5] = {&pp.at(f - 1), &pc.at(f - 1), &me, &pc.at(f), &pp.at(f + 1)};
+    real d1[8], dB1, UH[8];
+    fvs_derivative(0, L, dx, d1, dB1);
+    for (int k = 0; k < 8; ++k) UH[k] = me.U[k] + dt * (real(0.0) - d1[k]);
+    real out[8];
+    if (!C.pp_on) {
+      for (int k = 0; k < 8; ++k) out[k] = UH[k];
+    } else {
+      set_phase(PH_POINT_PP);
+      real Fr[8], Fl[8], UL[8], t1, t2;
+      llf_flux(0, me, pp.at(f + 1), Fr, nullptr);
+      llf_flux(0, pp.at(f - 1), me, Fl, nullptr);
+      for (int k = 0; k < 8; ++k) UL[k] = me.U[k] - dt / real(dx) * (Fr[k] - Fl[k]);
+      scaling_limiter(UH, UL, C.gamma, out, t1, t2);
+      if (t1 < real(1.0) || t2 < real(1.0)) st[ST_POINT_LIMITED]++;
+      if (!in_G(out, C.gamma)) {   // Remark 4.1, as in 2D
+        st[ST_SHRINK]++;
+        real Us[8];
+        for (int k = 0; k < 8; ++k) Us[k] = UH[k];
+        Us[0] = t1 * UH[0] + (real(1.0) - t1) * UL[0];
+        bool ok = false;
+        for (int m = 0; m < 10 && !ok; ++m) {
+          real th = rmax(real(0.0), t2 - real(std::ldexp(1e-8, m)));
+          for (int k = 0; k < 8; ++k) out[k] = th * Us[k] + (real(1.0) - th) * UL[k];
+          ok = in_G(out, C.gamma);
+        }
+        if (!ok) for (int k = 0; k < 8; ++k) out[k] = UL[k];
+        if (!in_G(out, C.gamma)) st[ST_NONADMISSIBLE]++;
+      }
+    }
+    for (int k = 0; k < 8; ++k) PF.at(k, f) = out[k];
+  }
+  // sensor phi on cells [-1, n] (y-differences zero)
+  set_phase(PH_SENSOR_PHI);
+  Arr1 phi;
+  phi.init(3, C.n);
+  for (int i = -1; i <= C.n; ++i) {
+    real ph[4];
+    const PD &c = pa.at(i);
+    sensor_phi(c, pa.at(i + 1), pa.at(i - 1), c, c, dx, dx, ph);
+    phi.at(0, i) = ph[0];
+    phi.at(1, i) = ph[2];
+    phi.at(2, i) = ph[3];
+  }
+  // faces: F1 of the point value, LLF flux between the adjacent averages, theta^s
+  set_phase(PH_FACE);
+  Arr1 Fh, Fl, ts, al;
+  Fh.init(8, C.nf); Fl.init(8, C.nf); ts.init(1, C.nf); al.init(1, C.nf);
+  for (int f = 0; f < C.nf; ++f) {
+    real F[8], alpha;
+    llf_flux(0, pa.at(f - 1), pa.at(f), F, &alpha);
+    for (int k = 0; k < 8; ++k) {
+      Fh.at(k, f) = pp.at(f).F[0][k];
+      Fl.at(k, f) = F[k];
+    }
+    al.at(0, f) = alpha;
+    set_phase(PH_SENSOR_THETA);
+    real t = real(1.0);
+    if (C.kappa != 0.0) {
+      real p1 = rmax(phi.at(0, f - 1), phi.at(0, f)), p2 = rmax(phi.at(1, f - 1), phi.at(1, f));
+      real p3 = rmax(phi.at(2, f - 1), phi.at(2, f));
+      t = exp(real(0.0) - real(C.kappa) * (p1 * p2 + p3));
+    }
+    ts.at(0, f) = t;
+    if (val(t) < 0.99) st[ST_SENSOR_LT099]++;
+    set_phase(PH_FACE);
+  }
+  ghost_fill1(C, Fh, 1);
+  ghost_fill1(C, Fl, 1);
+  ghost_fill1(C, ts, 1);
+  ghost_fill1(C, al, 1);
+  // cell averages
+  set_phase(PH_CELL_UPDATE);
+  Arr1 AF, L1, H, Lam;
+  AF.init(8, C.n); L1.init(8, C.n); H.init(16, C.n); Lam.init(2, C.n);
+  NewtonLog nl;
+  for (int i = 0; i < C.n; ++i) {
+    real Fss[2][8], Fll[2][8];
+    for (int I = 0; I < 2; ++I)
+      for (int k = 0; k < 8; ++k) {
+        const int f = i + I;
+        Fll[I][k] = Fl.at(k, f);
+        Fss[I][k] = (C.kappa == 0.0) ? Fh.at(k, f) : ts.at(0, f) * Fh.at(k, f) + (real(1.0) - ts.at(0, f)) * Fll[I][k];
+      }
+    if (!C.pp_on) {
+      for (int k = 0; k < 8; ++k) AF.at(k, i) = As.at(k, i) - dt / real(dx) * (Fss[1][k] - Fss[0][k]);
+      continue;
+    }
+    real Ullf[8];
+    for (int k = 0; k < 8; ++k) Ullf[k] = As.at(k, i) - dt / real(dx) * (Fll[1][k] - Fll[0][k]);
+    // Lemma 3.1 CFL condition restricted to x (diagnostic only)
+    if (val(dt * (al.at(0, i) / real(dx) + al.at(0, i + 1) / real(dx))) > 1.0 + 1e-12) st[ST_CFL_VIOLATIONS]++;
+    real eps_rho = rmin(real(1e-13), Ullf[0]);
+    real eps_p = rmin(real(1e-13), pressure(Ullf, C.gamma));
+    real Hb[4][8];
+    for (int k = 0; k < 8; ++k) {
+      Hb[0][k] = dt / real(dx) * (Fss[0][k] - Fll[0][k]);
+      Hb[1][k] = real(0.0) - dt / real(dx) * (Fss[1][k] - Fll[1][k]);
+      Hb[2][k] = real(0.0);
+      Hb[3][k] = real(0.0);
+    }
+    real lam[4];
+    flux_limiter_box(Ullf, Hb, eps_rho, eps_p, C.gamma, lam, nl);   // the zero directions leave 4 vertices
+    if (lam[0] < real(1.0) || lam[1] < real(1.0)) st[ST_LAMBDA_LT1]++;
+    for (int k = 0; k < 8; ++k) {
+      L1.at(k, i) = Ullf[k];
+      H.at(k, i) = Hb[0][k];
+      H.at(8 + k, i) = Hb[1][k];
+    }
+    Lam.at(0, i) = lam[0];
+    Lam.at(1, i) = lam[1];
+  }
+  st[ST_NEWTON_SOLVES] += nl.solves;
+  st[ST_NEWTON_MAXIT] = std::max<long long>(st[ST_NEWTON_MAXIT], nl.maxit);
+  if (C.pp_on) {
+    set_phase(PH_CELL_FINAL);
+    ghost_fill1(C, Lam, 0);
+    Arr1 th;
+    th.init(1, C.nf);
+    for (int f = 0; f < C.nf; ++f) {
+      if (C.bc == 1 && f == 0) th.at(0, f) = Lam.at(0, 0);
+      else if (C.bc == 1 && f == C.n) th.at(0, f) = Lam.at(1, C.n - 1);
+      else th.at(0, f) = rmin(Lam.at(1, f - 1), Lam.at(0, f));
+      if (val(th.at(0, f)) < 1.0) st[ST_FACE_THETA_LT1]++;
+    }
+    ghost_fill1(C, th, 1);
+    auto value = [&](int i, real tl, real tr, real *out) {
+      for (int k = 0; k < 8; ++k) out[k] = L1.at(k, i) + tl * H.at(k, i) + tr * H.at(8 + k, i);
+    };
+    for (int i = 0; i < C.n; ++i) {
+      real out[8];
+      value(i, th.at(0, i), th.at(0, i + 1), out);
+      for (int k = 0; k < 8; ++k) AF.at(k, i) = out[k];
+    }
+    // Remark 4.1, in cell order; neighbours sharing a lowered face are recomputed
+    for (int i = 0; i < C.n; ++i) {
+      real cur[8];
+      for (int k = 0; k < 8; ++k) cur[k] = AF.at(k, i);
+      if (in_G(cur, C.gamma)) continue;
+      st[ST_SHRINK]++;
+      const real t0[2] = {th.at(0, i), th.at(0, i + 1)};
+      for (int m = 0; m <= 10; ++m) {
+        real t[2], out[8];
+        for (int I = 0; I < 2; ++I) t[I] = (m < 10) ? rmax(real(0.0), t0[I] - real(std::ldexp(1e-8, m))) : real(0.0);
+        value(i, t[0], t[1], out);
+        if (in_G(out, C.gamma) || m == 10) {
+          th.at(0, i) = t[0];
+          th.at(0, i + 1) = t[1];
+          for (int k = 0; k < 8; ++k) AF.at(k, i) = out[k];
+          if (!in_G(out, C.gamma)) st[ST_NONADMISSIBLE]++;
+          break;
+        }
+      }
+      ghost_fill1(C, th, 1);
+      for (int q = -1; q <= 1; q += 2) {
+        int ii = i + q;
+        if (C.bc == 1 && (ii < 0 || ii >= C.n)) continue;
+        ii = imod(ii, C.n);
+        real o2[8];
+        value(ii, th.at(0, ii), th.at(0, ii + 1), o2);
+        for (int k = 0; k < 8; ++k) AF.at(k, ii) = o2[k];
+      }
+    }
+  }
+  set_phase(PH_RK);
+  Ao.init(8, C.n);
+  Po.init(8, C.nf);
+  for (int k = 0; k < 8; ++k) {
+    for (int i = 0; i < C.n; ++i) Ao.at(k, i) = (val(a) == 0.0) ? AF.at(k, i) : a * An.at(k, i) + b * AF.at(k, i);
+    for (int f = 0; f < C.nf; ++f) Po.at(k, f) = (val(a) == 0.0) ? PF.at(k, f) : a * Pn.at(k, f) + b * PF.at(k, f);
+  }
+}
+
+static void load1(const Ctx1 &C, const double *const *U, Arr1 &A, Arr1 &P) {
+  A.init(8, C.n);
+  P.init(8, C.nf);
+  for (int k = 0; k < 8; ++k) {
+    for (int i = 0; i < C.n; ++i) A.at(k, i) = real(U[0][(size_t)k * C.n + i]);
+    for (int f = 0; f < C.nf; ++f) P.at(k, f) = real(U[1][(size_t)k * C.nf + f]);
+  }
+}
+static void store1(const Ctx1 &C, Arr1 &A, Arr1 &P, double *const *U) {
+  for (int k = 0; k < 8; ++k) {
+    for (int i = 0; i < C.n; ++i) U[0][(size_t)k * C.n + i] = val(A.at(k, i));
+    for (int f = 0; f < C.nf; ++f) U[1][(size_t)k * C.nf + f] = val(P.at(k, f));
+  }
+}
+
 extern "C" {
 
 int or_sizes(int nx, int ny, int bc, int cls, int *nxp, int *nyp) {
@@ -1402,6 +1701,46 @@ void or_sensor_phi(const double *c, const double *e, const double *w, const doub
   real ph[4];
   sensor_phi(d[0], d[1], d[2], d[3], d[4], dx, dy, ph);
   for (int q = 0; q < 4; ++q) phi[q] = val(ph[q]);
+}
+
+// ---- the 1D scheme (see the block above) ----------------------------------
+// U[0]: averages [8][n], U[1]: point values [8][nf], nf = n (periodic) or n+1.
+double or1d_dt(const or_params *p, int n, const double *const *U) {
+  Ctx1 C;
+  make_ctx1(p, n, C);
+  Arr1 A, P;
+  load1(C, U, A, P);
+  return val(compute_dt1(C, A, P));
+}
+
+int or1d_stage(const or_params *p, int n, const double *const *Un, const double *const *Us, double dt, double a,
+               double b, double *const *out, long long *st) {
+  Ctx1 C;
+  make_ctx1(p, n, C);
+  Arr1 An, Pn, As, Ps, Ao, Po;
+  load1(C, Un, An, Pn);
+  load1(C, Us, As, Ps);
+  long long loc[ST_NSTATS] = {0};
+  stage1(C, An, Pn, As, Ps, real(dt), real(a), real(b), Ao, Po, loc);
+  store1(C, Ao, Po, out);
+  if (st) for (int k = 0; k < ST_NSTATS; ++k) st[k] = (k == ST_NEWTON_MAXIT) ? std::max(st[k], loc[k]) : st[k] + loc[k];
+  return 0;
+}
+
+int or1d_step(const or_params *p, int n, double *const *U, double dt_in, double *dt_used, long long *st) {
+  Ctx1 C;
+  make_ctx1(p, n, C);
+  Arr1 An, Pn, A1, P1, A2, P2, A3, P3;
+  load1(C, U, An, Pn);
+  real dt = (dt_in > 0.0) ? real(dt_in) : compute_dt1(C, An, Pn);
+  long long loc[ST_NSTATS] = {0};
+  stage1(C, An, Pn, An, Pn, dt, real(0.0), real(1.0), A1, P1, loc);
+  stage1(C, An, Pn, A1, P1, dt, real(3.0) / real(4.0), real(1.0) / real(4.0), A2, P2, loc);
+  stage1(C, An, Pn, A2, P2, dt, real(1.0) / real(3.0), real(2.0) / real(3.0), A3, P3, loc);
+  store1(C, A3, P3, U);
+  if (dt_used) *dt_used = val(dt);
+  if (st) for (int k = 0; k < ST_NSTATS; ++k) st[k] = (k == ST_NEWTON_MAXIT) ? std::max(st[k], loc[k]) : st[k] + loc[k];
+  return 0;
 }
 
 #ifdef AF_ORACLE_COMPLEX

@@ -604,3 +604,101 @@ def test_divb_closed_forms():
     assert pb.dx != pb.dy
     d1, d2 = oracle.divb(pb, ai.dofs(pb))
     assert d1 <= 1e-12 and d2 <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# The 1D scheme (Sec. 4, Examples 4.1-4.2: the 2D scheme restricted to x)
+# ---------------------------------------------------------------------------
+def _prims1(U, gamma):
+    rho = U[0]
+    p = (gamma - 1.0) * (U[7] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / rho - 0.5 * (U[4] ** 2 + U[5] ** 2 + U[6] ** 2))
+    return rho, p
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_1d_free_stream(bc):
+    def prim(x):
+        z = 0.0 * np.asarray(x, dtype=np.float64)
+        return (z + 1.3, z + 0.4, z - 0.2, z + 0.1, z + 0.7, z - 0.5, z + 0.3, z + 2.0)
+    pb = ai.Problem1D("const1d", 23, 0.0, 1.0, bc, 5.0 / 3.0, prim, kappa=1.0)
+    U0 = ai.dofs1(pb)
+    U = U0
+    for _ in range(20):
+        U, _ = oracle.step1(pb, U)
+    for a, b in zip(U, U0):
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+
+
+def test_1d_entropy_wave_third_order():
+    errs = []
+    for n in (16, 32, 64):
+        pb = ai.entropy_wave1d(n)
+        U = ai.dofs1(pb)
+        t, T = 0.0, 0.1
+        while t < T - 1e-15:
+            dt = min(oracle.dt1(pb, U), T - t)
+            U, _ = oracle.step1(pb, U, dt_in=dt)
+            t += dt
+        ex = ai.dofs1(ai.entropy_wave1d(n, t=T))
+        errs.append(np.abs(U[0][0] - ex[0][0]).mean())
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) >= 2.8, (errs, rates)
+
+
+def test_1d_mass_conservation_and_mirror_symmetry():
+    # periodic: sum of the averages of rho is conserved
+    pb = ai.entropy_wave1d(40, amp=0.5)
+    pb.kappa = 1.0
+    U = ai.dofs1(pb)
+    m0 = U[0][0].sum()
+    for _ in range(10):
+        U, _ = oracle.step1(pb, U)
+    assert abs(U[0][0].sum() - m0) <= 1e-13 * abs(m0)
+    # the mirror image of a Riemann problem evolves into the mirror image (v1, B1 odd).
+    # With the sensor off: the modified Ducros ratio of Sec. 3.4 is O(1)-sensitive
+    # where div v and curl v are rounding noise, and the limiter's sum over the two
+    # faces is formed in mirrored order, so with kappa > 0 the two runs part at the
+    # noise floor (the first Riemann problem shows it within a step).
+    for pb in (ai.riemann_rj(60), ai.riemann_2(60), ai.blast1d(60)):
+        pb.kappa = 0.0
+        U = ai.dofs1(pb)
+        A, B = U, ai.mirror1d(U)
+        for _ in range(5):
+            A, dta = oracle.step1(pb, A)
+            B, dtb = oracle.step1(pb, B)
+            assert dta == pytest.approx(dtb, rel=1e-15)
+        for a, b in zip(ai.mirror1d(A), B):
+            for k in range(8):
+                assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(np.abs(b).max(), 1e-300)
+
+
+def test_1d_positivity_and_pp_necessity():
+    """The strong 1D blast leaves the admissible set in its first step without the
+    PP limiters and stays in it with them (the limiters act)."""
+    pb = ai.blast1d(64)
+    V, _ = oracle.step1(pb, ai.dofs1(pb), pp_on=False)
+    bad = any((not np.isfinite(a).all()) or _prims1(a, pb.gamma)[1].min() <= 0 or a[0].min() <= 0 for a in V)
+    assert bad
+    U = ai.dofs1(pb)
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    for _ in range(30):
+        U, _ = oracle.step1(pb, U, stats=st)
+        for a in U:
+            rho, p = _prims1(a, pb.gamma)
+            assert rho.min() > 0 and p.min() > 0
+    assert st[oracle.STAT_NAMES.index("nonadmissible")] == 0
+    assert st[oracle.STAT_NAMES.index("point_limited")] + st[oracle.STAT_NAMES.index("lambda_lt1")] > 0
+
+
+def test_1d_riemann_problems_stay_admissible():
+    for pb in (ai.riemann_rj(200), ai.riemann_2(200)):
+        U = ai.dofs1(pb)
+        t = 0.0
+        while t < 0.05:
+            U, dt = oracle.step1(pb, U)
+            t += dt
+        for a in U:
+            rho, p = _prims1(a, pb.gamma)
+            assert rho.min() > 0 and p.min() > 0
+        # B1 is constant in 1D
+        assert np.abs(U[0][4] - U[0][4][0]).max() == 0.0
