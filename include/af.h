@@ -273,6 +273,40 @@ int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, double x1, d
  * roofline of the kernels, which are bound by the FP64 pipe. */
 int af_probe_fp64(void *stream, double *tflops);
 
+/* ---------------------------------------------------------------------------
+ * The 1D scheme (Sec. 4: the 1D tests use the 1D AF scheme with the LLF FVS
+ * and without the Godunov-Powell source term; B1 is constant).  Reading: the
+ * scheme of Sec. 2-3 restricted to one dimension.  Degrees of freedom: cell
+ * averages [8][n] (class 0) and interface point values [8][nf] (class 1;
+ * point f at x0 + f dx; nf = n periodic, n + 1 outflow).  Per stage: the
+ * parabola centre value (6 Ubar - U_L - U_R)/4 limited by Remark 3.2; the LLF
+ * FVS point update on the line (point f-1, centre f-1, point f, centre f,
+ * point f+1); the Sec. 3.3 point limiter with the LLF state between
+ * neighbouring points; the face flux F1 of the face point value blended with
+ * the LLF flux of the adjacent averages by theta^s (Sec. 3.4, y-differences
+ * zero); the Sec. 3.2 flux limiter with the faces L, R; Remark 4.1.  dt =
+ * cfl dx / max varrho_1.  Conventions, parameters (af_params; the source
+ * switches are ignored), counters and errors as for af_ctx.
+ * ------------------------------------------------------------------------- */
+typedef struct af1d_ctx af1d_ctx;
+int af1d_create(int n, double gamma, int bc, af1d_ctx **out);   /* n >= 4; domain [0,1] */
+int af1d_set_domain(af1d_ctx *ctx, double x0, double x1);
+int af1d_set_params(af1d_ctx *ctx, const af_params *p);
+int af1d_set_stream(af1d_ctx *ctx, void *stream);
+/* *len = n (cls 0, averages) or nf (cls 1, point values) */
+int af1d_sizes(const af1d_ctx *ctx, int cls, int *len);
+int af1d_set_state(af1d_ctx *ctx, const double *const U[2], int on_device);
+int af1d_get_state(af1d_ctx *ctx, double *const U[2], int on_device);
+/* the output of the most recent stage (as af_get_stage) */
+int af1d_get_stage(af1d_ctx *ctx, double *const U[2], int on_device);
+int af1d_dt(af1d_ctx *ctx, double *dt_out, int on_device);
+/* stage s in {0,1,2} as af_stage; dt NULL uses the last af1d_dt / af1d_step value */
+int af1d_stage(af1d_ctx *ctx, int s, const double *dt, int on_device);
+int af1d_step(af1d_ctx *ctx, double *dt_used, int on_device);
+int af1d_status(af1d_ctx *ctx, long long *counters, int reset);
+const char *af1d_last_error(const af1d_ctx *ctx);
+void af1d_destroy(af1d_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -110,6 +110,22 @@ def _lib():
             lib.af_batch_destroy.restype = None
             lib.af_rhs_noalloc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double,
                                            C.c_double, C.c_double, pp, pp, vp]
+            lib.af1d_create.argtypes = [C.c_int, C.c_double, C.c_int, C.POINTER(C.c_void_p)]
+            lib.af1d_set_domain.argtypes = [vp, C.c_double, C.c_double]
+            lib.af1d_set_params.argtypes = [vp, C.POINTER(af_params)]
+            lib.af1d_set_stream.argtypes = [vp, vp]
+            lib.af1d_sizes.argtypes = [vp, C.c_int, ip]
+            lib.af1d_set_state.argtypes = [vp, pp, C.c_int]
+            lib.af1d_get_state.argtypes = [vp, pp, C.c_int]
+            lib.af1d_get_stage.argtypes = [vp, pp, C.c_int]
+            lib.af1d_dt.argtypes = [vp, vp, C.c_int]
+            lib.af1d_stage.argtypes = [vp, C.c_int, vp, C.c_int]
+            lib.af1d_step.argtypes = [vp, vp, C.c_int]
+            lib.af1d_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+            lib.af1d_last_error.argtypes = [vp]
+            lib.af1d_last_error.restype = C.c_char_p
+            lib.af1d_destroy.argtypes = [vp]
+            lib.af1d_destroy.restype = None
             _LIB = lib
         return _LIB
 
@@ -556,6 +572,171 @@ class Solver:
     def close(self):
         if self.ctx:
             af_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# The 1D scheme (af1d_*): states are [averages [8, n], point values [8, nf]]
+# ---------------------------------------------------------------------------
+def _check1d(ctx, rc: int):
+    if rc != AF_OK:
+        raise AFError(rc, _lib().af1d_last_error(ctx).decode() if ctx else "")
+
+
+def af1d_create(n: int, gamma: float, bc: int = AF_BC_PERIODIC):
+    h = C.c_void_p()
+    rc = _lib().af1d_create(n, gamma, bc, C.byref(h))
+    if rc != AF_OK:
+        raise AFError(rc, "af1d_create failed")
+    return h
+
+
+def af1d_sizes(ctx):
+    a, b = C.c_int(), C.c_int()
+    _check1d(ctx, _lib().af1d_sizes(ctx, 0, C.byref(a)))
+    _check1d(ctx, _lib().af1d_sizes(ctx, 1, C.byref(b)))
+    return a.value, b.value
+
+
+def _marshal1d(ctx, U, out: bool = False, device: bool = True):
+    n, nf = af1d_sizes(ctx)
+    shapes = [(8, n), (8, nf)]
+    if U is None:
+        if device:
+            torch = _torch()
+            U = [torch.empty(s, dtype=torch.float64, device="cuda") for s in shapes]
+        else:
+            U = [np.empty(s) for s in shapes]
+    keep = []
+    ptrs = []
+    on_dev = int(_is_tensor(U[0]) and U[0].is_cuda)
+    for u, s in zip(U, shapes):
+        if on_dev:
+            if tuple(u.shape) != s or not u.is_contiguous():
+                raise ValueError("1D array must be a contiguous %s tensor" % (s,))
+            ptrs.append(u.data_ptr())
+        else:
+            a = u if out else np.ascontiguousarray(u, dtype=np.float64)
+            if a.shape != s:
+                raise ValueError("1D array must be %s, got %s" % (s, a.shape))
+            keep.append(a)
+            ptrs.append(a.ctypes.data)
+    return U, _ptr_array(ptrs), on_dev, keep
+
+
+def af1d_set_domain(ctx, x0: float, x1: float) -> None:
+    _check1d(ctx, _lib().af1d_set_domain(ctx, float(x0), float(x1)))
+
+
+def af1d_set_stream(ctx, stream=None) -> None:
+    _check1d(ctx, _lib().af1d_set_stream(ctx, C.c_void_p(stream.cuda_stream if stream is not None else 0)))
+
+
+def af1d_set_params(ctx, cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True) -> None:
+    p = af_params(cfl, kappa, int(pp_on), 0, 0)
+    _check1d(ctx, _lib().af1d_set_params(ctx, C.byref(p)))
+
+
+def af1d_set_state(ctx, U) -> None:
+    _, ptrs, dev, keep = _marshal1d(ctx, U)
+    _check1d(ctx, _lib().af1d_set_state(ctx, ptrs, dev))
+    del keep
+
+
+def af1d_get_state(ctx, out=None, device: bool = True):
+    out, ptrs, dev, keep = _marshal1d(ctx, out, out=True, device=device)
+    _check1d(ctx, _lib().af1d_get_state(ctx, ptrs, dev))
+    return out
+
+
+def af1d_get_stage(ctx, out=None, device: bool = True):
+    out, ptrs, dev, keep = _marshal1d(ctx, out, out=True, device=device)
+    _check1d(ctx, _lib().af1d_get_stage(ctx, ptrs, dev))
+    return out
+
+
+def af1d_dt(ctx) -> float:
+    d = C.c_double()
+    _check1d(ctx, _lib().af1d_dt(ctx, C.cast(C.byref(d), C.c_void_p), 0))
+    return d.value
+
+
+def af1d_stage(ctx, s: int, dt=None) -> None:
+    if dt is None:
+        rc = _lib().af1d_stage(ctx, s, None, 0)
+    elif _is_tensor(dt) and dt.is_cuda:
+        rc = _lib().af1d_stage(ctx, s, dt.data_ptr(), 1)
+    else:
+        v = C.c_double(float(dt))
+        rc = _lib().af1d_stage(ctx, s, C.cast(C.byref(v), C.c_void_p), 0)
+    _check1d(ctx, rc)
+
+
+def af1d_step(ctx, dt_out=None):
+    if dt_out is False:
+        _check1d(ctx, _lib().af1d_step(ctx, None, 0))
+        return None
+    d = C.c_double()
+    _check1d(ctx, _lib().af1d_step(ctx, C.cast(C.byref(d), C.c_void_p), 0))
+    return d.value
+
+
+def af1d_status(ctx, reset: bool = False):
+    cnt = (C.c_longlong * AF_NSTAT)()
+    rc = _lib().af1d_status(ctx, cnt, int(reset))
+    return rc, dict(zip(STAT_NAMES, [int(v) for v in cnt]))
+
+
+def af1d_last_error(ctx) -> str:
+    return _lib().af1d_last_error(ctx).decode()
+
+
+def af1d_destroy(ctx) -> None:
+    if ctx:
+        _lib().af1d_destroy(ctx)
+
+
+class Solver1D:
+    """A 1D run (af1d_*): n cells, gamma, periodic or outflow, on [x0, x1]."""
+
+    def __init__(self, n: int, gamma: float, bc: int = AF_BC_PERIODIC, domain=(0.0, 1.0), cfl: float = 0.2,
+                 kappa: float = 0.0, pp_on: bool = True, stream=None):
+        self.ctx = af1d_create(n, gamma, bc)
+        af1d_set_domain(self.ctx, domain[0], domain[1])
+        af1d_set_params(self.ctx, cfl, kappa, pp_on)
+        if stream is not None:
+            af1d_set_stream(self.ctx, stream)
+
+    def set_state(self, U):
+        af1d_set_state(self.ctx, U)
+
+    def get_state(self, out=None, device: bool = True):
+        return af1d_get_state(self.ctx, out, device)
+
+    def get_stage(self, out=None, device: bool = True):
+        return af1d_get_stage(self.ctx, out, device)
+
+    def dt(self):
+        return af1d_dt(self.ctx)
+
+    def stage(self, s: int, dt=None):
+        af1d_stage(self.ctx, s, dt)
+
+    def step(self, dt_out=None):
+        return af1d_step(self.ctx, dt_out)
+
+    def status(self, reset: bool = False):
+        return af1d_status(self.ctx, reset)
+
+    def close(self):
+        if self.ctx:
+            af1d_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

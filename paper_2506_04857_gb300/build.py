@@ -13,8 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libaf.so")
-SOURCES = ["af_kernels.cu", "af_adjoint.cu", "af_api.cu", "af_batch.cu", "af_noalloc.cu"]
-HEADERS = ["af_internal.h", "af_math.cuh", "af_device.cuh"]
+SOURCES = ["af_kernels.cu", "af_adjoint.cu", "af_api.cu", "af_batch.cu", "af_noalloc.cu", "af_api1d.cu"]
+HEADERS = ["af_internal.h", "af_math.cuh", "af_device.cuh", "af_kernels1d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

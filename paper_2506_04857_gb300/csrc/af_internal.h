@@ -88,6 +88,10 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
+// the 1D scheme (af_kernels1d.cuh) on the 2D structures with ny = 1: one stage
+// out = a U^n + b FE(U^s) (the dt pass first when reduce_dt), and the dt pass alone
+void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s);
+void af_launch_dt1d(const AfDev &d, const AfGrid &g, cudaStream_t s);
 // divergence measures of Example 4.4 of the state bound in d.us into out[2]
 // (device); partials: 2 * af_divb_nblocks(g) doubles
 int af_divb_nblocks(const AfGrid &g);

@@ -1376,3 +1376,5 @@ int af_batch_occupancy(int pass, dim3 block) {
   }
   return n > 0 ? n : 1;
 }
+
+#include "af_kernels1d.cuh"
