@@ -292,8 +292,9 @@ def sensor_phi(c, e, w, n, s, gamma, dx, dy) -> np.ndarray:
 
 
 def step_complex(pb, U_re, U_im, dt, **kw):
-    """One SSP-RK3 step of the complex state U_re + i U_im with fixed dt
-    (complex-step differentiation).  Returns (re, im, limiter events)."""
+    """One SSP-RK3 step of the complex state U_re + i U_im (complex-step
+    differentiation) with the fixed real dt, or with dt <= 0 the step's own dt
+    of the complex state.  Returns (re, im, limiter events)."""
     P = params_for(pb, **kw)
     re = [a.copy() for a in _check(U_re, pb.nx, pb.ny, pb.bc)]
     im = [a.copy() for a in _check(U_im, pb.nx, pb.ny, pb.bc)]

@@ -1744,8 +1744,10 @@ int or1d_step(const or_params *p, int n, double *const *U, double dt_in, double 
 }
 
 #ifdef AF_ORACLE_COMPLEX
-// One SSP-RK3 step of the complex state (re[cls], im[cls]) with the fixed time
-// step dt (complex-step differentiation; dt is not perturbed).
+// One SSP-RK3 step of the complex state (re[cls], im[cls]) (complex-step
+// differentiation).  dt > 0: that fixed, real time step; dt <= 0: the step's
+// own dt of the complex state (the A16 formula in complex arithmetic, the
+// maxima taken by real part), so that the derivative includes d(dt)/dU.
 int or_step_cs(const or_params *p, int nx, int ny, double *const *re, double *const *im, double dt) {
   Ctx C;
   make_ctx(p, nx, ny, C);
@@ -1762,9 +1764,10 @@ int or_step_cs(const or_params *p, int nx, int ny, double *const *re, double *co
   }
   long long loc[ST_NSTATS] = {0};
   State S1, S2, S3;
-  stage(C, Sn, Sn, real(dt), real(0.0), real(1.0), S1, loc);
-  stage(C, Sn, S1, real(dt), real(3.0) / real(4.0), real(1.0) / real(4.0), S2, loc);
-  stage(C, Sn, S2, real(dt), real(1.0) / real(3.0), real(2.0) / real(3.0), S3, loc);
+  const real h = dt > 0.0 ? real(dt) : compute_dt(C, Sn);
+  stage(C, Sn, Sn, h, real(0.0), real(1.0), S1, loc);
+  stage(C, Sn, S1, h, real(3.0) / real(4.0), real(1.0) / real(4.0), S2, loc);
+  stage(C, Sn, S2, h, real(1.0) / real(3.0), real(2.0) / real(3.0), S3, loc);
   for (int cls = 0; cls < 4; ++cls) {
     int ex = C.ext[cls][0], ey = C.ext[cls][1];
     for (int k = 0; k < 8; ++k)

@@ -702,3 +702,27 @@ def test_1d_riemann_problems_stay_admissible():
             assert rho.min() > 0 and p.min() > 0
         # B1 is constant in 1D
         assert np.abs(U[0][4] - U[0][4][0]).max() == 0.0
+
+
+def test_complex_step_with_the_states_own_dt():
+    """The complex-step build with dt <= 0 differentiates through dt(U): it
+    matches central differences of the oracle's own step (dt recomputed), and
+    differs from the frozen-dt derivative."""
+    pb = ai.perturbed_vortex(16, seed=2)
+    U = ai.dofs(pb)
+    d = ai.smooth_direction(pb, seed=4)
+    h = 1e-30
+    re, im, act = oracle.step_complex(pb, U, [h * x for x in d], 0.0)
+    assert act == 0
+    V, dt = oracle.step(pb, U)
+    for a, b in zip(re, V):
+        assert np.abs(a - b).max() <= 1e-14 * np.abs(b).max()
+    # a step of 1e-7 |U| stays clear of the kinks of the maxima (LLF alpha, dt)
+    eps = 1e-7 * math.sqrt(sum(float((u * u).sum()) for u in U))
+    Vp, _ = oracle.step(pb, [u + eps * x for u, x in zip(U, d)])
+    Vm, _ = oracle.step(pb, [u - eps * x for u, x in zip(U, d)])
+    scale = max(np.abs((a - b) / (2 * eps)).max() for a, b in zip(Vp, Vm))
+    err = max(np.abs(c / h - (a - b) / (2 * eps)).max() for c, a, b in zip(im, Vp, Vm))
+    assert err <= 1e-7 * scale
+    _, im_frozen, _ = oracle.step_complex(pb, U, [h * x for x in d], dt)
+    assert max(np.abs(a - b).max() for a, b in zip(im, im_frozen)) / h >= 1e-6 * scale
