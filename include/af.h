@@ -169,9 +169,16 @@ int af_rhs_vjp(af_ctx *ctx, const double *const v[4], double *const out[4], int 
  * returns AF_EINVAL (lam_out then holds no gradient).  AF_ADJ_RECORDED: the
  * caller has established, from the counters of the forward step (af_status),
  * that no limiter acted in its last stage, which is then not recomputed.
+ * AF_ADJ_DT: dt is not held fixed but differentiated as the function of U^n
+ * that af_step forms, dt = cfl / (M1/dx + M2/dy) with M_l = max varrho_l:
+ * lam_out gains mu d(dt)/dU^n, mu = lam_in . dU^{n+1}/d(dt) (from the stage
+ * increments), at the DoFs attaining M1 and M2 (a subgradient where the
+ * maximum is not unique: the first such DoF in class, then row-major order).
+ * It implies the recomputation of the last stage.  Meaningful only when the
+ * forward step took its dt from U^n.
  * lam_out may alias lam_in.  The state is not advanced.  The call
  * synchronises the stream once, at its end. */
-enum { AF_ADJ_RECORDED = 1 };
+enum { AF_ADJ_RECORDED = 1, AF_ADJ_DT = 2 };
 int af_adjoint_step(af_ctx *ctx, const double *dt, int dt_on_device, const double *const lam_in[4],
                     double *const lam_out[4], int on_device, int flags);
 

@@ -33,6 +33,7 @@ AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
 AF_OK, AF_EINVAL, AF_ECUDA, AF_ENOMEM, AF_ENONPHYS, AF_EBOUNDS, AF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 AF_NSTAT = 11
 AF_ADJ_RECORDED = 1
+AF_ADJ_DT = 2
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
               "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
 _CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
@@ -278,15 +279,17 @@ def af_rhs_vjp(ctx, v, out=None, device: bool = True):
     return out
 
 
-def af_adjoint_step(ctx, dt, lam, out=None, device: bool = True, recorded: bool = False):
+def af_adjoint_step(ctx, dt, lam, out=None, device: bool = True, recorded: bool = False,
+                    dt_sensitivity: bool = False):
     """lambda^n = (dU^{n+1}/dU^n)^T lambda^{n+1} for one step from the current state with time step dt
     (a float or a one-element CUDA float64 tensor).  recorded=True (AF_ADJ_RECORDED): the caller has
-    checked, from the forward step's counters, that no limiter acted in its last stage."""
+    checked, from the forward step's counters, that no limiter acted in its last stage.
+    dt_sensitivity=True (AF_ADJ_DT): dt is differentiated as the function of U^n that af_step forms."""
     ptrs, dev, keep = _marshal_in(ctx, lam)
     out, optrs, odev = _outputs(ctx, out, device)
     if dev != odev:
         raise ValueError("lam and out must both be on the device or both on the host")
-    flags = AF_ADJ_RECORDED if recorded else 0
+    flags = (AF_ADJ_RECORDED if recorded else 0) | (AF_ADJ_DT if dt_sensitivity else 0)
     if _is_tensor(dt) and dt.is_cuda:
         rc = _lib().af_adjoint_step(ctx, dt.data_ptr(), 1, ptrs, optrs, dev, flags)
     else:

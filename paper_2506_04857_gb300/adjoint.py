@@ -5,7 +5,10 @@ a checkpoint of the state every `checkpoint_every` steps.  It also records,
 from the limiter counters, whether every positivity limiter stayed inactive.
 Its backward pass recomputes each segment from its checkpoint (with the
 recorded dt) and applies af_adjoint_step in reverse, so gradients are those of
-the discrete scheme with dt held fixed.  The transpose is that of the smooth
+the discrete scheme with dt held fixed, or, with dt_sensitivity=True, with
+every step's dt differentiated as the function of its state that af_step
+forms (dt = cfl / (max varrho_1/dx + max varrho_2/dy), a subgradient at the
+maximising DoFs).  The transpose is that of the smooth
 branch: shock sensor off (kappa = 0) and every positivity limiter inactive;
 backward raises when the forward pass left that branch.
 
@@ -68,8 +71,9 @@ class AFSteps(torch.autograd.Function):
     """out = U after n steps of solver from U0 (four CUDA float64 tensors)."""
 
     @staticmethod
-    def forward(ctx, solver: Solver, nsteps: int, checkpoint_every: int, *U0):
+    def forward(ctx, solver: Solver, nsteps: int, checkpoint_every: int, dt_sensitivity: bool, *U0):
         ctx.solver = solver
+        ctx.dt_sensitivity = bool(dt_sensitivity)
         ctx.nsteps = nsteps
         ctx.every = max(1, int(checkpoint_every))
         dts = torch.empty(max(nsteps, 1), dtype=torch.float64, device=U0[0].device)
@@ -108,10 +112,12 @@ class AFSteps(torch.autograd.Function):
                 af_stage(s.ctx, 2, dt)
             for n in reversed(range(n0, n1)):
                 af_set_state(s.ctx, states[n - n0])
-                lam = af_adjoint_step(s.ctx, ctx.dts[n:n + 1], lam, recorded=True)
-        return (None, None, None) + tuple(lam)
+                lam = af_adjoint_step(s.ctx, ctx.dts[n:n + 1], lam, recorded=True,
+                                      dt_sensitivity=ctx.dt_sensitivity)
+        return (None, None, None, None) + tuple(lam)
 
 
-def af_steps(solver: Solver, U0: List[torch.Tensor], nsteps: int, checkpoint_every: int = 20):
+def af_steps(solver: Solver, U0: List[torch.Tensor], nsteps: int, checkpoint_every: int = 20,
+             dt_sensitivity: bool = False):
     """Differentiable n-step solve (see AFSteps)."""
-    return list(AFSteps.apply(solver, nsteps, checkpoint_every, *U0))
+    return list(AFSteps.apply(solver, nsteps, checkpoint_every, dt_sensitivity, *U0))

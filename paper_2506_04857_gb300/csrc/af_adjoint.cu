@@ -622,10 +622,163 @@ __global__ void __launch_bounds__(128) k_adj3(const __grid_constant__ AfGrid g, 
 
 inline dim3 grid3(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 3) / 4, 4); }
 
+// ---------------------------------------------------------------------------
+// Sensitivity to dt.  dt = cfl / (M1/dx + M2/dy), M_l = max varrho_l over the
+// DoFs of U^n, so dJ/dU^n gains mu * d(dt)/dU^n with mu = dJ/d(dt) and
+// d(dt)/dU = -(dt^2/cfl) (dM1/dU / dx + dM2/dU / dy), dM_l/dU = d varrho_l / dU
+// at the DoF attaining the maximum (a subgradient where it is not unique: the
+// first such DoF in class-then-index order).  On the smooth branch FE(U) =
+// U + dt L(U), so with the reverse-sweep variables
+//   mu dt = 2/3 L3.(FE(U2) - U2) + 1/4 L2.(FE(U1) - U1) + L1.(FE(U0) - U0),
+//   FE(U0) = U1,  FE(U1) = 4 U2 - 3 U0,  FE(U2) = (3 U3 - U0)/2.
+// ---------------------------------------------------------------------------
+struct DtVec {
+  const double *L3[4], *L2[4], *L1[4], *U0[4], *U1[4], *U2[4], *U3[4];
+  long long len[4];
+};
+
+__global__ void __launch_bounds__(256) k_dt_dot(const __grid_constant__ DtVec v, double *partials) {
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int c = 0; c < 4; ++c)
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < v.len[c]; t += stride) {
+      const double u0 = v.U0[c][t], u1 = v.U1[c][t], u2 = v.U2[c][t], u3 = v.U3[c][t];
+      const double fe2 = fma(1.5, u3, -0.5 * u0) - u2;
+      const double fe1 = fma(4.0, u2, fma(-3.0, u0, -u1));
+      const double fe0 = u1 - u0;
+      acc = fma(2.0 / 3.0, v.L3[c][t] * fe2, acc);
+      acc = fma(0.25, v.L2[c][t] * fe1, acc);
+      acc = fma(v.L1[c][t], fe0, acc);
+    }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+// the larger varrho wins; equal values: the smaller DoF id (class << 28 | index)
+__device__ __forceinline__ void better(double &bv, long long &bi, double v, long long i) {
+  if (v > bv || (v == bv && i < bi)) { bv = v; bi = i; }
+}
+
+// per block: the DoF of U^n with the largest varrho_1 and varrho_2 (point data set of U^n bound in d)
+__global__ void __launch_bounds__(256) k_dt_argmax(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                                   double *pv, long long *pi) {
+  double b1 = -1.0, b2 = -1.0;
+  long long i1 = 1LL << 62, i2 = 1LL << 62;
+  const long long PS = (long long)g.nxa * g.nya, stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < PS; t += stride) {
+    const int i = (int)(t % g.nxa), j = (int)(t / g.nxa);
+    for (int c = 0; c < 4; ++c) {
+      if (i >= g.ex[c] || j >= g.ey[c]) continue;
+      const long long id = ((long long)c << 28) | ((long long)j * g.ex[c] + i);
+      double s1, s2;
+      const double *w = d.pd[c];
+      if (c == 0) {
+        s1 = absd(w[QA_V1 * PS + t]) + w[QA_CF1 * PS + t];
+        s2 = absd(w[QA_V2 * PS + t]) + w[QA_CF2 * PS + t];
+      } else {
+        s1 = w[QP_SR1 * PS + t];
+        s2 = w[QP_SR2 * PS + t];
+      }
+      better(b1, i1, s1, id);
+      better(b2, i2, s2, id);
+    }
+  }
+  __shared__ double sv[2][256];
+  __shared__ long long si[2][256];
+  sv[0][threadIdx.x] = b1; si[0][threadIdx.x] = i1;
+  sv[1][threadIdx.x] = b2; si[1][threadIdx.x] = i2;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      for (int l = 0; l < 2; ++l) better(sv[l][threadIdx.x], si[l][threadIdx.x], sv[l][threadIdx.x + h], si[l][threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int l = 0; l < 2; ++l) {
+      pv[2 * blockIdx.x + l] = sv[l][0];
+      pi[2 * blockIdx.x + l] = si[l][0];
+    }
+}
+
+// one block: sums the dot partials, reduces the argmax partials, and adds
+// mu * d(dt)/dU at the two maximising DoFs to lambda (class pointers)
+__global__ void __launch_bounds__(256) k_dt_apply(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                                  const double *dpart, const double *pv, const long long *pi, int nb,
+                                                  const __grid_constant__ OVec4 lam, double *mu_out) {
+  __shared__ double sd[256], sv[2][256];
+  __shared__ long long si[2][256];
+  double a = 0.0, b1 = -1.0, b2 = -1.0;
+  long long i1 = 1LL << 62, i2 = 1LL << 62;
+  for (int k = threadIdx.x; k < nb; k += 256) {
+    a += dpart[k];
+    better(b1, i1, pv[2 * k], pi[2 * k]);
+    better(b2, i2, pv[2 * k + 1], pi[2 * k + 1]);
+  }
+  sd[threadIdx.x] = a;
+  sv[0][threadIdx.x] = b1; si[0][threadIdx.x] = i1;
+  sv[1][threadIdx.x] = b2; si[1][threadIdx.x] = i2;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sd[threadIdx.x] += sd[threadIdx.x + h];
+      for (int l = 0; l < 2; ++l) better(sv[l][threadIdx.x], si[l][threadIdx.x], sv[l][threadIdx.x + h], si[l][threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double dt = d.sc->dt, mudt = sd[0];
+  if (mu_out) *mu_out = mudt / dt;
+  for (int l = 0; l < 2; ++l) {
+    const long long id = si[l][0];
+    const int c = (int)(id >> 28);
+    const long long o = id & ((1LL << 28) - 1);
+    const size_t cs = (size_t)g.ex[c] * g.ey[c];
+    double U[8], grad[8];
+    for (int k = 0; k < 8; ++k) U[k] = d.un[c][k * cs + o];
+    Acc acc;
+    for (int k = 0; k < 8; ++k) acc.F[0][k] = acc.F[1][k] = acc.ps[k] = acc.U[k] = 0.0;
+    acc.sr[0] = acc.sr[1] = acc.B[0] = acc.B[1] = 0.0;
+    acc.sr[l] = 1.0;
+    pointwise_transpose(U, g, acc, grad);                       // d varrho_l / dU at that DoF
+    const double coef = -mudt * dt / g.cfl * (l == 0 ? g.rdx : g.rdy);   // mu * (-dt^2/cfl) / h_l
+    for (int k = 0; k < 8; ++k) lam.p[c][k * cs + o] = fma(coef, grad[k], lam.p[c][k * cs + o]);
+  }
+}
+
 }  // namespace
 
 int af_adj_nslots() { return A_N; }
 
+int af_dt_sens_nblocks() { return 152 * 4; }
+
+void af_launch_dt_dot(const AfGrid &g, const double *const *L3, const double *const *L2, const double *const *L1,
+                      const double *const *U0, const double *const *U1, const double *const *U2,
+                      const double *const *U3, double *work, cudaStream_t s) {
+  DtVec v;
+  for (int c = 0; c < 4; ++c) {
+    v.L3[c] = L3[c]; v.L2[c] = L2[c]; v.L1[c] = L1[c];
+    v.U0[c] = U0[c]; v.U1[c] = U1[c]; v.U2[c] = U2[c]; v.U3[c] = U3[c];
+    v.len[c] = 8LL * g.ex[c] * g.ey[c];
+  }
+  k_dt_dot<<<af_dt_sens_nblocks(), 256, 0, s>>>(v, work);
+}
+
+void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, double *work, double *mu_out,
+                        cudaStream_t s) {
+  const int nb = af_dt_sens_nblocks();
+  OVec4 lo;
+  for (int c = 0; c < 4; ++c) lo.p[c] = lam[c];
+  double *dpart = work, *pv = work + nb;
+  long long *pi = reinterpret_cast<long long *>(work + 3 * nb);
+  k_dt_argmax<<<nb, 256, 0, s>>>(d, g, pv, pi);
+  k_dt_apply<<<1, 256, 0, s>>>(d, g, dpart, pv, pi, nb, lo, mu_out);
+}
 void af_launch_vjp(const AfDev &d, const AfGrid &g, const AfAdjEpi &e, double *a, double *zc, double *const *tpart,
                    cudaStream_t s) {
   Vec4 vv;

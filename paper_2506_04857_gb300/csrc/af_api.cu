@@ -30,6 +30,7 @@ struct af_ctx {
   double *adj;            // af_adj_nslots() + 8 arrays per index point
   double *abuf;           // 6 state-sized buffers: lambda copies, VJP scratch, extra stage output
   double *adj_pd;         // two more point-data sets (point data and centre values of U^(0), U^(1))
+  double *dts;            // dt-sensitivity work (5 * af_dt_sens_nblocks() doubles) and mu
   unsigned long long *cnt_pin;   // pinned host copy of the counters before / after a recomputation
   double *divb_buf;       // divergence measures: 2 per block, then the 2 results (allocated on first use)
   int timing;
@@ -377,6 +378,7 @@ int ensure_adjoint(af_ctx *c) {
   if (cudaMalloc(&c->adj, sizeof(double) * PS * (af_adj_nslots() + 8)) != cudaSuccess ||
       cudaMalloc(&c->abuf, sizeof(double) * 6 * c->state_len) != cudaSuccess ||
       cudaMalloc(&c->adj_pd, sizeof(double) * 2 * kPdLen * PS) != cudaSuccess ||
+      cudaMalloc(&c->dts, sizeof(double) * (5 * (size_t)af_dt_sens_nblocks() + 1)) != cudaSuccess ||
       cudaMallocHost(&c->cnt_pin, sizeof(unsigned long long) * 32) != cudaSuccess) {
     cudaGetLastError();
     return fail(c, AF_ENOMEM, "adjoint workspace");
@@ -472,7 +474,8 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   if (!c || !dt || !lam_in || !lam_out) return AF_EINVAL;
   for (int cls = 0; cls < 4; ++cls)
     if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
-  if (flags & ~AF_ADJ_RECORDED) return fail(c, AF_EINVAL, "unknown flags %d", flags);
+  if (flags & ~(AF_ADJ_RECORDED | AF_ADJ_DT)) return fail(c, AF_EINVAL, "unknown flags %d", flags);
+  const bool with_dt = (flags & AF_ADJ_DT) != 0;
   if (c->g.kappa != 0.0)
     return fail(c, AF_EINVAL, "af_adjoint_step differentiates the scheme with the shock sensor off (kappa = 0)");
   CK(cudaSetDevice(c->device), "set device");
@@ -493,7 +496,7 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   bind_states(c, n, b1, b2);
   run_stage(c, RK_A[1], RK_B[1], 0);
   bind_pd(c, 2);
-  if (flags & AF_ADJ_RECORDED) {
+  if ((flags & AF_ADJ_RECORDED) && !with_dt) {
     bind_states(c, b2, b2, b2);
     af_launch_pointdata(c->dev, c->g, 0, c->stream);
   } else {
@@ -511,7 +514,7 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   class_ptrs(c, abuf(c, 2), L2);
   class_ptrs(c, abuf(c, 3), L1);
   class_ptrs(c, abuf(c, 4), W);
-  class_ptrs(c, abuf(c, 0), L0b);
+  class_ptrs(c, abuf(c, 1), L0b);   // the scratch of the last VJP; L3 stays readable
   if (!on_device) {
     rc = copy_in_buf(c, abuf(c, 0), lam_in, 0);
     if (rc) return rc;
@@ -531,14 +534,28 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   e1.e = 0.75;
   e1.f = 1.0 / 3.0;
   vjp_at(c, b1, 1, e1);
+  if (with_dt) {   // mu dt from L3, L2, L1 and the stage states, before the last VJP may overwrite L3
+    double *U[4][4];
+    class_ptrs(c, c->state[n], U[0]);
+    class_ptrs(c, c->state[b1], U[1]);
+    class_ptrs(c, c->state[b2], U[2]);
+    class_ptrs(c, abuf(c, 5), U[3]);
+    af_launch_dt_dot(c->g, L3, L2, L1, U[0], U[1], U[2], U[3], c->dts, c->stream);
+  }
   AfAdjEpi e0 = epi(L1, L0, 1.0, 1.0, dtp);
   for (int cls = 0; cls < 4; ++cls) e0.z1[cls] = W[cls];
   e0.c = 1.0;
   vjp_at(c, n, 0, e0);
+  if (with_dt) {
+    bind_pd(c, 0);
+    bind_states(c, n, n, n);
+    af_launch_dt_apply(c->dev, c->g, L0, c->dts, c->dts + 5 * (size_t)af_dt_sens_nblocks(), c->stream);
+    bind_pd(c, 2);
+  }
   CK(cudaGetLastError(), "adjoint launch");
   c->next_stage = 0;
   if (!on_device) {
-    rc = copy_out_buf(c, abuf(c, 0), lam_out, 0);
+    rc = copy_out_buf(c, abuf(c, 1), lam_out, 0);
     if (rc) return rc;
   }
   CK(cudaStreamSynchronize(c->stream), "synchronise");
@@ -646,6 +663,7 @@ void af_destroy(af_ctx *c) {
   if (c->st) cudaFree(c->st);
   if (c->adj) cudaFree(c->adj);
   if (c->adj_pd) cudaFree(c->adj_pd);
+  if (c->dts) cudaFree(c->dts);
   if (c->divb_buf) cudaFree(c->divb_buf);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);

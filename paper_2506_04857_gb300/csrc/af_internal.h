@@ -88,6 +88,18 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
+// sensitivity of one step to its dt (af_adjoint.cu), in two launches: the dot
+// product mu dt of the reverse-sweep variables with the stage increments
+// (before the last VJP, which may overwrite L3), then the maximising DoFs of
+// varrho_1, varrho_2 over U^n (point data of U^n bound in d, d.un = U^n) and
+// lam += mu d(dt)/dU^n there.  work: 5 * af_dt_sens_nblocks() doubles; mu_out
+// (device, may be NULL) receives mu = dJ/d(dt).
+int af_dt_sens_nblocks();
+void af_launch_dt_dot(const AfGrid &g, const double *const *L3, const double *const *L2, const double *const *L1,
+                      const double *const *U0, const double *const *U1, const double *const *U2,
+                      const double *const *U3, double *work, cudaStream_t s);
+void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, double *work, double *mu_out,
+                        cudaStream_t s);
 // the 1D scheme (af_kernels1d.cuh) on the 2D structures with ny = 1: one stage
 // out = a U^n + b FE(U^s) (the dt pass first when reduce_dt), and the dt pass alone
 void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s);
