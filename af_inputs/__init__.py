@@ -47,6 +47,13 @@ class Problem:
     kappa: float = 0.0
     cfl: float = 0.2
     t_end: float = 0.0
+    # outflow problems only: boundary kind of each side (left, right, bottom,
+    # top): 0 outflow, 1 reflective, 2 inflow (bottom/top) with the conserved
+    # inflow state inflow_U where inflow_lo < x < inflow_hi
+    sides: tuple = (0, 0, 0, 0)
+    inflow_lo: float = 0.0
+    inflow_hi: float = 0.0
+    inflow_U: tuple = None
 
     @property
     def dx(self) -> float:
@@ -285,6 +292,27 @@ def shock_cloud(n: int = 400, kappa: float = 1.0) -> Problem:
         return (rho, v1, _b(x, 0.0), _b(x, 0.0), _b(x, 0.0), b2, b3, p)
 
     return Problem("shock_cloud", n, n, 0.0, 1.0, 0.0, 1.0, OUTFLOW, 5.0 / 3.0, prim, kappa=kappa)
+
+
+REFLECT, INFLOW = 1, 2
+
+
+def jets(n: int = 200, ba: float = math.sqrt(20000.0), kappa: float = 2.0) -> Problem:
+    """MHD jets (Example 4.8): the left half [-0.5, 0] x [0, 1.5] on n x 3n
+    cells, gamma = 1.4; ambient rho = 0.1 gamma, p = 1, v = 0, B = (0, ba, 0);
+    the jet (rho, v1, v2, p) = (gamma, 0, 800, 1) enters through the bottom for
+    |x| < 0.05; reflective at x = 0, outflow on the other sides; T = 0.002.
+    Reading: the jet carries the ambient field B = (0, ba, 0)."""
+    g = 1.4
+    jet = prim_to_cons((g, 0.0, 800.0, 0.0, 0.0, ba, 0.0, 1.0), g)
+
+    def prim(x, y):
+        z = 0.0 * np.asarray(x, dtype=np.float64) + 0.0 * np.asarray(y, dtype=np.float64)
+        return (z + 0.1 * g, z, z, z, z, z + ba, z, z + 1.0)
+
+    return Problem("jets", n, 3 * n, -0.5, 0.0, 0.0, 1.5, OUTFLOW, g, prim, kappa=kappa, t_end=0.002,
+                   sides=(0, REFLECT, INFLOW, 0), inflow_lo=-0.05, inflow_hi=0.05,
+                   inflow_U=tuple(float(v) for v in jet))
 
 
 def constant(n: int = 16, ny: int | None = None, bc: int = PERIODIC, gamma: float = 5.0 / 3.0,

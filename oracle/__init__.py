@@ -34,12 +34,23 @@ KINDS = ["add", "mul", "div", "sqrt", "exp", "minmax", "cmp"]
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
                 ("y1", C.c_double), ("cfl", C.c_double), ("kappa", C.c_double), ("bc", C.c_int),
-                ("pp_on", C.c_int), ("src_cell_on", C.c_int), ("src_point_on", C.c_int)]
+                ("pp_on", C.c_int), ("src_cell_on", C.c_int), ("src_point_on", C.c_int),
+                ("side", C.c_int * 4), ("inflow_lo", C.c_double), ("inflow_hi", C.c_double),
+                ("inflow_U", C.c_double * 8)]
 
 
 def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, cfl=None) -> Params:
-    return Params(pb.gamma, pb.x0, pb.x1, pb.y0, pb.y1, pb.cfl if cfl is None else cfl,
-                  pb.kappa if kappa is None else kappa, pb.bc, int(pp_on), int(src_cell_on), int(src_point_on))
+    P = Params(pb.gamma, pb.x0, pb.x1, pb.y0, pb.y1, pb.cfl if cfl is None else cfl,
+               pb.kappa if kappa is None else kappa, pb.bc, int(pp_on), int(src_cell_on), int(src_point_on))
+    sides = getattr(pb, "sides", (0, 0, 0, 0))
+    for k in range(4):
+        P.side[k] = int(sides[k])
+    P.inflow_lo = float(getattr(pb, "inflow_lo", 0.0))
+    P.inflow_hi = float(getattr(pb, "inflow_hi", 0.0))
+    inU = getattr(pb, "inflow_U", None)
+    for k in range(8):
+        P.inflow_U[k] = float(inU[k]) if inU is not None else 0.0
+    return P
 
 
 def build(force: bool = False) -> None:

@@ -146,6 +146,14 @@ typedef struct {
   int pp_on;         // positivity-preserving limiters
   int src_cell_on;   // Godunov-Powell source in the cell-average update
   int src_point_on;  // Godunov-Powell source in the point-value update
+  // Per-side boundary kinds for bc = 1 (sides: 0 left, 1 right, 2 bottom, 3
+  // top): 0 outflow (mirror), 1 reflective (mirror with the normal components
+  // of the momentum and of B negated), 2 inflow (bottom/top only: ghost DoFs
+  // whose mirror point lies in inflow_lo < x < inflow_hi take inflow_U, the
+  // conserved inflow state; outflow elsewhere on that side).
+  int side[4];
+  double inflow_lo, inflow_hi;
+  double inflow_U[8];
 } or_params;
 
 // Stats slots (cumulative over the call).
@@ -168,6 +176,9 @@ enum {
 static const int G = 2;  // ghost width (the shock sensor reaches two cells)
 
 struct Ctx {
+  int side[4];       // per-side boundary kinds (bc = 1)
+  bool special;      // a reflective or inflow side is present
+  double x0, y0, in_lo, in_hi, inU[8];
   int nx, ny, bc;
   double dx, dy, gamma, cfl, kappa;
   int pp_on, src_cell_on, src_point_on;
@@ -188,6 +199,14 @@ static void make_ctx(const or_params *p, int nx, int ny, Ctx &C) {
   C.ext[1][0] = fx; C.ext[1][1] = ny;
   C.ext[2][0] = nx; C.ext[2][1] = fy;
   C.ext[3][0] = fx; C.ext[3][1] = fy;
+  C.x0 = p->x0; C.y0 = p->y0;
+  C.special = false;
+  for (int k = 0; k < 4; ++k) {
+    C.side[k] = p->bc == 0 ? 0 : p->side[k];
+    if (C.side[k] != 0) C.special = true;
+  }
+  C.in_lo = p->inflow_lo; C.in_hi = p->inflow_hi;
+  for (int k = 0; k < 8; ++k) C.inU[k] = p->inflow_U[k];
 }
 
 // Axis kind of each class: 0 = cell-centred index, 1 = face/node index.
@@ -226,6 +245,40 @@ static void ghost_fill(const Ctx &C, Arr &A, int cls) {
       if (i >= 0 && i < ex && j >= 0 && j < ey) continue;
       int si = map_idx(i, nx, AXK[cls][0], C.bc), sj = map_idx(j, ny, AXK[cls][1], C.bc);
       for (int k = 0; k < A.nc; ++k) A.at(C, k, i, j) = A.at(C, k, si, sj);
+    }
+}
+
+// Ghosts of an 8-component state on a class's index set, with the per-side
+// kinds.  A ghost index is mapped along x first (mirror; a reflective side
+// negates m1 and B1), then along y (mirror; a reflective side negates m2 and
+// B2; an inflow side gives the inflow state where the x coordinate of the
+// x-mapped index lies strictly inside the inflow range).  Reading: the paper
+// names the conditions only (Example 4.8).
+static void ghost_fill_state(const Ctx &C, Arr &A, int cls) {
+  if (!C.special) {
+    ghost_fill(C, A, cls);
+    return;
+  }
+  int ex = C.ext[cls][0], ey = C.ext[cls][1];
+  for (int j = -G; j < ey + G; ++j)
+    for (int i = -G; i < ex + G; ++i) {
+      if (i >= 0 && i < ex && j >= 0 && j < ey) continue;
+      int si = map_idx(i, C.nx, AXK[cls][0], C.bc), sj = map_idx(j, C.ny, AXK[cls][1], C.bc);
+      bool fx = false, fy = false, inflow = false;
+      if (i < 0 || i >= ex) fx = C.side[i < 0 ? 0 : 1] == 1;
+      if (j < 0 || j >= ey) {
+        const int sd = C.side[j < 0 ? 2 : 3];
+        fy = sd == 1;
+        if (sd == 2) {
+          const double x = C.x0 + (si + (AXK[cls][0] == 0 ? 0.5 : 0.0)) * C.dx;
+          inflow = x > C.in_lo && x < C.in_hi;
+        }
+      }
+      for (int k = 0; k < 8; ++k) {
+        real v = A.at(C, k, si, sj);
+        if ((fx && (k == 1 || k == 4)) || (fy && (k == 2 || k == 5))) v = real(0.0) - v;
+        A.at(C, k, i, j) = inflow ? real(C.inU[k]) : v;
+      }
     }
 }
 
@@ -504,8 +557,20 @@ struct PDGrid {
   PD &at(const Ctx &C, int i, int j) { return d[C.id(i, j)]; }
 };
 
-static void pd_ghost_fill(const Ctx &C, PDGrid &Pg, int cls) {
+// Point data of the ghost DoFs: copies of the mapped interior DoFs, or, with
+// reflective / inflow sides, the point data of the ghost states in A.
+static void pd_ghost_fill(const Ctx &C, PDGrid &Pg, int cls, Arr *A = nullptr) {
   int ex = C.ext[cls][0], ey = C.ext[cls][1];
+  if (C.special && A) {
+    for (int j = -G; j < ey + G; ++j)
+      for (int i = -G; i < ex + G; ++i) {
+        if (i >= 0 && i < ex && j >= 0 && j < ey) continue;
+        real U[8];
+        for (int k = 0; k < 8; ++k) U[k] = A->at(C, k, i, j);
+        point_data(U, C.gamma, Pg.at(C, i, j));
+      }
+    return;
+  }
   for (int j = -G; j < ey + G; ++j)
     for (int i = -G; i < ex + G; ++i) {
       if (i >= 0 && i < ex && j >= 0 && j < ey) continue;
@@ -544,7 +609,7 @@ static void compute_point_data(const Ctx &C, State &S, Work &W) {
         S.get(C, cls, i, j, U);
         point_data(U, C.gamma, W.pd[cls].at(C, i, j));
       }
-    pd_ghost_fill(C, W.pd[cls], cls);
+    pd_ghost_fill(C, W.pd[cls], cls, &S.c[cls]);
   }
 }
 
@@ -573,7 +638,7 @@ static void compute_centers(const Ctx &C, State &S, Work &W, long long *st) {
       for (int k = 0; k < 8; ++k) W.Uc.at(C, k, i, j) = out[k];
     }
   st[ST_CENTER_LIMITED] += nlim;
-  ghost_fill(C, W.Uc, 0);
+  ghost_fill_state(C, W.Uc, 0);
   set_phase(PH_POINTDATA);
   W.pdc.init(C);
 #ifndef AF_ORACLE_COUNT
@@ -585,7 +650,7 @@ static void compute_centers(const Ctx &C, State &S, Work &W, long long *st) {
       for (int k = 0; k < 8; ++k) U[k] = W.Uc.at(C, k, i, j);
       point_data(U, C.gamma, W.pdc.at(C, i, j));
     }
-  pd_ghost_fill(C, W.pdc, 0);
+  pd_ghost_fill(C, W.pdc, 0, &W.Uc);
 }
 
 // Sec. 2.3: the 5-point line through a point value and its LLF-FVS derivative
@@ -1089,7 +1154,7 @@ static real compute_dt(const Ctx &C, State &S) {
 // combination out = a Un + b FE(Us).
 static int stage(const Ctx &C, State &Un, State &Us, real dt, real a, real b, State &out, long long *st) {
   Work W;
-  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, Us.c[cls], cls);
+  for (int cls = 0; cls < 4; ++cls) ghost_fill_state(C, Us.c[cls], cls);
   compute_point_data(C, Us, W);
   compute_centers(C, Us, W, st);
   point_ho_updates(C, dt, W);
@@ -1119,7 +1184,7 @@ static int stage(const Ctx &C, State &Un, State &Us, real dt, real a, real b, St
 static void rhs(const Ctx &C, State &S, State &out) {
   Work W;
   long long st[ST_NSTATS] = {0};
-  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, S.c[cls], cls);
+  for (int cls = 0; cls < 4; ++cls) ghost_fill_state(C, S.c[cls], cls);
   compute_point_data(C, S, W);
   compute_centers(C, S, W, st);
   out.init(C);
@@ -1545,7 +1610,7 @@ int or_sensor(const or_params *p, int nx, int ny, const double *const *U, double
   load_state(C, U, S);
   long long st[ST_NSTATS] = {0};
   Work W;
-  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, S.c[cls], cls);
+  for (int cls = 0; cls < 4; ++cls) ghost_fill_state(C, S.c[cls], cls);
   compute_point_data(C, S, W);
   compute_sensor(C, W);
   compute_faces(C, W, st);
@@ -1572,7 +1637,7 @@ int or_divb(const or_params *p, int nx, int ny, const double *const *U, double *
   make_ctx(p, nx, ny, C);
   State S;
   load_state(C, U, S);
-  for (int cls = 0; cls < 4; ++cls) ghost_fill(C, S.c[cls], cls);
+  for (int cls = 0; cls < 4; ++cls) ghost_fill_state(C, S.c[cls], cls);
   Work W;
   long long st[ST_NSTATS] = {0};
   compute_centers(C, S, W, st);

@@ -726,3 +726,68 @@ def test_complex_step_with_the_states_own_dt():
     assert err <= 1e-7 * scale
     _, im_frozen, _ = oracle.step_complex(pb, U, [h * x for x in d], dt)
     assert max(np.abs(a - b).max() for a, b in zip(im, im_frozen)) / h >= 1e-6 * scale
+
+
+# ---------------------------------------------------------------------------
+# Reflective and inflow boundaries (Example 4.8)
+# ---------------------------------------------------------------------------
+def _blast_b2(nx, ny, x1):
+    """A blast with B = (0, 1, 0): mirror symmetric about x = 0 (v1, B1 odd)."""
+    def prim(x, y):
+        z = 0.0 * np.asarray(x, dtype=np.float64)
+        r2 = x * x + y * y
+        return (z + 1.0, z, z, z, z, z + 1.0, z, np.where(r2 < 0.13 ** 2, 10.0, 0.1) + z)   # no node on the circle
+    sides = (0, ai.REFLECT, 0, 0) if x1 == 0.0 else (0, 0, 0, 0)
+    return ai.Problem("blast_b2", nx, ny, -0.5, x1, -0.5, 0.5, ai.OUTFLOW, 5.0 / 3.0, prim, sides=sides)
+
+
+def test_reflective_boundary_is_the_mirror_plane():
+    """The half domain with a reflective side at x = 0 evolves like the left
+    half of the mirror-symmetric full domain (sensor off: see the 1D mirror pin)."""
+    m, ny = 10, 16
+    full, half = _blast_b2(2 * m, ny, 0.5), _blast_b2(m, ny, 0.0)
+    F, H = ai.dofs(full), ai.dofs(half)
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    for _ in range(4):
+        F, dtf = oracle.step(full, F, stats=st, kappa=0.0)
+        H, dth = oracle.step(half, H, kappa=0.0)
+        assert dth == pytest.approx(dtf, rel=1e-14)
+    assert st[oracle.STAT_NAMES.index("point_limited")] > 0     # the limiters take part
+    # averages and y-faces: columns 0..m-1; x-faces and corners: 0..m (the mirror plane included)
+    for c in range(4):
+        cols = H[c].shape[2]
+        a, b = H[c], F[c][:, :, :cols]
+        for k in range(8):
+            assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(np.abs(b).max(), 1e-300), (c, k)
+    # on the mirror plane v1 and B1 vanish
+    assert np.abs(H[1][1, :, m]).max() <= 1e-12 and np.abs(H[1][4, :, m]).max() <= 1e-12
+
+
+def test_inflow_of_the_free_stream_and_jets_need_pp():
+    pb = ai.jets(8)
+    # a uniform state equal to the inflow state stays uniform through all three kinds of side
+    uni = ai.Problem("jet_state", 8, 24, pb.x0, pb.x1, pb.y0, pb.y1, ai.OUTFLOW, pb.gamma,
+                     lambda x, y: tuple(0.0 * np.asarray(x) + v for v in (1.4, 0.0, 800.0, 0.0, 0.0, pb.prim(0.0, 0.0)[5], 0.0, 1.0)),
+                     sides=pb.sides, inflow_lo=pb.inflow_lo, inflow_hi=pb.inflow_hi, inflow_U=pb.inflow_U)
+    U0 = ai.dofs(uni)
+    U = U0
+    for _ in range(5):
+        U, _ = oracle.step(uni, U)
+    for a, b in zip(U, U0):
+        for k in range(8):
+            assert np.abs(a[k] - b[k]).max() <= 1e-12 * max(np.abs(b[k]).max(), 1.0)
+    # Example 4.8: the jets cannot be run without the PP limiters
+    def admissible(V):
+        return all(np.isfinite(a).all() and a[0].min() > 0 and pressure_field(a, pb.gamma).min() > 0 for a in V)
+    V = ai.dofs(pb)
+    ok = True
+    for _ in range(5):
+        V, _ = oracle.step(pb, V, pp_on=False)
+        ok = ok and admissible(V)
+    assert not ok
+    V = ai.dofs(pb)
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    for _ in range(10):
+        V, _ = oracle.step(pb, V, stats=st)
+        assert admissible(V)
+    assert st[oracle.STAT_NAMES.index("point_limited")] > 0
