@@ -89,6 +89,21 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out);
 /* Domain [x0,x1] x [y0,y1] (x1 > x0, y1 > y0); sets dx = (x1-x0)/nx, dy = (y1-y0)/ny. */
 int af_set_domain(af_ctx *ctx, double x0, double x1, double y0, double y1);
 
+/* Boundary kind of each side of an outflow grid (side[0] left, [1] right,
+ * [2] bottom, [3] top), for problems such as the jets of Example 4.8 (the
+ * paper names the conditions only; readings):
+ *   AF_SIDE_OUTFLOW    ghost DoFs mirror the interior across the side (default);
+ *   AF_SIDE_REFLECTIVE mirror, with the normal components of the momentum and
+ *                      of B negated (a symmetry plane);
+ *   AF_SIDE_INFLOW     bottom/top only: ghost DoFs whose mirror point has
+ *                      inflow_lo < x < inflow_hi take the conserved state
+ *                      inflow_U[8]; outflow elsewhere on that side.
+ * A ghost index is resolved along x first, then along y.  Periodic grids
+ * return AF_EINVAL.  The discrete adjoint (af_rhs_vjp, af_adjoint_step)
+ * rejects grids with reflective or inflow sides. */
+enum { AF_SIDE_OUTFLOW = 0, AF_SIDE_REFLECTIVE = 1, AF_SIDE_INFLOW = 2 };
+int af_set_boundary(af_ctx *ctx, const int side[4], double inflow_lo, double inflow_hi, const double inflow_U[8]);
+
 int af_set_params(af_ctx *ctx, const af_params *p);
 int af_get_params(const af_ctx *ctx, af_params *p);
 

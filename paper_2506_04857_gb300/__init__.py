@@ -34,6 +34,7 @@ AF_OK, AF_EINVAL, AF_ECUDA, AF_ENOMEM, AF_ENONPHYS, AF_EBOUNDS, AF_ETIMEOUT = 0,
 AF_NSTAT = 11
 AF_ADJ_RECORDED = 1
 AF_ADJ_DT = 2
+AF_SIDE_OUTFLOW, AF_SIDE_REFLECTIVE, AF_SIDE_INFLOW = 0, 1, 2
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
               "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
 _CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
@@ -71,6 +72,7 @@ def _lib():
             lib.af_create.argtypes = [C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_void_p)]
             lib.af_set_domain.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double]
             lib.af_set_params.argtypes = [vp, C.POINTER(af_params)]
+            lib.af_set_boundary.argtypes = [vp, ip, C.c_double, C.c_double, dp]
             lib.af_get_params.argtypes = [vp, C.POINTER(af_params)]
             lib.af_set_stream.argtypes = [vp, vp]
             lib.af_sizes.argtypes = [vp, C.c_int, ip, ip]
@@ -172,6 +174,13 @@ def af_set_params(ctx, cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True,
                   src_point_on: bool = True) -> None:
     p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on))
     _check(ctx, _lib().af_set_params(ctx, C.byref(p)))
+
+
+def af_set_boundary(ctx, sides, inflow_lo: float = 0.0, inflow_hi: float = 0.0, inflow_U=None) -> None:
+    """Per-side boundary kinds (left, right, bottom, top) of an outflow grid; see af.h."""
+    sd = (C.c_int * 4)(*[int(v) for v in sides])
+    u = (C.c_double * 8)(*([float(v) for v in inflow_U] if inflow_U is not None else [0.0] * 8))
+    _check(ctx, _lib().af_set_boundary(ctx, sd, float(inflow_lo), float(inflow_hi), u))
 
 
 def af_get_params(ctx) -> dict:
@@ -528,13 +537,18 @@ class Solver:
 
     def __init__(self, nx: int, ny: int, gamma: float, bc: int = AF_BC_PERIODIC, domain=(0.0, 1.0, 0.0, 1.0),
                  cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True, src_cell_on: bool = True,
-                 src_point_on: bool = True, stream=None):
+                 src_point_on: bool = True, stream=None, sides=None, inflow=None):
+        """sides: per-side boundary kinds (left, right, bottom, top) of an outflow grid;
+        inflow: (lo, hi, conserved state) for AF_SIDE_INFLOW sides."""
         self.ctx = af_create(nx, ny, gamma, bc)
         self.nx, self.ny, self.bc = nx, ny, bc
         af_set_domain(self.ctx, *domain)
         af_set_params(self.ctx, cfl, kappa, pp_on, src_cell_on, src_point_on)
         if stream is not None:
             af_set_stream(self.ctx, stream)
+        if sides is not None and any(sides):
+            lo, hi, U = inflow if inflow is not None else (0.0, 0.0, None)
+            af_set_boundary(self.ctx, sides, lo, hi, U)
 
     def sizes(self):
         return [af_sizes(self.ctx, c) for c in range(4)]

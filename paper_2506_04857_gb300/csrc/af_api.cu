@@ -10,6 +10,9 @@
 
 struct af_ctx {
   int device;
+  int side[4];            // per-side boundary kinds (af_set_boundary)
+  double in_lo, in_hi;
+  double *inflow_dev;     // inflow state and its point data (device)
   int nx, ny, bc;
   double gamma, x0, x1, y0, y1;
   af_params prm;
@@ -88,6 +91,14 @@ void refresh_grid(af_ctx *c) {
   g.pp_on = c->prm.pp_on;
   g.src_cell_on = c->prm.src_cell_on;
   g.src_point_on = c->prm.src_point_on;
+  g.special = 0;
+  for (int k = 0; k < 4; ++k) {
+    g.side[k] = c->bc == AF_BC_OUTFLOW ? c->side[k] : 0;
+    if (g.side[k]) g.special = 1;
+  }
+  g.x0 = c->x0;
+  g.in_lo = c->in_lo;
+  g.in_hi = c->in_hi;
 }
 
 const double *cls_ptr(const af_ctx *c, int buf, int cls) { return c->state[buf] + c->class_off[cls]; }
@@ -268,6 +279,38 @@ int af_set_domain(af_ctx *c, double x0, double x1, double y0, double y1) {
   return AF_OK;
 }
 
+int af_set_boundary(af_ctx *c, const int side[4], double inflow_lo, double inflow_hi, const double inflow_U[8]) {
+  if (!c || !side) return AF_EINVAL;
+  if (c->bc != AF_BC_OUTFLOW) return fail(c, AF_EINVAL, "per-side boundary kinds need an outflow (non-periodic) grid");
+  bool inflow = false;
+  for (int k = 0; k < 4; ++k) {
+    if (side[k] < AF_SIDE_OUTFLOW || side[k] > AF_SIDE_INFLOW) return fail(c, AF_EINVAL, "side %d: unknown kind", k);
+    if (side[k] == AF_SIDE_INFLOW && k < 2) return fail(c, AF_EINVAL, "inflow is supported on the bottom and top sides");
+    inflow = inflow || side[k] == AF_SIDE_INFLOW;
+  }
+  if (inflow && (!inflow_U || !(inflow_U[0] > 0.0))) return fail(c, AF_EINVAL, "inflow state missing or rho <= 0");
+  CK(cudaSetDevice(c->device), "set device");
+  for (int k = 0; k < 4; ++k) c->side[k] = side[k];
+  c->in_lo = inflow_lo;
+  c->in_hi = inflow_hi;
+  refresh_grid(c);
+  if (!c->inflow_dev) {
+    if (cudaMalloc(&c->inflow_dev, sizeof(double) * (8 + AF_NQP + AF_NQA)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, AF_ENOMEM, "inflow table");
+    }
+    CK(cudaMemset(c->inflow_dev, 0, sizeof(double) * (8 + AF_NQP + AF_NQA)), "clear inflow table");
+  }
+  if (inflow) {
+    CK(cudaMemcpy(c->inflow_dev, inflow_U, 8 * sizeof(double), cudaMemcpyHostToDevice), "inflow state");
+    af_launch_inflow_pd(c->g, c->inflow_dev, c->inflow_dev, c->stream);
+    CK(cudaGetLastError(), "inflow point data");
+    CK(cudaStreamSynchronize(c->stream), "synchronise");
+  }
+  c->dev.inflow = c->inflow_dev;
+  return AF_OK;
+}
+
 int af_set_params(af_ctx *c, const af_params *p) {
   if (!c || !p) return AF_EINVAL;
   if (!(p->cfl > 0.0) || !(p->kappa >= 0.0)) return fail(c, AF_EINVAL, "cfl must be > 0 and kappa >= 0");
@@ -443,6 +486,7 @@ int copy_out_buf(af_ctx *c, const double *src, double *const U[4], int on_device
 
 int af_rhs_vjp(af_ctx *c, const double *const v[4], double *const out[4], int on_device) {
   if (!c || !v || !out) return AF_EINVAL;
+  if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
   for (int cls = 0; cls < 4; ++cls)
     if (!v[cls] || !out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
   CK(cudaSetDevice(c->device), "set device");
@@ -475,6 +519,7 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   for (int cls = 0; cls < 4; ++cls)
     if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
   if (flags & ~(AF_ADJ_RECORDED | AF_ADJ_DT)) return fail(c, AF_EINVAL, "unknown flags %d", flags);
+  if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
   const bool with_dt = (flags & AF_ADJ_DT) != 0;
   if (c->g.kappa != 0.0)
     return fail(c, AF_EINVAL, "af_adjoint_step differentiates the scheme with the shock sensor off (kappa = 0)");
@@ -665,6 +710,7 @@ void af_destroy(af_ctx *c) {
   if (c->adj_pd) cudaFree(c->adj_pd);
   if (c->dts) cudaFree(c->dts);
   if (c->divb_buf) cudaFree(c->divb_buf);
+  if (c->inflow_dev) cudaFree(c->inflow_dev);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);
   for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);

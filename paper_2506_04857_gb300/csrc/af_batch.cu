@@ -91,6 +91,10 @@ void fill_grid(af_batch *b, int r) {
   g.pp_on = b->prm[r].pp_on;
   g.src_cell_on = b->prm[r].src_cell_on;
   g.src_point_on = b->prm[r].src_point_on;
+  for (int k = 0; k < 4; ++k) g.side[k] = 0;
+  g.special = 0;
+  g.x0 = 0.0;
+  g.in_lo = g.in_hi = 0.0;
 }
 
 double *state_ptr(af_batch *b, int buf, int r, int cls) {

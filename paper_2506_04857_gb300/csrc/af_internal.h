@@ -42,6 +42,12 @@ struct AfGrid {
   double kappa, cfl;
   double c13;              // 1e-13 / (gamma - 1)
   int pp_on, src_cell_on, src_point_on;
+  // bc = 1: kind of each side (0 left, 1 right, 2 bottom, 3 top): 0 outflow
+  // (mirror), 1 reflective (mirror, normal momentum and B negated), 2 inflow
+  // (bottom/top: the inflow state where in_lo < x < in_hi, outflow elsewhere)
+  int side[4];
+  int special;             // some side is reflective or inflow
+  double x0, in_lo, in_hi;
 };
 
 // Device-resident per-step scalars: dt stays on the device so that a whole
@@ -71,6 +77,7 @@ struct AfDev {
   double *thx, *thy;      // unique face coefficients (read back by the repair pass)
   AfScalars *sc;
   AfStatus *st;
+  const double *inflow;   // inflow state [8], its point data as a point [AF_NQP] and as an average [AF_NQA]
 };
 
 // one member of a batch (af_batch.cu): its work pointers and grid
@@ -88,6 +95,8 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
+// point data of the inflow state U (device, 8 doubles) into out (8 + AF_NQP + AF_NQA doubles)
+void af_launch_inflow_pd(const AfGrid &g, const double *U, double *out, cudaStream_t s);
 // sensitivity of one step to its dt (af_adjoint.cu), in two launches: the dot
 // product mu dt of the reverse-sweep variables with the stage increments
 // (before the last VJP, which may overwrite L3), then the maximising DoFs of

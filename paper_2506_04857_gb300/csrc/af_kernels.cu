@@ -332,6 +332,102 @@ __device__ __forceinline__ double pw(const PP &p, size_t PS, int nxa, int q) {
   return __ldg(p.w + (size_t)q * PS + (size_t)p.j * nxa + p.i);
 }
 
+// ---- reflective and inflow sides -------------------------------------------
+// Kernels are instantiated twice: GB = false (periodic or mirror outflow on all
+// sides: ghost indices map onto interior DoFs) and GB = true (some side
+// reflective or inflow).  With GB a ghost index is mapped along x first
+// (mirror; a reflective side negates m1, B1 and the point-data slots that
+// change sign with them), then along y (mirror; reflective: m2, B2; inflow:
+// the inflow state where the x coordinate of the x-mapped index lies inside
+// the inflow range).  Reading: the paper names the conditions only (Example 4.8).
+constexpr unsigned kFlipUx = (1u << 1) | (1u << 4), kFlipUy = (1u << 2) | (1u << 5);
+// point-data slots (QP and QA share the positions that change sign): F1 and F2
+// without their B_l component, v1 / v2
+constexpr unsigned kFlipWx = (1u << 0) | (1u << 2) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 8) |
+                             (1u << 11) | (1u << 16);
+constexpr unsigned kFlipWy = (1u << 2) | (1u << 4) | (1u << 7) | (1u << 8) | (1u << 10) | (1u << 11) | (1u << 12) |
+                             (1u << 13) | (1u << 17);
+
+struct GR {
+  int i, j;        // mapped index
+  unsigned um, wm; // sign masks of the state components and of the point-data slots
+  bool in;         // the inflow state
+};
+// cls 0 average, 1 x-face, 2 y-face, 3 corner, 4 cell centre; (i, j) unmapped
+__device__ __forceinline__ GR gres(const AfGrid &g, int cls, int i, int j) {
+  const bool xf = cls == 1 || cls == 3, yf = cls == 2 || cls == 3;
+  const int nxe = xf ? g.nx + 1 : g.nx, nye = yf ? g.ny + 1 : g.ny;
+  GR r;
+  r.um = r.wm = 0u;
+  r.in = false;
+  r.i = xf ? mface(i, g.nx, g.bc) : mcell(i, g.nx, g.bc);
+  r.j = yf ? mface(j, g.ny, g.bc) : mcell(j, g.ny, g.bc);
+  if ((i < 0 || i >= nxe) && g.side[i < 0 ? 0 : 1] == 1) {
+    r.um ^= kFlipUx;
+    r.wm ^= kFlipWx;
+  }
+  if (j < 0 || j >= nye) {
+    const int sd = g.side[j < 0 ? 2 : 3];
+    if (sd == 1) {
+      r.um ^= kFlipUy;
+      r.wm ^= kFlipWy;
+    } else if (sd == 2) {
+      const double x = g.x0 + (r.i + (xf ? 0.0 : 0.5)) * g.dx;
+      r.in = x > g.in_lo && x < g.in_hi;
+    }
+  }
+  return r;
+}
+__device__ __forceinline__ double flipv(double v, unsigned mask, int k) { return ((mask >> k) & 1u) ? -v : v; }
+
+// a point on an FVS line with its own point-data strides and sign masks
+struct PPG {
+  PP p;
+  size_t wps;
+  int wnx;
+  unsigned um, wm;
+};
+__device__ __forceinline__ PPG prefg(const AfDev &d, const AfGrid &g, int c, int i, int j) {
+  const GR r = gres(g, c, i, j);
+  PPG q;
+  if (r.in) {
+    q.p.u = d.inflow;
+    q.p.ucs = 1;
+    q.p.uex = 0;
+    q.p.w = d.inflow + 8 + (c == 0 ? AF_NQP : 0);
+    q.p.i = q.p.j = 0;
+    q.wps = 1;
+    q.wnx = 0;
+    q.um = q.wm = 0u;
+  } else {
+    q.p = pref(d, g, c, r.i, r.j);
+    q.wps = (size_t)g.nxa * g.nya;
+    q.wnx = g.nxa;
+    q.um = r.um;
+    q.wm = r.wm;
+  }
+  return q;
+}
+__device__ __forceinline__ double pug(const PPG &q, int k) { return flipv(pu(q.p, k), q.um, k); }
+__device__ __forceinline__ double pwg(const PPG &q, int s) {
+  return flipv(__ldg(q.p.w + (size_t)s * q.wps + (size_t)q.p.j * q.wnx + q.p.i), q.wm, s);
+}
+// the 8 state values of DoF (cls, i, j) (unmapped; cls 0..3)
+template <bool GB>
+__device__ __forceinline__ void gload8(const AfDev &d, const AfGrid &g, int cls, int i, int j, double *U) {
+  if constexpr (GB) {
+    const PPG q = prefg(d, g, cls, i, j);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) U[k] = pug(q, k);
+  } else {
+    const int mi = (cls == 1 || cls == 3) ? mface(i, g.nx, g.bc) : mcell(i, g.nx, g.bc);
+    const int mj = (cls == 2 || cls == 3) ? mface(j, g.ny, g.bc) : mcell(j, g.ny, g.bc);
+    const SV v = sview(d.us[cls], g, cls);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) U[k] = v(mi, mj, k);
+  }
+}
+
 // Accumulate -c * [ (D+ F+ + D- F-) * h ] of direction l along the line P[0..4]
 // into acc (per component), with F^pm = (F +- alpha U)/2.  Writing out D+ and D-:
 // (D+F+ + D-F-) h = ((F0 - F4) + 4 (F3 - F1) + alpha ((U0 + U4) - 4 (U1 + U3) + 6 U2)) / 2.
@@ -360,6 +456,29 @@ __device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double
   }
 }
 
+// fvs_line on ghost-aware points (reflective / inflow sides)
+template <int L>
+__device__ __forceinline__ void fvs_line_g(const PPG *P, double c, double *acc, double &dBl) {
+  const int qsr = L == 0 ? QP_SR1 : QP_SR2;
+  double al = pwg(P[0], qsr);
+#pragma unroll
+  for (int q = 1; q < 5; ++q) al = maxnn(al, pwg(P[q], qsr));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double u0 = pug(P[0], k), u1 = pug(P[1], k), u2 = pug(P[2], k), u3 = pug(P[3], k), u4 = pug(P[4], k);
+    const double up = fma(6.0, u2, fma(-4.0, u1 + u3, u0 + u4));
+    double dk;
+    if (k == 4 + L) {
+      dk = al * up;
+      dBl = fma(4.0, u3 - u1, u0 - u4);
+    } else {
+      const int s = (L == 0 ? QP_F1 : QP_F2) + fslot(L, k);
+      dk = fma(al, up, fma(4.0, pwg(P[3], s) - pwg(P[1], s), pwg(P[0], s) - pwg(P[4], s)));
+    }
+    acc[k] = fma(-c, dk, acc[k]);
+  }
+}
+
 // Central derivative of F_l between two points lo, hi: acc -= c (F(hi) - F(lo)).
 template <int L>
 __device__ __forceinline__ void central_line(const PP &lo, const PP &hi, size_t PS, int nxa, double c, double *acc,
@@ -377,39 +496,39 @@ __device__ __forceinline__ void central_line(const PP &lo, const PP &hi, size_t 
 
 // Slow path of Sec. 3.3 for one point value (cls 1, 2, 3 at (i,j)): its
 // first-order LLF state, the scaling limiter and the round-off shrink.
+template <bool GB>
 __device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, int i, int j, const double *UH,
                                       double dt, double *out, int &limited, int &shrunk, int &bad) {
-  const int im = mface(i - 1, g.nx, g.bc), ip = mface(i + 1, g.nx, g.bc);
-  const int jm = mface(j - 1, g.ny, g.bc), jp = mface(j + 1, g.ny, g.bc);
-  int cx[2], ix[2], jx[2], cy[2], iy[2], jy[2];   // neighbours for the x and y fluxes (left/low, right/high)
+  // neighbours (class, unmapped index) for the x and y fluxes (left/low, right/high)
+  int cx[2], ix[2], jx[2], cy[2], iy[2], jy[2];
   if (cls == 3) {
-    cx[0] = cx[1] = 3; ix[0] = im; ix[1] = ip; jx[0] = jx[1] = j;
-    cy[0] = cy[1] = 3; iy[0] = iy[1] = i; jy[0] = jm; jy[1] = jp;
+    cx[0] = cx[1] = 3; ix[0] = i - 1; ix[1] = i + 1; jx[0] = jx[1] = j;
+    cy[0] = cy[1] = 3; iy[0] = iy[1] = i; jy[0] = j - 1; jy[1] = j + 1;
   } else if (cls == 1) {
-    cx[0] = cx[1] = 1; ix[0] = im; ix[1] = ip; jx[0] = jx[1] = j;
-    cy[0] = cy[1] = 3; iy[0] = iy[1] = i; jy[0] = j; jy[1] = jp;
+    cx[0] = cx[1] = 1; ix[0] = i - 1; ix[1] = i + 1; jx[0] = jx[1] = j;
+    cy[0] = cy[1] = 3; iy[0] = iy[1] = i; jy[0] = j; jy[1] = j + 1;
   } else {
-    cx[0] = cx[1] = 3; ix[0] = i; ix[1] = ip; jx[0] = jx[1] = j;
-    cy[0] = cy[1] = 2; iy[0] = iy[1] = i; jy[0] = jm; jy[1] = jp;
+    cx[0] = cx[1] = 3; ix[0] = i; ix[1] = i + 1; jx[0] = jx[1] = j;
+    cy[0] = cy[1] = 2; iy[0] = iy[1] = i; jy[0] = j - 1; jy[1] = j + 1;
   }
   double U[8];
   load8(sview(d.us[cls], g, cls), i, j, U);
   Full me, nb;
   full_data(U, g, me);
   double Fxl[8], Fxr[8], Fyl[8], Fyr[8];
-  load8(sview(d.us[cx[0]], g, cx[0]), ix[0], jx[0], U);
+  gload8<GB>(d, g, cx[0], ix[0], jx[0], U);
   full_data(U, g, nb);
   llf_flux_full(0, nb, me, Fxl);
   const double b1l = nb.B[0];
-  load8(sview(d.us[cx[1]], g, cx[1]), ix[1], jx[1], U);
+  gload8<GB>(d, g, cx[1], ix[1], jx[1], U);
   full_data(U, g, nb);
   llf_flux_full(0, me, nb, Fxr);
   const double b1r = nb.B[0];
-  load8(sview(d.us[cy[0]], g, cy[0]), iy[0], jy[0], U);
+  gload8<GB>(d, g, cy[0], iy[0], jy[0], U);
   full_data(U, g, nb);
   llf_flux_full(1, nb, me, Fyl);
   const double b2l = nb.B[1];
-  load8(sview(d.us[cy[1]], g, cy[1]), iy[1], jy[1], U);
+  gload8<GB>(d, g, cy[1], iy[1], jy[1], U);
   full_data(U, g, nb);
   llf_flux_full(1, me, nb, Fyr);
   const double b2r = nb.B[1];
@@ -450,27 +569,40 @@ __device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, 
 // Shock-sensor values of cell (ci, cj) (ghost cells allowed) from the cell
 // averages around it, with boundary-mapped neighbour indices (Sec. 3.4).
 // Reading: phi_1 is differenced along x for x-faces and along y for y-faces.
+template <bool GB>
 __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, double *phi) {
-  const WV A = wview(d.pd[0], g);
-  const SV Ub = sview(d.us[0], g, 0);
-  const int c_i = mcell(ci, g.nx, g.bc), c_j = mcell(cj, g.ny, g.bc);
-  const int e = mcell(ci + 1, g.nx, g.bc), w = mcell(ci - 1, g.nx, g.bc);
-  const int n = mcell(cj + 1, g.ny, g.bc), s = mcell(cj - 1, g.ny, g.bc);
-  const double ptc = A(c_i, c_j, QA_PT), pte = A(e, c_j, QA_PT), ptw = A(w, c_j, QA_PT);
-  const double ptn = A(c_i, n, QA_PT), pts = A(c_i, s, QA_PT);
+  // slot q of the average's point data and component k of the average, cell (a, b) unmapped
+  auto A = [&](int a, int b, int q) -> double {
+    if constexpr (GB) {
+      return pwg(prefg(d, g, 0, a, b), q);
+    } else {
+      return __ldg(d.pd[0] + (size_t)q * g.nxa * g.nya + (size_t)mcell(b, g.ny, g.bc) * g.nxa + mcell(a, g.nx, g.bc));
+    }
+  };
+  auto Ub = [&](int a, int b, int k) -> double {
+    if constexpr (GB) {
+      return pug(prefg(d, g, 0, a, b), k);
+    } else {
+      return __ldg(d.us[0] + (size_t)k * g.nx * g.ny + (size_t)mcell(b, g.ny, g.bc) * g.nx + mcell(a, g.nx, g.bc));
+    }
+  };
+  const int e = ci + 1, w = ci - 1, n = cj + 1, s = cj - 1;
+  const double ptc = A(ci, cj, QA_PT), pte = A(e, cj, QA_PT), ptw = A(w, cj, QA_PT);
+  const double ptn = A(ci, n, QA_PT), pts = A(ci, s, QA_PT);
   const double sx = pte + ptw, sy = ptn + pts;
   phi[0] = ddiv(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
   phi[1] = ddiv(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
-  const double divv = fma(A(e, c_j, QA_V1) - A(w, c_j, QA_V1), hx, (A(c_i, n, QA_V2) - A(c_i, s, QA_V2)) * hy);
-  const double curl = fma(A(e, c_j, QA_V2) - A(w, c_j, QA_V2), hx, -(A(c_i, n, QA_V1) - A(c_i, s, QA_V1)) * hy);
+  const double divv = fma(A(e, cj, QA_V1) - A(w, cj, QA_V1), hx, (A(ci, n, QA_V2) - A(ci, s, QA_V2)) * hy);
+  const double curl = fma(A(e, cj, QA_V2) - A(w, cj, QA_V2), hx, -(A(ci, n, QA_V1) - A(ci, s, QA_V1)) * hy);
   const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
   const double ph2 = ddiv(-divv, den);
   phi[2] = ph2 > 0.0 ? ph2 : 0.0;
-  const double num = (Ub(e, c_j, 4) - Ub(w, c_j, 4)) + (Ub(c_i, n, 5) - Ub(c_i, s, 5));
-  phi[3] = ddiv(absd(num), absd(Ub(c_i, c_j, 4) + Ub(c_i, c_j, 5)) + 1e-40);
+  const double num = (Ub(e, cj, 4) - Ub(w, cj, 4)) + (Ub(ci, n, 5) - Ub(ci, s, 5));
+  phi[3] = ddiv(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
 }
 
+template <bool GB>
 __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b,
                                          int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
@@ -491,7 +623,30 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
 #pragma unroll
       for (int k = 0; k < 8; ++k) acc[k] = mode == 1 ? 0.0 : pu(me, k);
       double dBx, dBy, divB;
-      if (cls == 3) {
+      if constexpr (GB) {   // lines through reflective / inflow ghosts (unmapped indices)
+        const PPG mg = prefg(d, g, cls, i, j);
+        if (cls == 3) {
+          const PPG Px[5] = {prefg(d, g, 3, i - 1, j), prefg(d, g, 2, i - 1, j), mg, prefg(d, g, 2, i, j),
+                             prefg(d, g, 3, i + 1, j)};
+          const PPG Py[5] = {prefg(d, g, 3, i, j - 1), prefg(d, g, 1, i, j - 1), mg, prefg(d, g, 1, i, j),
+                             prefg(d, g, 3, i, j + 1)};
+          fvs_line_g<0>(Px, cx, acc, dBx);
+          fvs_line_g<1>(Py, cy, acc, dBy);
+          divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
+        } else if (cls == 1) {
+          const PPG Px[5] = {prefg(d, g, 1, i - 1, j), prefg(d, g, 4, i - 1, j), mg, prefg(d, g, 4, i, j),
+                             prefg(d, g, 1, i + 1, j)};
+          fvs_line_g<0>(Px, cx, acc, dBx);
+          central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
+          divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
+        } else {
+          central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
+          const PPG Py[5] = {prefg(d, g, 2, i, j - 1), prefg(d, g, 4, i, j - 1), mg, prefg(d, g, 4, i, j),
+                             prefg(d, g, 2, i, j + 1)};
+          fvs_line_g<1>(Py, cy, acc, dBy);
+          divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
+        }
+      } else if (cls == 3) {
         const PP Px[5] = {pref(d, g, 3, im, j), pref(d, g, 2, ci0, j), me, pref(d, g, 2, ci1, j), pref(d, g, 3, ip, j)};
         const PP Py[5] = {pref(d, g, 3, i, jm), pref(d, g, 1, i, cj0), me, pref(d, g, 1, i, cj1), pref(d, g, 3, i, jp)};
         fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx);
@@ -529,7 +684,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
       if (g.pp_on && !clear_of_floor(acc, g)) {
         double out[8];
         int lim, shr, bad;
-        point_pp(d, g, cls, i, j, acc, dt, out, lim, shr, bad);
+        point_pp<GB>(d, g, cls, i, j, acc, dt, out, lim, shr, bad);
         nlim += lim;
         nshr += shr;
         nbad += bad;
@@ -546,7 +701,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
     }
     if (mode != 1 && i < g.nx && j < g.ny && g.kappa != 0.0) {
       double phi[4];
-      sensor_phi(d, g, i, j, phi);
+      sensor_phi<GB>(d, g, i, j, phi);
       const size_t o = (size_t)j * g.nxa + i;
 #pragma unroll
       for (int q = 0; q < 4; ++q) d.phi[q * PS + o] = phi[q];
@@ -564,6 +719,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
 // P3: faces
 // ---------------------------------------------------------------------------
 // phi of cell (ci, cj): stored for interior cells, recomputed for ghost cells
+template <bool GB>
 __device__ __forceinline__ void get_phi(const AfDev &d, const AfGrid &g, int ci, int cj, double *phi) {
   if (ci >= 0 && ci < g.nx && cj >= 0 && cj < g.ny) {
     const WV P = wview(d.phi, g);
@@ -575,27 +731,42 @@ __device__ __forceinline__ void get_phi(const AfDev &d, const AfGrid &g, int ci,
 #pragma unroll
     for (int q = 0; q < 4; ++q) phi[q] = P(a, b2, q);
   } else {
-    sensor_phi(d, g, ci, cj, phi);
+    sensor_phi<GB>(d, g, ci, cj, phi);
   }
 }
 
 // theta^s = exp(-kappa [phi_1 phi_2 + phi_3]) with each phi maxed over the two cells
+template <bool GB>
 __device__ __forceinline__ double theta_s(const AfDev &d, const AfGrid &g, int dir, int ia, int ja, int ib, int jb) {
   if (g.kappa == 0.0) return 1.0;
   double pa[4], pb[4];
-  get_phi(d, g, ia, ja, pa);
-  get_phi(d, g, ib, jb, pb);
+  get_phi<GB>(d, g, ia, ja, pa);
+  get_phi<GB>(d, g, ib, jb, pb);
   const double p1 = maxnn(pa[dir], pb[dir]), p2 = maxnn(pa[2], pb[2]), p3 = maxnn(pa[3], pb[3]);
   return exp(-g.kappa * fma(p1, p2, p3));
 }
 
 // One face in direction L between cell averages ca, cb (mapped indices),
 // Simpson nodes lo, mid, hi.  Writes F^LLF, G = theta^s (F - F^LLF), theta^s, alpha.
-template <int L>
+// GB: the cell indices are unmapped and resolved through reflective / inflow sides.
+template <int L, bool GB>
 __device__ __forceinline__ void face(const AfDev &d, const AfGrid &g, double *out, size_t PS, const PP &lo, const PP &mid,
                                      const PP &hi, int cai, int caj, int cbi, int cbj, double ts, bool llf, int &nsens) {
-  const WV A = wview(d.pd[0], g);
-  const SV Ub = sview(d.us[0], g, 0);
+  const WV Aw = wview(d.pd[0], g);
+  const SV Uw = sview(d.us[0], g, 0);
+  PPG ga, gb;
+  if constexpr (GB) {
+    ga = prefg(d, g, 0, cai, caj);
+    gb = prefg(d, g, 0, cbi, cbj);
+  }
+  auto A = [&](int a, int b, int q) -> double {
+    if constexpr (GB) return pwg(a == cai && b == caj ? ga : gb, q);
+    else return Aw(a, b, q);
+  };
+  auto Ub = [&](int a, int b, int k) -> double {
+    if constexpr (GB) return pug(a == cai && b == caj ? ga : gb, k);
+    else return Uw(a, b, k);
+  };
   double al = 0.0;
   if (llf) {
     const int qv = L == 0 ? QA_V1 : QA_V2, qc = L == 0 ? QA_CF1 : QA_CF2;
@@ -623,6 +794,7 @@ __device__ __forceinline__ void face(const AfDev &d, const AfGrid &g, double *ou
   nsens += ts < 0.99;
 }
 
+template <bool GB>
 __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const int i, const int j, int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
@@ -633,16 +805,24 @@ __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const i
     // x-face (f = i, row j): cells i-1 | i; Simpson nodes: corners (i,j), (i,j+1), x-face (i,j)
     if (i < g.ex[1] && j < g.ey[1]) {
       const int jp = mface(j + 1, g.ny, g.bc);
-      const double ts = sens ? theta_s(d, g, 0, i - 1, j, i, j) : 1.0;
-      face<0>(d, g, d.fx + o, PS, pref(d, g, 3, i, j), pref(d, g, 1, i, j), pref(d, g, 3, i, jp),
-              mcell(i - 1, g.nx, g.bc), j, mcell(i, g.nx, g.bc), j, ts, llf, nsens);
+      const double ts = sens ? theta_s<GB>(d, g, 0, i - 1, j, i, j) : 1.0;
+      if constexpr (GB)
+        face<0, true>(d, g, d.fx + o, PS, pref(d, g, 3, i, j), pref(d, g, 1, i, j), pref(d, g, 3, i, jp), i - 1, j, i, j,
+                      ts, llf, nsens);
+      else
+        face<0, false>(d, g, d.fx + o, PS, pref(d, g, 3, i, j), pref(d, g, 1, i, j), pref(d, g, 3, i, jp),
+                       mcell(i - 1, g.nx, g.bc), j, mcell(i, g.nx, g.bc), j, ts, llf, nsens);
     }
     // y-face (i, g = j): cells j-1 | j; Simpson nodes: corners (i,j), (i+1,j), y-face (i,j)
     if (i < g.ex[2] && j < g.ey[2]) {
       const int ip = mface(i + 1, g.nx, g.bc);
-      const double ts = sens ? theta_s(d, g, 1, i, j - 1, i, j) : 1.0;
-      face<1>(d, g, d.fy + o, PS, pref(d, g, 3, i, j), pref(d, g, 2, i, j), pref(d, g, 3, ip, j), i,
-              mcell(j - 1, g.ny, g.bc), i, mcell(j, g.ny, g.bc), ts, llf, nsens);
+      const double ts = sens ? theta_s<GB>(d, g, 1, i, j - 1, i, j) : 1.0;
+      if constexpr (GB)
+        face<1, true>(d, g, d.fy + o, PS, pref(d, g, 3, i, j), pref(d, g, 2, i, j), pref(d, g, 3, ip, j), i, j - 1, i, j,
+                      ts, llf, nsens);
+      else
+        face<1, false>(d, g, d.fy + o, PS, pref(d, g, 3, i, j), pref(d, g, 2, i, j), pref(d, g, 3, ip, j), i,
+                       mcell(j - 1, g.ny, g.bc), i, mcell(j, g.ny, g.bc), ts, llf, nsens);
     }
   }
   if (sens && g.kappa != 0.0) {
@@ -747,6 +927,7 @@ __device__ __noinline__ void cell_limiter_full(const double *Ullf, const double 
   flux_limiter_box(L1, H, eps_rho, eps_p, g.gm1, Lam, nl);
 }
 
+template <bool GB>
 __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b,
                                         int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
@@ -830,9 +1011,21 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
       }
     } else {
       // S^LLF = (central div Bbar) Psi(Ubar)
-      const int ie = mcell(i + 1, g.nx, g.bc), iw = mcell(i - 1, g.nx, g.bc);
-      const int jn = mcell(j + 1, g.ny, g.bc), js = mcell(j - 1, g.ny, g.bc);
-      const double divBb = fma(Ub(ie, j, 4) - Ub(iw, j, 4), 0.5 * g.rdx, (Ub(i, jn, 5) - Ub(i, js, 5)) * (0.5 * g.rdy));
+      double be, bw, bn, bs;
+      if constexpr (GB) {
+        be = pug(prefg(d, g, 0, i + 1, j), 4);
+        bw = pug(prefg(d, g, 0, i - 1, j), 4);
+        bn = pug(prefg(d, g, 0, i, j + 1), 5);
+        bs = pug(prefg(d, g, 0, i, j - 1), 5);
+      } else {
+        const int ie = mcell(i + 1, g.nx, g.bc), iw = mcell(i - 1, g.nx, g.bc);
+        const int jn = mcell(j + 1, g.ny, g.bc), js = mcell(j - 1, g.ny, g.bc);
+        be = Ub(ie, j, 4);
+        bw = Ub(iw, j, 4);
+        bn = Ub(i, jn, 5);
+        bs = Ub(i, js, 5);
+      }
+      const double divBb = fma(be - bw, 0.5 * g.rdx, (bn - bs) * (0.5 * g.rdy));
       double Ubar[8];
       load8(Ub, i, j, Ubar);
       const double vb1 = A(i, j, QA_V1), vb2 = A(i, j, QA_V2), vb3 = A(i, j, QA_V3);
@@ -1138,29 +1331,32 @@ __global__ void kb_dt(const AfRun *__restrict__ runs, int nruns) {
 }
 // At most 128 registers (4 blocks per SM): the limiter slow path spills a
 // little, the common path runs at twice the occupancy (measured 8 % faster).
+template <bool GB>
 __global__ void __launch_bounds__(128, 4) k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                 double a, double b, int mode) {
-  b_points(d, g, AF_IJ, a, b, mode);
+  b_points<GB>(d, g, AF_IJ, a, b, mode);
 }
 __global__ void __launch_bounds__(256, 2) kb_points(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                  int nitems, double a, double b) {
-  AF_BATCH_LOOP(b_points(r->d, r->g, i, j, a, b, 0));
+  AF_BATCH_LOOP(b_points<false>(r->d, r->g, i, j, a, b, 0));
 }
+template <bool GB>
 __global__ void __launch_bounds__(128) k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                int mode) {
-  b_faces(d, g, AF_IJ, mode);
+  b_faces<GB>(d, g, AF_IJ, mode);
 }
 __global__ void __launch_bounds__(256) kb_faces(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                 int nitems) {
-  AF_BATCH_LOOP(b_faces(r->d, r->g, i, j, 0));
+  AF_BATCH_LOOP(b_faces<false>(r->d, r->g, i, j, 0));
 }
+template <bool GB>
 __global__ void __launch_bounds__(128) k_cells(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                double a, double b, int mode) {
-  b_cells(d, g, AF_IJ, a, b, mode);
+  b_cells<GB>(d, g, AF_IJ, a, b, mode);
 }
 __global__ void __launch_bounds__(256, 2) kb_cells(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                 int nitems, double a, double b) {
-  AF_BATCH_LOOP(b_cells(r->d, r->g, i, j, a, b, 0));
+  AF_BATCH_LOOP(b_cells<false>(r->d, r->g, i, j, a, b, 0));
 }
 __global__ void __launch_bounds__(128) k_final(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                double a, double b) {
@@ -1181,6 +1377,14 @@ __global__ void kb_repair(const AfRun *__restrict__ runs, int nruns, double a, d
 // ---------------------------------------------------------------------------
 // math self-check: out = rcp(x) (op 0), ddiv(x, y) (op 1), dsqrt(x) (op 2)
 // ---------------------------------------------------------------------------
+// point data of the inflow state: out = [U (8)][as a point (AF_NQP)][as an average (AF_NQA)]
+__global__ void k_inflow_pd(const __grid_constant__ AfGrid g, const double *U, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double u[8], s1, s2;
+  for (int k = 0; k < 8; ++k) out[k] = u[k] = U[k];
+  point_data(u, g, out + 8, 1, false, s1, s2);
+  point_data(u, g, out + 8 + AF_NQP, 1, true, s1, s2);
+}
 __global__ void k_math_check(int op, const double *x, const double *y, double *out, long long n) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -1305,13 +1509,16 @@ void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *o
   k_divb_sum<<<1, 256, 0, s>>>(partials, (int)(b.x * b.y), out);
 }
 void af_launch_points(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s) {
-  k_points<<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
+  if (g.special) k_points<true><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
+  else k_points<false><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
 }
 void af_launch_faces(const AfDev &d, const AfGrid &g, int mode, cudaStream_t s) {
-  k_faces<<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, mode);
+  if (g.special) k_faces<true><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, mode);
+  else k_faces<false><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, mode);
 }
 void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s) {
-  k_cells<<<grid2(g.nx, g.ny), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
+  if (g.special) k_cells<true><<<grid2(g.nx, g.ny), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
+  else k_cells<false><<<grid2(g.nx, g.ny), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
 }
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
   k_final<<<grid2(g.nx, g.ny), dim3(32, 4), 0, s>>>(d, g, a, b);
@@ -1342,6 +1549,10 @@ float af_run_fp64_probe(cudaStream_t s, double *flops) {
   cudaEventDestroy(e1);
   *flops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
   return ms;
+}
+
+void af_launch_inflow_pd(const AfGrid &g, const double *U, double *out, cudaStream_t s) {
+  k_inflow_pd<<<1, 32, 0, s>>>(g, U, out);
 }
 
 void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s) {

@@ -137,7 +137,7 @@ __device__ __forceinline__ void b1_points(const AfDev &d, const AfGrid &g, int f
   }
   if (f < g.nx && g.kappa != 0.0) {
     double phi[4];
-    sensor_phi(d, g, f, 0, phi);
+    sensor_phi<false>(d, g, f, 0, phi);
 #pragma unroll
     for (int q = 0; q < 4; ++q) d.phi[q * PS + f] = phi[q];
   }
@@ -163,7 +163,7 @@ __device__ __forceinline__ void b1_faces(const AfDev &d, const AfGrid &g, int f)
     const double al = alpha_llf(A(ca, 0, QA_V1), A(cb, 0, QA_V1), A(ca, 0, QA_CF1), A(cb, 0, QA_CF1),
                                 A(ca, 0, QA_SRHO), A(cb, 0, QA_SRHO), Ba, Bb);
     // unmapped cell indices: an outflow ghost cell's phi comes from its own (mirrored) neighbours
-    const double ts = theta_s(d, g, 0, f - 1, 0, f, 0);
+    const double ts = theta_s<false>(d, g, 0, f - 1, 0, f, 0);
     double *out = d.fx + f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {

@@ -93,6 +93,10 @@ extern "C" int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, d
   g.pp_on = 0;
   g.src_cell_on = 1;
   g.src_point_on = 1;
+  for (int k = 0; k < 4; ++k) g.side[k] = 0;
+  g.special = 0;
+  g.x0 = 0.0;
+  g.in_lo = g.in_hi = 0.0;
 
   const size_t PS = (size_t)nxa * nya;
   double *w = (double *)base;
