@@ -67,6 +67,7 @@ enum {
   AF_STAT_CFL_VIOLATIONS,    /* cells violating the LLF CFL condition of Lemma 3.1 */
   AF_STAT_CENTER_LIMITED,    /* cell-centre values modified (Remark 3.2) */
   AF_STAT_NONADMISSIBLE,     /* DoFs left outside G after every safeguard */
+  AF_STAT_CELL_SHRINK,       /* the cell-average part of AF_STAT_SHRINK (Remark 4.1) */
   AF_NSTAT
 };
 

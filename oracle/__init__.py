@@ -23,9 +23,9 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIBS = {}
 _LOCK = threading.Lock()
 
-NSTATS = 11
+NSTATS = 12
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
-              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
+              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible", "cell_shrink"]
 PHASES = ["dt", "pointdata", "center", "point_ho", "point_pp", "sensor_phi", "sensor_theta", "face", "cell_src",
           "cell_update", "cell_final", "rk"]
 KINDS = ["add", "mul", "div", "sqrt", "exp", "minmax", "cmp"]

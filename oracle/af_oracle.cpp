@@ -169,6 +169,7 @@ enum {
   ST_CFL_VIOLATIONS,    // cells violating the LLF CFL condition of Lemma 3.1
   ST_CENTER_LIMITED,    // cell-centre values modified by Remark 3.2
   ST_NONADMISSIBLE,     // DoFs left outside G after every safeguard
+  ST_CELL_SHRINK,       // the cell-average part of ST_SHRINK (Remark 4.1 for the averages)
   ST_NSTATS
 };
 }
@@ -1129,6 +1130,7 @@ static void cell_final(const Ctx &C, Work &W, long long *st) {
       }
     }
   st[ST_SHRINK] += nshrink;
+  st[ST_CELL_SHRINK] += nshrink;
   st[ST_NONADMISSIBLE] += nbad;
 }
 
@@ -1490,6 +1492,7 @@ static void stage1(const Ctx1 &C, Arr1 &An, Arr1 &Pn, Arr1 &As, Arr1 &Ps, real d
       for (int k = 0; k < 8; ++k) cur[k] = AF.at(k, i);
       if (in_G(cur, C.gamma)) continue;
       st[ST_SHRINK]++;
+      st[ST_CELL_SHRINK]++;
       const real t0[2] = {th.at(0, i), th.at(0, i + 1)};
       for (int m = 0; m <= 10; ++m) {
         real t[2], out[8];

@@ -31,12 +31,12 @@ __all__ = [
 
 AF_BC_PERIODIC, AF_BC_OUTFLOW = 0, 1
 AF_OK, AF_EINVAL, AF_ECUDA, AF_ENOMEM, AF_ENONPHYS, AF_EBOUNDS, AF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
-AF_NSTAT = 11
+AF_NSTAT = 12
 AF_ADJ_RECORDED = 1
 AF_ADJ_DT = 2
 AF_SIDE_OUTFLOW, AF_SIDE_REFLECTIVE, AF_SIDE_INFLOW = 0, 1, 2
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
-              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible"]
+              "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible", "cell_shrink"]
 _CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
           AF_EBOUNDS: "AF_EBOUNDS", AF_ETIMEOUT: "AF_ETIMEOUT"}
 

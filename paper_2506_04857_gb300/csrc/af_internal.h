@@ -15,7 +15,7 @@
 #define AF_NQP 20   // per point value: F1 (7), F2 (7), varrho_1, varrho_2, v (3), v.B
 #define AF_NQA 21   // per cell average: F1 (7), F2 (7), c_f1, c_f2, v (3), p_t, sqrt(rho)
 #define AF_NQF 18   // per face: F^LLF (8), G = theta^s (F - F^LLF) (8), theta^s, alpha^LLF
-#define AF_NSTAT 11
+#define AF_NSTAT 12
 #define AF_MAX_REPAIR 4096
 
 // F1 is stored without its B1 component (identically 0), F2 without B2.
@@ -26,7 +26,7 @@ enum { QF_FLLF = 0, QF_G = 8, QF_TS = 16, QF_AL = 17 };
 // counters (same meaning and order as the af_status counters in af.h)
 enum {
   ST_SRC_LIMITED = 0, ST_LAMBDA_LT1, ST_FACE_THETA_LT1, ST_SENSOR_LT099, ST_NEWTON_SOLVES, ST_NEWTON_MAXIT,
-  ST_SHRINK, ST_POINT_LIMITED, ST_CFL_VIOLATIONS, ST_CENTER_LIMITED, ST_NONADMISSIBLE
+  ST_SHRINK, ST_POINT_LIMITED, ST_CFL_VIOLATIONS, ST_CENTER_LIMITED, ST_NONADMISSIBLE, ST_CELL_SHRINK
 };
 
 // device error bits

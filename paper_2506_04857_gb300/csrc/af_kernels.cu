@@ -1295,6 +1295,7 @@ __device__ void b_repair(const AfDev &d, const AfGrid &g, double a, double b) {
     }
   }
   d.st->cnt[ST_SHRINK] += nshr;
+  d.st->cnt[ST_CELL_SHRINK] += nshr;
   d.st->cnt[ST_NONADMISSIBLE] += nbad;
   if (nbad) d.st->err |= AFE_NONADMISSIBLE;
   d.st->nrepair = 0;

@@ -334,7 +334,10 @@ __device__ void b1_repair(const AfDev &d, const AfGrid &g, double a, double b) {
     }
   }
   d.st->nrepair = 0;
-  if (nshr) d.st->cnt[ST_SHRINK] += nshr;
+  if (nshr) {
+    d.st->cnt[ST_SHRINK] += nshr;
+    d.st->cnt[ST_CELL_SHRINK] += nshr;
+  }
   if (nbad) {
     d.st->cnt[ST_NONADMISSIBLE] += nbad;
     d.st->err |= AFE_NONADMISSIBLE;
