@@ -177,3 +177,32 @@ def test_stage_order_and_host_buffers():
     A, P = s.get_state(device=False)
     V, _ = oracle.step1(pb, U, dt_in=dt)
     assert rel_err([A, P], V) <= 1e-12
+
+
+def test_1d_reduction_of_the_2d_path():
+    """On the GPU: one stage of the 2D path on y-invariant data whose y-face
+    values are the 1D parabola centres equals one stage of the 1D path (the
+    x-faces and averages; smooth data, sensor on)."""
+    n, ny = 24, 4
+    p1 = ai.entropy_wave1d(n, amp=0.3)
+    p1.kappa = 1.0
+    A1, P1 = ai.dofs1(p1)
+    A = np.repeat(A1[:, None, :], ny, axis=1)
+    X = np.repeat(P1[:, None, :], ny, axis=1)
+    Y = np.repeat(((6.0 * A1 - P1 - np.roll(P1, -1, axis=1)) / 4.0)[:, None, :], ny, axis=1)
+    U2 = [np.ascontiguousarray(a) for a in (A, X, Y, X.copy())]
+    s1 = solver(p1)
+    s1.set_state([A1, P1])
+    dt = s1.dt()
+    s1.set_state([A1, P1])
+    s1.stage(0, dt)
+    G1 = s1.get_stage(device=False)
+    s2 = af.Solver(n, ny, p1.gamma, af.AF_BC_PERIODIC, domain=(0.0, 1.0, 0.0, 0.25), kappa=1.0)
+    s2.set_state(U2)
+    s2.stage(0, dt)
+    G2 = s2.get_stage(device=False)
+    for j in range(ny):
+        for c in (0, 1):
+            for k in range(8):
+                ref = G1[c][k]
+                assert np.abs(G2[c][k, j] - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1.0), (c, j, k)

@@ -791,3 +791,31 @@ def test_inflow_of_the_free_stream_and_jets_need_pp():
         V, _ = oracle.step(pb, V, stats=st)
         assert admissible(V)
     assert st[oracle.STAT_NAMES.index("point_limited")] > 0
+
+
+def test_1d_reduction_of_the_2d_scheme():
+    """y-invariant 2D data whose y-face values are the 1D parabola centres
+    (6 Ubar - U_L - U_R)/4 make the 2D bi-parabola centre equal to the 1D
+    centre; one forward-Euler stage of the 2D scheme then updates the x-faces
+    and the averages exactly as the 1D scheme updates its points and averages
+    (smooth data, limiters inactive, sensor on)."""
+    n, ny = 24, 4
+    p1 = ai.entropy_wave1d(n, amp=0.3)
+    p1.kappa = 1.0
+    A1, P1 = ai.dofs1(p1)
+    pb = ai.Problem("y_invariant", n, ny, 0.0, 1.0, 0.0, 0.25, ai.PERIODIC, p1.gamma, lambda x, y: None, kappa=1.0)
+    A = np.repeat(A1[:, None, :], ny, axis=1)
+    X = np.repeat(P1[:, None, :], ny, axis=1)
+    Yc = (6.0 * A1 - P1 - np.roll(P1, -1, axis=1)) / 4.0
+    Y = np.repeat(Yc[:, None, :], ny, axis=1)
+    C = X.copy()
+    U2 = [np.ascontiguousarray(a) for a in (A, X, Y, C)]
+    dt = oracle.dt1(p1, [A1, P1])
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    R2 = oracle.stage(pb, U2, U2, dt, 0.0, 1.0, stats=st)
+    R1 = oracle.stage1(p1, [A1, P1], [A1, P1], dt, 0.0, 1.0)
+    assert st[oracle.STAT_NAMES.index("point_limited")] == 0 and st[oracle.STAT_NAMES.index("lambda_lt1")] == 0
+    for j in range(ny):
+        for k in range(8):
+            for got, ref in ((R2[0][k, j], R1[0][k]), (R2[1][k, j], R1[1][k])):
+                assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1.0), (j, k)
