@@ -202,10 +202,31 @@ int af_adjoint_step(af_ctx *ctx, const double *dt, int dt_on_device, const doubl
  * receives the step's dt. */
 int af_step(af_ctx *ctx, double *dt_used, int on_device);
 
-/* Synchronise the stream, copy the AF_NSTAT counters into counters (may be
- * NULL) and report the device error word: AF_ENONPHYS for a non-admissible
- * DoF or a non-finite dt, AF_EBOUNDS for an overflowed repair list.  reset = 1
- * clears counters and error word afterwards. */
+/* One SSP-RK3 step (as af_step) of a HOST-resident state, pipelined for
+ * streams of independent states.  in[cls] and out[cls] are host arrays in the
+ * state layout; in pinned memory (cudaHostAlloc / cudaHostRegister) the copies
+ * run asynchronously, in pageable memory they serialise.  The call enqueues
+ * the copy of `in` to the device (a context-owned copy stream), the step on
+ * the context's stream with dt taken from `in`, and the copy of the result to
+ * `out` (a second copy stream), and returns without waiting: the input copy
+ * of the next call and the output copy of the previous one overlap this
+ * step.  Two input and two output staging states (4 state buffers) are
+ * allocated on first use.  `out` is complete, and `in` may be reused, only
+ * after af_sync, af_status or af_destroy.  An input that overlaps the output
+ * of one of the three previous calls (chained steps) is copied after that
+ * output has arrived.  The resident state of af_set_state / af_get_state is
+ * not changed; the limiter counters and the device error word accumulate as
+ * for af_step.  Not to be called in the middle of a step (af_stage). */
+int af_step_host(af_ctx *ctx, const double *const in[4], double *const out[4]);
+
+/* Wait for all work of the context: its stream and its copy streams. */
+int af_sync(af_ctx *ctx);
+
+/* Synchronise the stream (and the copy streams of af_step_host), copy the
+ * AF_NSTAT counters into counters (may be NULL) and report the device error
+ * word: AF_ENONPHYS for a non-admissible DoF or a non-finite dt, AF_EBOUNDS
+ * for an overflowed repair list.  reset = 1 clears counters and error word
+ * afterwards. */
 int af_status(af_ctx *ctx, long long *counters, int reset);
 
 /* Kernels of one stage, in the order af_timing reports them. */

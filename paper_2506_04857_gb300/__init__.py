@@ -23,7 +23,7 @@ __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
     "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step", "af_sensor", "af_dt",
     "af_stage",
-    "af_step", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
+    "af_step", "af_step_host", "af_sync", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
     "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
     "af_batch_step", "af_batch_graph", "af_batch_autotune", "af_batch_dt", "af_batch_status", "af_batch_last_error",
     "af_batch_destroy", "af_last_error", "af_destroy", "af_math_check", "Solver", "STAT_NAMES", "lib_path",
@@ -83,6 +83,8 @@ def _lib():
             lib.af_sensor.argtypes = [vp, vp, vp, C.c_int]
             lib.af_stage.argtypes = [vp, C.c_int, vp, C.c_int]
             lib.af_step.argtypes = [vp, vp, C.c_int]
+            lib.af_step_host.argtypes = [vp, pp, pp]
+            lib.af_sync.argtypes = [vp]
             lib.af_get_stage.argtypes = [vp, pp, C.c_int]
             lib.af_rhs_vjp.argtypes = [vp, pp, pp, C.c_int]
             lib.af_divb.argtypes = [vp, vp, C.c_int]
@@ -257,6 +259,38 @@ def af_get_state(ctx, out=None, device: bool = True):
     out, ptrs, dev = _outputs(ctx, out, device)
     _check(ctx, _lib().af_get_state(ctx, ptrs, dev))
     return out
+
+
+def _host_ptrs(ctx, U):
+    """Pointers of host arrays that an asynchronous call keeps using after it returns: no
+    conversion or copy is made (a temporary would be freed before the copy runs)."""
+    shapes = _shapes(ctx)
+    if len(U) != 4:
+        raise ValueError("a state has four DoF classes")
+    ptrs = []
+    for u, s in zip(U, shapes):
+        if _is_tensor(u):
+            torch = _torch()
+            if u.is_cuda or u.dtype != torch.float64 or not u.is_contiguous() or tuple(u.shape) != s:
+                raise ValueError("host tensor must be a contiguous CPU float64 %s" % (s,))
+            ptrs.append(u.data_ptr())
+        elif isinstance(u, np.ndarray):
+            if u.dtype != np.float64 or not u.flags.c_contiguous or u.shape != s:
+                raise ValueError("host array must be a C-contiguous float64 %s" % (s,))
+            ptrs.append(u.ctypes.data)
+        else:
+            raise ValueError("af_step_host takes numpy arrays or CPU tensors")
+    return _ptr_array(ptrs)
+
+
+def af_step_host(ctx, U_in, U_out) -> None:
+    """One step of a host-resident state, pipelined (see af.h): U_in and U_out are four
+    host arrays (pinned for overlap) that must stay alive and untouched until af_sync."""
+    _check(ctx, _lib().af_step_host(ctx, _host_ptrs(ctx, U_in), _host_ptrs(ctx, U_out)))
+
+
+def af_sync(ctx) -> None:
+    _check(ctx, _lib().af_sync(ctx))
 
 
 def af_get_stage(ctx, out=None, device: bool = True):
@@ -579,6 +613,12 @@ class Solver:
 
     def step(self, dt_out=None):
         return af_step(self.ctx, dt_out)
+
+    def step_host(self, U_in, U_out):
+        af_step_host(self.ctx, U_in, U_out)
+
+    def sync(self):
+        af_sync(self.ctx)
 
     def status(self, reset: bool = False):
         return af_status(self.ctx, reset)

@@ -36,6 +36,16 @@ struct af_ctx {
   double *dts;            // dt-sensitivity work (5 * af_dt_sens_nblocks() doubles) and mu
   unsigned long long *cnt_pin;   // pinned host copy of the counters before / after a recomputation
   double *divb_buf;       // divergence measures: 2 per block, then the 2 results (allocated on first use)
+  // pipelined host-buffer steps (af_step_host), created on first use: two input
+  // and two output staging states, one copy stream per direction, and per slot
+  // the events "input arrived", "step done with the slot", "output copied"
+  double *pipe_in[2], *pipe_out[2];
+  cudaStream_t h2d, d2h;
+  cudaEvent_t ev_in[2], ev_used[2], ev_out[2];
+  int pipe_ready;
+  int pipe_slot;
+  const char *recent_out[3][4];   // host output ranges of the last three af_step_host calls
+  size_t recent_len[4];
   int timing;
   int nev;                // event pairs in use
   int evcap;
@@ -126,6 +136,14 @@ void bind_states(af_ctx *c, int bn, int bs, int bo) {
     c->dev.un[cls] = cls_ptr(c, bn, cls);
     c->dev.us[cls] = cls_ptr(c, bs, cls);
     c->dev.uo[cls] = cls_ptr_mut(c, bo, cls);
+  }
+}
+
+void bind_ptrs(af_ctx *c, const double *n, const double *st, double *o) {
+  for (int cls = 0; cls < 4; ++cls) {
+    c->dev.un[cls] = n + c->class_off[cls];
+    c->dev.us[cls] = st + c->class_off[cls];
+    c->dev.uo[cls] = o + c->class_off[cls];
   }
 }
 
@@ -655,10 +673,113 @@ int af_step(af_ctx *c, double *dt_used, int on_device) {
   return AF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+int ensure_pipe(af_ctx *c) {
+  if (c->pipe_ready) return AF_OK;
+  const unsigned fl = cudaEventDisableTiming;
+  if (!c->h2d) CK(cudaStreamCreateWithFlags(&c->h2d, cudaStreamNonBlocking), "copy stream");
+  if (!c->d2h) CK(cudaStreamCreateWithFlags(&c->d2h, cudaStreamNonBlocking), "copy stream");
+  for (int k = 0; k < 2; ++k) {
+    if (!c->ev_in[k]) CK(cudaEventCreateWithFlags(&c->ev_in[k], fl), "event");
+    if (!c->ev_used[k]) CK(cudaEventCreateWithFlags(&c->ev_used[k], fl), "event");
+    if (!c->ev_out[k]) CK(cudaEventCreateWithFlags(&c->ev_out[k], fl), "event");
+    if (!c->pipe_in[k] && cudaMalloc(&c->pipe_in[k], c->state_len * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, AF_ENOMEM, "staging state for af_step_host");
+    }
+    if (!c->pipe_out[k] && cudaMalloc(&c->pipe_out[k], c->state_len * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, AF_ENOMEM, "staging state for af_step_host");
+    }
+  }
+  for (int cls = 0; cls < 4; ++cls) c->recent_len[cls] = cls_len(c, cls) * sizeof(double);
+  c->pipe_ready = 1;
+  return AF_OK;
+}
+
+// Does one of the host arrays in[] overlap an output array of the last three calls?
+bool reads_recent_output(const af_ctx *c, const double *const in[4]) {
+  for (int a = 0; a < 4; ++a) {
+    const char *lo = (const char *)in[a], *hi = lo + c->recent_len[a];
+    for (int r = 0; r < 3; ++r)
+      for (int b = 0; b < 4; ++b) {
+        const char *olo = c->recent_out[r][b];
+        if (olo && lo < olo + c->recent_len[b] && olo < hi) return true;
+      }
+  }
+  return false;
+}
+
+int sync_copies(af_ctx *c) {
+  if (c->h2d) CK(cudaStreamSynchronize(c->h2d), "synchronise copy stream");
+  if (c->d2h) CK(cudaStreamSynchronize(c->d2h), "synchronise copy stream");
+  return AF_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int af_step_host(af_ctx *c, const double *const in[4], double *const out[4]) {
+  if (!c || !in || !out) return AF_EINVAL;
+  for (int cls = 0; cls < 4; ++cls)
+    if (!in[cls] || !out[cls]) return fail(c, AF_EINVAL, "state class %d is NULL", cls);
+  if (c->next_stage != 0) return fail(c, AF_EINVAL, "af_step_host called in the middle of a step (stage %d next)", c->next_stage);
+  CK(cudaSetDevice(c->device), "set device");
+  int rc = ensure_pipe(c);
+  if (rc) return rc;
+  const int k = c->pipe_slot;
+  // input copy: after the step that last used this slot, and after every
+  // earlier output copy if the input is (part of) a recent output
+  CK(cudaStreamWaitEvent(c->h2d, c->ev_used[k], 0), "wait");
+  if (reads_recent_output(c, in)) CK(cudaStreamWaitEvent(c->h2d, c->ev_out[k ^ 1], 0), "wait");
+  for (int cls = 0; cls < 4; ++cls)
+    CK(cudaMemcpyAsync(c->pipe_in[k] + c->class_off[cls], in[cls], c->recent_len[cls], cudaMemcpyHostToDevice, c->h2d),
+       "copy state in");
+  CK(cudaEventRecord(c->ev_in[k], c->h2d), "record");
+  // the step: after its input arrived and after the output copy that last read this slot
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in[k], 0), "wait");
+  CK(cudaStreamWaitEvent(c->stream, c->ev_out[k], 0), "wait");
+  double *b1 = c->state[(c->cur + 1) % 3], *b2 = c->state[(c->cur + 2) % 3];
+  const double *u = c->pipe_in[k];
+  bind_ptrs(c, u, u, b1);
+  run_stage(c, RK_A[0], RK_B[0], 1);
+  bind_ptrs(c, u, b1, b2);
+  run_stage(c, RK_A[1], RK_B[1], 0);
+  bind_ptrs(c, u, b2, c->pipe_out[k]);
+  run_stage(c, RK_A[2], RK_B[2], 0);
+  CK(cudaGetLastError(), "stage launch");
+  CK(cudaEventRecord(c->ev_used[k], c->stream), "record");
+  // output copy
+  CK(cudaStreamWaitEvent(c->d2h, c->ev_used[k], 0), "wait");
+  for (int cls = 0; cls < 4; ++cls)
+    CK(cudaMemcpyAsync(out[cls], c->pipe_out[k] + c->class_off[cls], c->recent_len[cls], cudaMemcpyDeviceToHost, c->d2h),
+       "copy state out");
+  CK(cudaEventRecord(c->ev_out[k], c->d2h), "record");
+  for (int r = 2; r > 0; --r)
+    for (int cls = 0; cls < 4; ++cls) c->recent_out[r][cls] = c->recent_out[r - 1][cls];
+  for (int cls = 0; cls < 4; ++cls) c->recent_out[0][cls] = (const char *)out[cls];
+  c->pipe_slot = k ^ 1;
+  c->last_out = c->cur;
+  return AF_OK;
+}
+
+int af_sync(af_ctx *c) {
+  if (!c) return AF_EINVAL;
+  CK(cudaSetDevice(c->device), "set device");
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return sync_copies(c);
+}
+
 int af_status(af_ctx *c, long long *counters, int reset) {
   if (!c) return AF_EINVAL;
   CK(cudaSetDevice(c->device), "set device");
   CK(cudaStreamSynchronize(c->stream), "synchronise");
+  {
+    const int rc = sync_copies(c);
+    if (rc) return rc;
+  }
   AfStatus h;
   CK(cudaMemcpy(&h, c->st, offsetof(AfStatus, repair), cudaMemcpyDeviceToHost), "read status");
   if (counters)
@@ -701,6 +822,8 @@ const char *af_last_error(const af_ctx *c) { return c ? c->msg : "null context";
 void af_destroy(af_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->h2d) cudaStreamSynchronize(c->h2d);
+  if (c->d2h) cudaStreamSynchronize(c->d2h);
   for (int b = 0; b < 3; ++b)
     if (c->state[b]) cudaFree(c->state[b]);
   if (c->work) cudaFree(c->work);
@@ -713,6 +836,15 @@ void af_destroy(af_ctx *c) {
   if (c->inflow_dev) cudaFree(c->inflow_dev);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);
+  for (int k = 0; k < 2; ++k) {
+    if (c->pipe_in[k]) cudaFree(c->pipe_in[k]);
+    if (c->pipe_out[k]) cudaFree(c->pipe_out[k]);
+    if (c->ev_in[k]) cudaEventDestroy(c->ev_in[k]);
+    if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+    if (c->ev_out[k]) cudaEventDestroy(c->ev_out[k]);
+  }
+  if (c->h2d) cudaStreamDestroy(c->h2d);
+  if (c->d2h) cudaStreamDestroy(c->d2h);
   for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);
   free(c->ev);
   free(c->evk);
