@@ -36,10 +36,11 @@ class Params(C.Structure):
                 ("y1", C.c_double), ("cfl", C.c_double), ("kappa", C.c_double), ("bc", C.c_int),
                 ("pp_on", C.c_int), ("src_cell_on", C.c_int), ("src_point_on", C.c_int),
                 ("side", C.c_int * 4), ("inflow_lo", C.c_double), ("inflow_hi", C.c_double),
-                ("inflow_U", C.c_double * 8)]
+                ("inflow_U", C.c_double * 8), ("src_point_upwind", C.c_int)]
 
 
-def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, cfl=None) -> Params:
+def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, cfl=None,
+               src_point_upwind=False) -> Params:
     P = Params(pb.gamma, pb.x0, pb.x1, pb.y0, pb.y1, pb.cfl if cfl is None else cfl,
                pb.kappa if kappa is None else kappa, pb.bc, int(pp_on), int(src_cell_on), int(src_point_on))
     sides = getattr(pb, "sides", (0, 0, 0, 0))
@@ -50,6 +51,7 @@ def params_for(pb, kappa=None, pp_on=True, src_cell_on=True, src_point_on=True, 
     inU = getattr(pb, "inflow_U", None)
     for k in range(8):
         P.inflow_U[k] = float(inU[k]) if inU is not None else 0.0
+    P.src_point_upwind = int(src_point_upwind)
     return P
 
 

@@ -154,6 +154,11 @@ typedef struct {
   int side[4];
   double inflow_lo, inflow_hi;
   double inflow_U[8];
+  // Example 4.2 variant: the derivative of B_l in the divergence of the
+  // point-value source is one-sided along each FVS line, upwind with respect
+  // to v_l of the point (D^+ for v_l > 0, D^- for v_l < 0, the central
+  // average for v_l = 0) instead of the central (D^+ + D^-)/2 of Sec. 2.3.
+  int src_point_upwind;
 } or_params;
 
 // Stats slots (cumulative over the call).
@@ -182,7 +187,7 @@ struct Ctx {
   double x0, y0, in_lo, in_hi, inU[8];
   int nx, ny, bc;
   double dx, dy, gamma, cfl, kappa;
-  int pp_on, src_cell_on, src_point_on;
+  int pp_on, src_cell_on, src_point_on, src_point_upwind;
   int P, R;          // padded extents (x, y)
   int ext[4][2];     // interior extents per DoF class
   size_t plane() const { return (size_t)P * R; }
@@ -194,6 +199,7 @@ static void make_ctx(const or_params *p, int nx, int ny, Ctx &C) {
   C.dx = (p->x1 - p->x0) / nx; C.dy = (p->y1 - p->y0) / ny;
   C.gamma = p->gamma; C.cfl = p->cfl; C.kappa = p->kappa;
   C.pp_on = p->pp_on; C.src_cell_on = p->src_cell_on; C.src_point_on = p->src_point_on;
+  C.src_point_upwind = p->src_point_upwind;
   C.P = nx + 2 * G + 1; C.R = ny + 2 * G + 1;
   int fx = (p->bc == 0) ? nx : nx + 1, fy = (p->bc == 0) ? ny : ny + 1;
   C.ext[0][0] = nx; C.ext[0][1] = ny;
@@ -659,7 +665,10 @@ static void compute_centers(const Ctx &C, State &S, Work &W, long long *st) {
 // spectral radius on the line.  P[0..4] are the points at offsets -1, -1/2, 0,
 // +1/2, +1 (in units of the mesh size); the cell to the left/below holds
 // P[0..2], the one to the right/above holds P[2..4].
-static void fvs_derivative(int l, const PD *const P[5], double h, real *out, real &dBl) {
+// With upw = 0 the derivative of B_l in the point source is the central
+// (D^+ B_l + D^- B_l)/2 of Sec. 2.3; upw = +1 / -1 selects D^+ / D^- alone (the
+// velocity-upwind variant of Example 4.2).
+static void fvs_derivative(int l, const PD *const P[5], double h, real *out, real &dBl, int upw = 0) {
   real al = P[0]->sr[l];
   for (int q = 1; q < 5; ++q) al = rmax(al, P[q]->sr[l]);
   for (int k = 0; k < 8; ++k) {
@@ -668,8 +677,17 @@ static void fvs_derivative(int l, const PD *const P[5], double h, real *out, rea
     for (int q = 0; q < 3; ++q) Fm[q] = real(0.5) * (P[q + 2]->F[l][k] - al * P[q + 2]->U[k]);
     out[k] = Dplus(Fp[0], Fp[1], Fp[2], h) + Dminus(Fm[0], Fm[1], Fm[2], h);
   }
-  // central discrete derivative of B_l: (D^+ B_l + D^- B_l)/2
-  dBl = real(0.5) * (Dplus(P[0]->B[l], P[1]->B[l], P[2]->B[l], h) + Dminus(P[2]->B[l], P[3]->B[l], P[4]->B[l], h));
+  const real Dp = Dplus(P[0]->B[l], P[1]->B[l], P[2]->B[l], h), Dm = Dminus(P[2]->B[l], P[3]->B[l], P[4]->B[l], h);
+  if (upw > 0) dBl = Dp;
+  else if (upw < 0) dBl = Dm;
+  else dBl = real(0.5) * (Dp + Dm);   // central discrete derivative of B_l
+}
+
+// Direction selector of the upwind variant for the FVS line of direction l through point d.
+static int upwind_sign(const Ctx &C, const PD &d, int l) {
+  if (!C.src_point_upwind) return 0;
+  const double v = val(d.v[l]);
+  return v > 0.0 ? 1 : (v < 0.0 ? -1 : 0);
 }
 
 static void point_ho_updates(const Ctx &C, real dt, Work &W) {
@@ -690,13 +708,13 @@ static void point_ho_updates(const Ctx &C, real dt, Work &W) {
           // y-line of corners and x-face values on column f.
           const PD *Px[5] = {&W.pd[3].at(C, i - 1, j), &W.pd[2].at(C, i - 1, j), &me, &W.pd[2].at(C, i, j), &W.pd[3].at(C, i + 1, j)};
           const PD *Py[5] = {&W.pd[3].at(C, i, j - 1), &W.pd[1].at(C, i, j - 1), &me, &W.pd[1].at(C, i, j), &W.pd[3].at(C, i, j + 1)};
-          fvs_derivative(0, Px, dx, d1, dB1);
-          fvs_derivative(1, Py, dy, d2, dB2);
+          fvs_derivative(0, Px, dx, d1, dB1, upwind_sign(C, me, 0));
+          fvs_derivative(1, Py, dy, d2, dB2, upwind_sign(C, me, 1));
         } else if (cls == 1) {
           // x-face (f,j): x-line through the cell-centre values of cells f-1, f;
           // central D_2 F_2 between the corners (f,j) and (f,j+1).
           const PD *Px[5] = {&W.pd[1].at(C, i - 1, j), &W.pdc.at(C, i - 1, j), &me, &W.pdc.at(C, i, j), &W.pd[1].at(C, i + 1, j)};
-          fvs_derivative(0, Px, dx, d1, dB1);
+          fvs_derivative(0, Px, dx, d1, dB1, upwind_sign(C, me, 0));
           const PD &lo = W.pd[3].at(C, i, j), &hi = W.pd[3].at(C, i, j + 1);
           for (int k = 0; k < 8; ++k) d2[k] = Dcen(lo.F[1][k], hi.F[1][k], dy);
           dB2 = Dcen(lo.B[1], hi.B[1], dy);
@@ -707,7 +725,7 @@ static void point_ho_updates(const Ctx &C, real dt, Work &W) {
           for (int k = 0; k < 8; ++k) d1[k] = Dcen(lo.F[0][k], hi.F[0][k], dx);
           dB1 = Dcen(lo.B[0], hi.B[0], dx);
           const PD *Py[5] = {&W.pd[2].at(C, i, j - 1), &W.pdc.at(C, i, j - 1), &me, &W.pdc.at(C, i, j), &W.pd[2].at(C, i, j + 1)};
-          fvs_derivative(1, Py, dy, d2, dB2);
+          fvs_derivative(1, Py, dy, d2, dB2, upwind_sign(C, me, 1));
         }
         real divB = dB1 + dB2;
         real Ps[8];
@@ -1199,11 +1217,11 @@ static void rhs(const Ctx &C, State &S, State &out) {
         if (cls == 3) {
           const PD *Px[5] = {&W.pd[3].at(C, i - 1, j), &W.pd[2].at(C, i - 1, j), &me, &W.pd[2].at(C, i, j), &W.pd[3].at(C, i + 1, j)};
           const PD *Py[5] = {&W.pd[3].at(C, i, j - 1), &W.pd[1].at(C, i, j - 1), &me, &W.pd[1].at(C, i, j), &W.pd[3].at(C, i, j + 1)};
-          fvs_derivative(0, Px, dx, d1, dB1);
-          fvs_derivative(1, Py, dy, d2, dB2);
+          fvs_derivative(0, Px, dx, d1, dB1, upwind_sign(C, me, 0));
+          fvs_derivative(1, Py, dy, d2, dB2, upwind_sign(C, me, 1));
         } else if (cls == 1) {
           const PD *Px[5] = {&W.pd[1].at(C, i - 1, j), &W.pdc.at(C, i - 1, j), &me, &W.pdc.at(C, i, j), &W.pd[1].at(C, i + 1, j)};
-          fvs_derivative(0, Px, dx, d1, dB1);
+          fvs_derivative(0, Px, dx, d1, dB1, upwind_sign(C, me, 0));
           const PD &lo = W.pd[3].at(C, i, j), &hi = W.pd[3].at(C, i, j + 1);
           for (int k = 0; k < 8; ++k) d2[k] = Dcen(lo.F[1][k], hi.F[1][k], dy);
           dB2 = Dcen(lo.B[1], hi.B[1], dy);
@@ -1212,7 +1230,7 @@ static void rhs(const Ctx &C, State &S, State &out) {
           for (int k = 0; k < 8; ++k) d1[k] = Dcen(lo.F[0][k], hi.F[0][k], dx);
           dB1 = Dcen(lo.B[0], hi.B[0], dx);
           const PD *Py[5] = {&W.pd[2].at(C, i, j - 1), &W.pdc.at(C, i, j - 1), &me, &W.pdc.at(C, i, j), &W.pd[2].at(C, i, j + 1)};
-          fvs_derivative(1, Py, dy, d2, dB2);
+          fvs_derivative(1, Py, dy, d2, dB2, upwind_sign(C, me, 1));
         }
         real divB = dB1 + dB2, Ps[8];
         psi(me, Ps);

@@ -819,3 +819,69 @@ def test_1d_reduction_of_the_2d_scheme():
         for k in range(8):
             for got, ref in ((R2[0][k, j], R1[0][k]), (R2[1][k, j], R1[1][k])):
                 assert np.abs(got - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1.0), (j, k)
+
+
+# ---- velocity-upwind divergence in the point source (Example 4.2 variant) ----
+def _upwind_problem(B1, B2, v1, v2, n=12):
+    def prim(x, y):
+        z = np.zeros(np.shape(x))
+        return (z + 1.0, v1(x, y) + z, v2(x, y) + z, z, B1(x, y) + z, B2(x, y) + z, z, z + 1.0)
+    return ai.Problem("upwind", n, n, 0.0, 1.0, 0.0, 1.0, ai.OUTFLOW, 5.0 / 3.0, prim)
+
+
+def test_upwind_source_closed_form_on_quartic_b():
+    """B1 = eps (x - 1/2)^4, B2 constant.  Along a corner's x-line (points dx/2
+    apart) D+ and D- are exact for quadratics and agree on cubics, and on t^4
+    they give +3 dx^3/4 and -3 dx^3/4, so the one-sided divergence differs from
+    the central one by +-(3/4) eps dx^3 with the sign of v1; the y-line carries
+    a constant B2 and differs by nothing.  The right-hand sides then differ by
+    -(that) Psi(U) = -(that) (0, B, v, v.B)."""
+    eps = 1.0
+    pb = _upwind_problem(lambda x, y: eps * (x - 0.5) ** 4, lambda x, y: 0.3 + 0 * x,
+                         lambda x, y: 0.4 * np.cos(np.pi * y) + 0 * x, lambda x, y: 0.2 + 0 * x)
+    U = ai.dofs(pb)
+    rc = oracle.rhs(pb, U)
+    ru = oracle.rhs(pb, U, src_point_upwind=True)
+    corner = U[3]
+    v1 = corner[1] / corner[0]
+    d = 0.75 * eps * pb.dx ** 3 * np.sign(v1)   # divergence change, per corner
+    inner = (slice(2, -2), slice(2, -2))        # away from the mirrored ghosts
+    want_b1 = -d * v1                           # component B1: Psi = v1
+    want_b2 = -d * 0.2                          # component B2: Psi = v2
+    assert np.abs(want_b2[inner]).min() > 1e-5
+    for k, want in ((4, want_b1), (5, want_b2)):
+        got = (ru[3][k] - rc[3][k])[inner]
+        assert np.allclose(got, want[inner], rtol=1e-9, atol=1e-13), k
+    # y-faces: the x-derivative is central and B2 is constant, so nothing changes
+    # beyond the rounding of the one-sided differences of a constant
+    assert np.abs(ru[2] - rc[2]).max() <= 1e-13 * np.abs(rc[2]).max()
+    # cell averages do not use the point divergence
+    assert np.array_equal(ru[0], rc[0])
+
+
+def test_upwind_source_equals_central_on_quadratic_b():
+    """With B quadratic the one-sided and the central differences are all exact
+    (and the bi-parabola's centre values are exact), so every class agrees with
+    the central scheme to rounding."""
+    pb = _upwind_problem(lambda x, y: 0.3 + 0.5 * (x - 0.4) ** 2 + 0.1 * y, lambda x, y: 0.2 + 0.4 * (y - 0.6) ** 2,
+                         lambda x, y: 0.4 * np.cos(np.pi * y), lambda x, y: 0.3 * np.sin(np.pi * x))
+    U = ai.dofs(pb)
+    rc = oracle.rhs(pb, U)
+    ru = oracle.rhs(pb, U, src_point_upwind=True)
+    inner = (slice(None), slice(2, -2), slice(2, -2))   # the mirrored ghosts are not quadratic
+    for a, b in zip(ru, rc):
+        assert np.abs(a - b)[inner].max() <= 1e-12 * np.abs(b).max()
+    # and the choice matters once B is not quadratic
+    pb2 = _upwind_problem(lambda x, y: 0.3 + np.sin(2 * np.pi * x), lambda x, y: 0.2 + 0 * x,
+                          lambda x, y: 0.4 + 0 * x, lambda x, y: 0 * x)
+    U2 = ai.dofs(pb2)
+    assert np.abs(oracle.rhs(pb2, U2, src_point_upwind=True)[3] - oracle.rhs(pb2, U2)[3]).max() > 1e-4
+
+
+def test_upwind_source_at_rest_is_the_central_scheme():
+    """Reading: where v_l = 0 exactly the upwind variant takes the central average."""
+    pb = _upwind_problem(lambda x, y: 0.3 + np.sin(2 * np.pi * x), lambda x, y: 0.2 + np.cos(2 * np.pi * y),
+                         lambda x, y: 0 * x, lambda x, y: 0 * x)
+    U = ai.dofs(pb)
+    for a, b in zip(oracle.rhs(pb, U, src_point_upwind=True), oracle.rhs(pb, U)):
+        assert np.array_equal(a, b)
