@@ -78,6 +78,12 @@ typedef struct af_params {
   int pp_on;         /* positivity-preserving limiters of Sec. 3.2-3.3 and Remark 4.1.  Default 1. */
   int src_cell_on;   /* Godunov-Powell source in the cell-average update (eq. semi_av_src).  Default 1. */
   int src_point_on;  /* Godunov-Powell source in the point-value update (Sec. 2.3).  Default 1. */
+  int src_point_upwind; /* Example 4.2 variant: the derivative of B_l in the divergence of the
+                        point-value source is taken one-sided along each FVS line, upwind for v_l
+                        of the point (D^+ B_l for v_l > 0, D^- B_l for v_l < 0, the central
+                        (D^+ + D^-) / 2 for v_l = 0) instead of central.  The paper reports it
+                        unstable; for study only.  Default 0.  Ignored by the 1D scheme (no
+                        point source); the discrete adjoint rejects it (AF_EINVAL). */
 } af_params;
 
 /* Create a context for an nx x ny grid (nx, ny >= 4), ratio of specific heats

@@ -53,7 +53,7 @@ class AFError(RuntimeError):
 
 class af_params(C.Structure):
     _fields_ = [("cfl", C.c_double), ("kappa", C.c_double), ("pp_on", C.c_int), ("src_cell_on", C.c_int),
-                ("src_point_on", C.c_int)]
+                ("src_point_on", C.c_int), ("src_point_upwind", C.c_int)]
 
 
 def lib_path() -> str:
@@ -173,8 +173,8 @@ def af_set_domain(ctx, x0: float, x1: float, y0: float, y1: float) -> None:
 
 
 def af_set_params(ctx, cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True, src_cell_on: bool = True,
-                  src_point_on: bool = True) -> None:
-    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on))
+                  src_point_on: bool = True, src_point_upwind: bool = False) -> None:
+    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on), int(src_point_upwind))
     _check(ctx, _lib().af_set_params(ctx, C.byref(p)))
 
 
@@ -189,7 +189,7 @@ def af_get_params(ctx) -> dict:
     p = af_params()
     _check(ctx, _lib().af_get_params(ctx, C.byref(p)))
     return {"cfl": p.cfl, "kappa": p.kappa, "pp_on": bool(p.pp_on), "src_cell_on": bool(p.src_cell_on),
-            "src_point_on": bool(p.src_point_on)}
+            "src_point_on": bool(p.src_point_on), "src_point_upwind": bool(p.src_point_upwind)}
 
 
 def af_set_stream(ctx, stream=None) -> None:
@@ -495,8 +495,9 @@ def af_batch_set_domain(b, run, x0, x1, y0, y1):
     _bcheck(b, _lib().af_batch_set_domain(b, run, x0, x1, y0, y1))
 
 
-def af_batch_set_params(b, run, cfl=0.2, kappa=0.0, pp_on=True, src_cell_on=True, src_point_on=True):
-    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on))
+def af_batch_set_params(b, run, cfl=0.2, kappa=0.0, pp_on=True, src_cell_on=True, src_point_on=True,
+                        src_point_upwind=False):
+    p = af_params(cfl, kappa, int(pp_on), int(src_cell_on), int(src_point_on), int(src_point_upwind))
     _bcheck(b, _lib().af_batch_set_params(b, run, C.byref(p)))
 
 
@@ -571,13 +572,13 @@ class Solver:
 
     def __init__(self, nx: int, ny: int, gamma: float, bc: int = AF_BC_PERIODIC, domain=(0.0, 1.0, 0.0, 1.0),
                  cfl: float = 0.2, kappa: float = 0.0, pp_on: bool = True, src_cell_on: bool = True,
-                 src_point_on: bool = True, stream=None, sides=None, inflow=None):
+                 src_point_on: bool = True, stream=None, sides=None, inflow=None, src_point_upwind: bool = False):
         """sides: per-side boundary kinds (left, right, bottom, top) of an outflow grid;
         inflow: (lo, hi, conserved state) for AF_SIDE_INFLOW sides."""
         self.ctx = af_create(nx, ny, gamma, bc)
         self.nx, self.ny, self.bc = nx, ny, bc
         af_set_domain(self.ctx, *domain)
-        af_set_params(self.ctx, cfl, kappa, pp_on, src_cell_on, src_point_on)
+        af_set_params(self.ctx, cfl, kappa, pp_on, src_cell_on, src_point_on, src_point_upwind)
         if stream is not None:
             af_set_stream(self.ctx, stream)
         if sides is not None and any(sides):

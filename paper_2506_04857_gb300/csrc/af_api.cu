@@ -101,6 +101,7 @@ void refresh_grid(af_ctx *c) {
   g.pp_on = c->prm.pp_on;
   g.src_cell_on = c->prm.src_cell_on;
   g.src_point_on = c->prm.src_point_on;
+  g.upwind = c->prm.src_point_upwind;
   g.special = 0;
   for (int k = 0; k < 4; ++k) {
     g.side[k] = c->bc == AF_BC_OUTFLOW ? c->side[k] : 0;
@@ -238,6 +239,7 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   c->prm.pp_on = 1;
   c->prm.src_cell_on = 1;
   c->prm.src_point_on = 1;
+  c->prm.src_point_upwind = 0;
   c->stream = nullptr;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
@@ -505,6 +507,7 @@ int copy_out_buf(af_ctx *c, const double *src, double *const U[4], int on_device
 int af_rhs_vjp(af_ctx *c, const double *const v[4], double *const out[4], int on_device) {
   if (!c || !v || !out) return AF_EINVAL;
   if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
+  if (c->g.upwind) return fail(c, AF_EINVAL, "the transpose covers the central point source only");
   for (int cls = 0; cls < 4; ++cls)
     if (!v[cls] || !out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
   CK(cudaSetDevice(c->device), "set device");
@@ -538,6 +541,7 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
     if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
   if (flags & ~(AF_ADJ_RECORDED | AF_ADJ_DT)) return fail(c, AF_EINVAL, "unknown flags %d", flags);
   if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
+  if (c->g.upwind) return fail(c, AF_EINVAL, "the transpose covers the central point source only");
   const bool with_dt = (flags & AF_ADJ_DT) != 0;
   if (c->g.kappa != 0.0)
     return fail(c, AF_EINVAL, "af_adjoint_step differentiates the scheme with the shock sensor off (kappa = 0)");

@@ -69,6 +69,7 @@ void refresh1(af1d_ctx *c) {
   g.pp_on = c->prm.pp_on;
   g.src_cell_on = 0;   // 1D: no source (B1 is constant)
   g.src_point_on = 0;
+  g.upwind = 0;
 }
 
 void bind1(af1d_ctx *c, int bn, int bs, int bo) {

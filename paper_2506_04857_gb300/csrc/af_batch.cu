@@ -91,6 +91,7 @@ void fill_grid(af_batch *b, int r) {
   g.pp_on = b->prm[r].pp_on;
   g.src_cell_on = b->prm[r].src_cell_on;
   g.src_point_on = b->prm[r].src_point_on;
+  g.upwind = b->prm[r].src_point_upwind;
   for (int k = 0; k < 4; ++k) g.side[k] = 0;
   g.special = 0;
   g.x0 = 0.0;
@@ -182,12 +183,19 @@ void launch_pass(af_batch *b, int pass, const AfRun *tab, double a, double bb, i
   af_launch_batch(pass, tab, b->nruns, b->items, b->nitems, b->block, nblocks, a, bb, reduce_dt, b->stream);
 }
 
+// Does a run use the velocity-upwind point source (its own point-pass kernel)?
+int any_upwind(const af_batch *b) {
+  for (const af_params &p : b->prm)
+    if (p.src_point_upwind) return 1;
+  return 0;
+}
+
 // One stage of every run (rotation b->cur).
 void batch_stage(af_batch *b, int s, int with_dt, int bps_cap) {
   const AfRun *tab = b->tables + (size_t)(b->cur * 3 + s) * b->nruns;
   launch_pass(b, AF_K_POINTDATA, tab, 0, 0, with_dt, bps_cap);
   if (with_dt) af_launch_batch(AF_K_DT, tab, b->nruns, b->items, b->nitems, b->block, 1, 0, 0, 0, b->stream);
-  launch_pass(b, AF_K_POINTS, tab, RK_A[s], RK_B[s], 0, bps_cap);
+  launch_pass(b, AF_K_POINTS, tab, RK_A[s], RK_B[s], any_upwind(b), bps_cap);
   launch_pass(b, AF_K_FACES, tab, RK_A[s], RK_B[s], 0, bps_cap);
   launch_pass(b, AF_K_CELLS, tab, RK_A[s], RK_B[s], 0, bps_cap);
   launch_pass(b, AF_K_FINAL, tab, RK_A[s], RK_B[s], 0, bps_cap);

@@ -42,6 +42,7 @@ struct AfGrid {
   double kappa, cfl;
   double c13;              // 1e-13 / (gamma - 1)
   int pp_on, src_cell_on, src_point_on;
+  int upwind;          // velocity-upwind divergence in the point source (Example 4.2 variant)
   // bc = 1: kind of each side (0 left, 1 right, 2 bottom, 3 top): 0 outflow
   // (mirror), 1 reflective (mirror, normal momentum and B negated), 2 inflow
   // (bottom/top: the inflow state where in_lo < x < in_hi, outflow elsewhere)
@@ -117,9 +118,11 @@ void af_launch_dt1d(const AfDev &d, const AfGrid &g, cudaStream_t s);
 // (device); partials: 2 * af_divb_nblocks(g) doubles
 int af_divb_nblocks(const AfGrid &g);
 void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s);
-// persistent batched launch of one pass (AF_K_* id) over a (run, i0, j0) tile list
+// persistent batched launch of one pass (AF_K_* id) over a (run, i0, j0) tile
+// list; flag: reduce_dt for the point-data pass, "some run uses the upwind
+// point source" for the point pass
 void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
-                     double a, double b, int reduce_dt, cudaStream_t s);
+                     double a, double b, int flag, cudaStream_t s);
 int af_batch_occupancy(int pass, dim3 block);   // resident blocks per SM
 // adjoint (af_adjoint.cu).  With T = (dL/dU)^T v at the state bound in d (after
 // the point-data pass on it), the last kernel writes

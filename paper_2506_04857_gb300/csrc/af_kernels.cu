@@ -428,12 +428,29 @@ __device__ __forceinline__ void gload8(const AfDev &d, const AfGrid &g, int cls,
   }
 }
 
+// 2h times the derivative of B_l at the middle point of a line (spacing h/2)
+// for the point source: the central (D+ B + D- B)/2 of Sec. 2.3 gives
+// (B0 - B4) + 4 (B3 - B1); the velocity-upwind variant of Example 4.2 takes
+// D+ B = (B0 - 4 B1 + 3 B2)/h for upw > 0 and D- B = (4 B3 - B4 - 3 B2)/h for upw < 0.
+__device__ __forceinline__ double b_line(double u0, double u1, double u2, double u3, double u4, int upw) {
+  if (upw > 0) return 2.0 * fma(3.0, u2, fma(-4.0, u1, u0));
+  if (upw < 0) return 2.0 * fma(-3.0, u2, fma(4.0, u3, -u4));
+  return fma(4.0, u3 - u1, u0 - u4);
+}
+
+// Upwind selector of the Example 4.2 variant: the sign of v_l at the point, or 0.
+__device__ __forceinline__ int upwind_sign(const AfGrid &g, double vl) {
+  if (!g.upwind) return 0;
+  return vl > 0.0 ? 1 : (vl < 0.0 ? -1 : 0);
+}
+
 // Accumulate -c * [ (D+ F+ + D- F-) * h ] of direction l along the line P[0..4]
 // into acc (per component), with F^pm = (F +- alpha U)/2.  Writing out D+ and D-:
 // (D+F+ + D-F-) h = ((F0 - F4) + 4 (F3 - F1) + alpha ((U0 + U4) - 4 (U1 + U3) + 6 U2)) / 2.
-// Also returns (D+ B_l + D- B_l) h / 2 * 2 = (B0 - B4) + 4 (B3 - B1) in dBl.
+// Also returns 2h times the derivative of B_l for the point source in dBl (b_line).
 template <int L>
-__device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double c, double *acc, double &dBl) {
+__device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double c, double *acc, double &dBl,
+                                         int upw) {
   const int qsr = L == 0 ? QP_SR1 : QP_SR2;
   double al = pw(P[0], PS, nxa, qsr);
 #pragma unroll
@@ -445,7 +462,7 @@ __device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double
     double dk;
     if (k == 4 + L) {
       dk = al * up;
-      dBl = fma(4.0, u3 - u1, u0 - u4);
+      dBl = b_line(u0, u1, u2, u3, u4, upw);
     } else {
       const int s = (L == 0 ? QP_F1 : QP_F2) + fslot(L, k);
       const double f0 = pw(P[0], PS, nxa, s), f1 = pw(P[1], PS, nxa, s), f3 = pw(P[3], PS, nxa, s),
@@ -458,7 +475,7 @@ __device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double
 
 // fvs_line on ghost-aware points (reflective / inflow sides)
 template <int L>
-__device__ __forceinline__ void fvs_line_g(const PPG *P, double c, double *acc, double &dBl) {
+__device__ __forceinline__ void fvs_line_g(const PPG *P, double c, double *acc, double &dBl, int upw) {
   const int qsr = L == 0 ? QP_SR1 : QP_SR2;
   double al = pwg(P[0], qsr);
 #pragma unroll
@@ -470,7 +487,7 @@ __device__ __forceinline__ void fvs_line_g(const PPG *P, double c, double *acc, 
     double dk;
     if (k == 4 + L) {
       dk = al * up;
-      dBl = fma(4.0, u3 - u1, u0 - u4);
+      dBl = b_line(u0, u1, u2, u3, u4, upw);
     } else {
       const int s = (L == 0 ? QP_F1 : QP_F2) + fslot(L, k);
       dk = fma(al, up, fma(4.0, pwg(P[3], s) - pwg(P[1], s), pwg(P[0], s) - pwg(P[4], s)));
@@ -602,7 +619,7 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   phi[3] = ddiv(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
 }
 
-template <bool GB>
+template <bool GB, bool UP>
 __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b,
                                          int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
@@ -630,37 +647,37 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
                              prefg(d, g, 3, i + 1, j)};
           const PPG Py[5] = {prefg(d, g, 3, i, j - 1), prefg(d, g, 1, i, j - 1), mg, prefg(d, g, 1, i, j),
                              prefg(d, g, 3, i, j + 1)};
-          fvs_line_g<0>(Px, cx, acc, dBx);
-          fvs_line_g<1>(Py, cy, acc, dBy);
+          fvs_line_g<0>(Px, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
+          fvs_line_g<1>(Py, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
           divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
         } else if (cls == 1) {
           const PPG Px[5] = {prefg(d, g, 1, i - 1, j), prefg(d, g, 4, i - 1, j), mg, prefg(d, g, 4, i, j),
                              prefg(d, g, 1, i + 1, j)};
-          fvs_line_g<0>(Px, cx, acc, dBx);
+          fvs_line_g<0>(Px, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
           central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
           divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
         } else {
           central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
           const PPG Py[5] = {prefg(d, g, 2, i, j - 1), prefg(d, g, 4, i, j - 1), mg, prefg(d, g, 4, i, j),
                              prefg(d, g, 2, i, j + 1)};
-          fvs_line_g<1>(Py, cy, acc, dBy);
+          fvs_line_g<1>(Py, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
           divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
         }
       } else if (cls == 3) {
         const PP Px[5] = {pref(d, g, 3, im, j), pref(d, g, 2, ci0, j), me, pref(d, g, 2, ci1, j), pref(d, g, 3, ip, j)};
         const PP Py[5] = {pref(d, g, 3, i, jm), pref(d, g, 1, i, cj0), me, pref(d, g, 1, i, cj1), pref(d, g, 3, i, jp)};
-        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx);
-        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy);
+        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
+        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
         divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
       } else if (cls == 1) {
         const PP Px[5] = {pref(d, g, 1, im, j), pref(d, g, 4, ci0, j), me, pref(d, g, 4, ci1, j), pref(d, g, 1, ip, j)};
-        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx);
+        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
         central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
         divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
       } else {
         central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
         const PP Py[5] = {pref(d, g, 2, i, jm), pref(d, g, 4, i, cj0), me, pref(d, g, 4, i, cj1), pref(d, g, 2, i, jp)};
-        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy);
+        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
         divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
       }
       if (g.src_point_on) {
@@ -1332,14 +1349,17 @@ __global__ void kb_dt(const AfRun *__restrict__ runs, int nruns) {
 }
 // At most 128 registers (4 blocks per SM): the limiter slow path spills a
 // little, the common path runs at twice the occupancy (measured 8 % faster).
-template <bool GB>
+// UP: the velocity-upwind point source (Example 4.2 variant) is compiled in
+// only where it is asked for; the central scheme pays nothing for it.
+template <bool GB, bool UP>
 __global__ void __launch_bounds__(128, 4) k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                 double a, double b, int mode) {
-  b_points<GB>(d, g, AF_IJ, a, b, mode);
+  b_points<GB, UP>(d, g, AF_IJ, a, b, mode);
 }
+template <bool UP>
 __global__ void __launch_bounds__(256, 2) kb_points(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                  int nitems, double a, double b) {
-  AF_BATCH_LOOP(b_points<false>(r->d, r->g, i, j, a, b, 0));
+  AF_BATCH_LOOP((b_points<false, UP>(r->d, r->g, i, j, a, b, 0)));
 }
 template <bool GB>
 __global__ void __launch_bounds__(128) k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
@@ -1510,8 +1530,14 @@ void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *o
   k_divb_sum<<<1, 256, 0, s>>>(partials, (int)(b.x * b.y), out);
 }
 void af_launch_points(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s) {
-  if (g.special) k_points<true><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
-  else k_points<false><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, a, b, mode);
+  const dim3 gr = grid2(g.nxa, g.nya), bl(32, 4);
+  if (g.special) {
+    if (g.upwind) k_points<true, true><<<gr, bl, 0, s>>>(d, g, a, b, mode);
+    else k_points<true, false><<<gr, bl, 0, s>>>(d, g, a, b, mode);
+  } else {
+    if (g.upwind) k_points<false, true><<<gr, bl, 0, s>>>(d, g, a, b, mode);
+    else k_points<false, false><<<gr, bl, 0, s>>>(d, g, a, b, mode);
+  }
 }
 void af_launch_faces(const AfDev &d, const AfGrid &g, int mode, cudaStream_t s) {
   if (g.special) k_faces<true><<<grid2(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, mode);
@@ -1562,11 +1588,15 @@ void af_launch_math_check(int op, const double *x, const double *y, double *out,
 }
 
 void af_launch_batch(int pass, const AfRun *runs, int nruns, const int4 *items, int nitems, dim3 block, int nblocks,
-                     double a, double b, int reduce_dt, cudaStream_t s) {
+                     double a, double b, int flag, cudaStream_t s) {
+  const int reduce_dt = flag;
   switch (pass) {
     case AF_K_POINTDATA: kb_pointdata<<<nblocks, block, 0, s>>>(runs, items, nitems, reduce_dt); break;
     case AF_K_DT: kb_dt<<<(nruns + 127) / 128, 128, 0, s>>>(runs, nruns); break;
-    case AF_K_POINTS: kb_points<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
+    case AF_K_POINTS:
+      if (flag) kb_points<true><<<nblocks, block, 0, s>>>(runs, items, nitems, a, b);
+      else kb_points<false><<<nblocks, block, 0, s>>>(runs, items, nitems, a, b);
+      break;
     case AF_K_FACES: kb_faces<<<nblocks, block, 0, s>>>(runs, items, nitems); break;
     case AF_K_CELLS: kb_cells<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
     case AF_K_FINAL: kb_final<<<nblocks, block, 0, s>>>(runs, items, nitems, a, b); break;
@@ -1580,7 +1610,7 @@ int af_batch_occupancy(int pass, dim3 block) {
   const int threads = block.x * block.y;
   switch (pass) {
     case AF_K_POINTDATA: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_pointdata, threads, 0); break;
-    case AF_K_POINTS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_points, threads, 0); break;
+    case AF_K_POINTS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_points<false>, threads, 0); break;
     case AF_K_FACES: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_faces, threads, 0); break;
     case AF_K_CELLS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_cells, threads, 0); break;
     case AF_K_FINAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kb_final, threads, 0); break;

@@ -116,7 +116,7 @@ __device__ __forceinline__ void b1_points(const AfDev &d, const AfGrid &g, int f
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] = pu(me, k);
     const PP L[5] = {pref(d, g, 1, fm, 0), pref(d, g, 4, c0, 0), me, pref(d, g, 4, c1, 0), pref(d, g, 1, fp, 0)};
-    fvs_line<0>(L, PS, g.nxa, 0.5 * dt * g.rdx, acc, dB);
+    fvs_line<0>(L, PS, g.nxa, 0.5 * dt * g.rdx, acc, dB, 0);
     if (g.pp_on && !clear_of_floor(acc, g)) {
       double out[8];
       int lim, shr, bad;

@@ -93,6 +93,7 @@ extern "C" int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, d
   g.pp_on = 0;
   g.src_cell_on = 1;
   g.src_point_on = 1;
+  g.upwind = 0;
   for (int k = 0; k < 4; ++k) g.side[k] = 0;
   g.special = 0;
   g.x0 = 0.0;

@@ -26,21 +26,21 @@ def members():
     return pbs
 
 
-def make_batch(pbs, stream):
+def make_batch(pbs, stream, upwind=()):
     b = af.af_batch_create([p.nx for p in pbs], [p.ny for p in pbs], [p.gamma for p in pbs], [p.bc for p in pbs])
     af.af_batch_set_stream(b, stream)
     for r, p in enumerate(pbs):
         af.af_batch_set_domain(b, r, p.x0, p.x1, p.y0, p.y1)
-        af.af_batch_set_params(b, r, cfl=p.cfl, kappa=p.kappa, pp_on=(r != 5))
+        af.af_batch_set_params(b, r, cfl=p.cfl, kappa=p.kappa, pp_on=(r != 5), src_point_upwind=(r in upwind))
         af.af_batch_set_state(b, r, [torch.from_numpy(u).cuda() for u in ai.dofs(p)])
     return b
 
 
-def singles(pbs, nsteps, stream):
+def singles(pbs, nsteps, stream, upwind=()):
     out = []
     for r, p in enumerate(pbs):
         s = af.Solver(p.nx, p.ny, p.gamma, p.bc, domain=(p.x0, p.x1, p.y0, p.y1), cfl=p.cfl, kappa=p.kappa,
-                      pp_on=(r != 5), stream=stream)
+                      pp_on=(r != 5), stream=stream, src_point_upwind=(r in upwind))
         s.set_state(ai.dofs(p))
         for _ in range(nsteps):
             s.step(dt_out=False)
@@ -69,6 +69,28 @@ def test_batch_equals_single_runs(graph):
             got = batch_state(b, r, p)
             for x, y in zip(got, ref[r]):
                 assert torch.equal(x, y), (r, p.name)
+        rc, cnt = af.af_batch_status(b)
+        assert rc == af.AF_OK, af.af_batch_last_error(b)
+        af.af_batch_destroy(b)
+
+
+def test_batch_with_upwind_runs():
+    """Runs with the velocity-upwind point source (Example 4.2 variant) next to
+    central ones: the batch selects the point kernel that evaluates the flag per run."""
+    stream = torch.cuda.Stream()
+    pbs = members()
+    up = (1, 3, 4)
+    with torch.cuda.stream(stream):
+        b = make_batch(pbs, stream, upwind=up)
+        af.af_batch_step(b, 4)
+        ref = singles(pbs, 4, stream, upwind=up)
+        plain = singles(pbs, 4, stream)
+        torch.cuda.synchronize()
+        for r, p in enumerate(pbs):
+            got = batch_state(b, r, p)
+            for x, y in zip(got, ref[r]):
+                assert torch.equal(x, y), (r, p.name)
+        assert not all(torch.equal(x, y) for x, y in zip(ref[4], plain[4]))
         rc, cnt = af.af_batch_status(b)
         assert rc == af.AF_OK, af.af_batch_last_error(b)
         af.af_batch_destroy(b)

@@ -66,7 +66,8 @@ def solver_for(pb, **kw):
 
 
 def oracle_kw(kw):
-    return {k: v for k, v in kw.items() if k in ("kappa", "pp_on", "src_cell_on", "src_point_on", "cfl")}
+    return {k: v for k, v in kw.items() if k in ("kappa", "pp_on", "src_cell_on", "src_point_on", "cfl",
+                                                  "src_point_upwind")}
 
 
 # --------------------------------------------------------------------------
@@ -229,6 +230,54 @@ def test_pp_off_and_source_toggles():
     for kw in (dict(pp_on=False, kappa=1.0), dict(src_cell_on=False), dict(src_point_on=False)):
         G, R, _, _ = one_step(pb, **kw)
         assert rel_err(G, R) <= 1e-12, kw
+
+
+def _signed_flow(n=20, bc=ai.PERIODIC):
+    """Smooth periodic data whose velocities change sign, with div B != 0."""
+    tp = 2.0 * math.pi
+
+    def prim(x, y):
+        z = np.zeros(np.shape(x))
+        return (1.0 + 0.2 * np.sin(tp * (x + y)) + z, 0.4 * np.cos(tp * y) + z, 0.3 * np.sin(tp * x) + z, 0.1 + z,
+                0.3 + 0.2 * np.sin(tp * x) * np.cos(tp * y) + z, 0.2 + 0.1 * np.cos(tp * x) + z, z, 1.0 + z)
+    return ai.Problem("signed_flow", n, n, 0.0, 1.0, 0.0, 1.0, bc, 5.0 / 3.0, prim)
+
+
+@pytest.mark.parametrize("bc", [ai.PERIODIC, ai.OUTFLOW])
+def test_upwind_source_parity(bc):
+    """The velocity-upwind point source (Example 4.2 variant): right-hand side and
+    chained steps against the oracle, and the change it makes is not rounding."""
+    pb = _signed_flow(20, bc)
+    U = ai.dofs(pb)
+    s = solver_for(pb, src_point_upwind=True)
+    s.set_state(U)
+    ref_up = oracle.rhs(pb, U, src_point_upwind=True)
+    assert rel_err(s.rhs(), ref_up) <= 1e-12
+    assert rel_err([torch.from_numpy(a) for a in ref_up], oracle.rhs(pb, U)) > 1e-6
+    pb.kappa = 1.0
+    G, R, _, _ = one_step(pb, nsteps=3, kappa=1.0, src_point_upwind=True)
+    assert rel_err(G, R) <= 1e-12
+
+
+def test_upwind_source_vortex_and_limited_stage():
+    """The paper's study case (mu = 1 vortex, 20 x 20, no PP limiting) for 20
+    steps, and one limited stage of the low-beta blast, with the upwind source."""
+    pb = ai.vortex(20)
+    G, R, _, _ = one_step(pb, nsteps=20, pp_on=False, src_point_upwind=True)
+    assert rel_err(G, R) <= 1e-10
+    pb = ai.blast(40)
+    U = ai.dofs(pb)
+    dt = oracle.dt(pb, U)
+    st = np.zeros(oracle.NSTATS, dtype=np.int64)
+    R = oracle.stage(pb, U, U, dt, 0.0, 1.0, stats=st, src_point_upwind=True)
+    G, cnt = fe_on(pb, U, dt, src_point_upwind=True)
+    assert rel_err(G, R) <= 1e-12
+    assert cnt["point_limited"] == st[oracle.STAT_NAMES.index("point_limited")]
+    # the transpose covers the central source only
+    s = solver_for(pb, src_point_upwind=True)
+    s.set_state(U)
+    with pytest.raises(af.AFError):
+        af.af_rhs_vjp(s.ctx, U, device=False)
 
 
 def test_stage_api_matches_step():
