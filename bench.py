@@ -353,7 +353,7 @@ def adjoint_cost(stream, nsteps=200, every=20):
                         "kappa=0, %d steps, checkpoints every %d steps, objective total magnetic energy" % (nsteps, every),
             "forward_ms": fwd, "backward_ms": bwd, "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": bwd / nsteps, "ratio": bwd / fwd,
-            "target": "<= 4", "includes": "segment recompute from checkpoints + per-step stage recompute + 3 VJPs"}
+            "target": "<= 4", "includes": "segment recompute from checkpoints (stage states kept) + point data of 3 stage states + 3 VJPs"}
 
 
 def adjoint_bench(args, desc):

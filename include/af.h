@@ -204,6 +204,23 @@ enum { AF_ADJ_RECORDED = 1, AF_ADJ_DT = 2 };
 int af_adjoint_step(af_ctx *ctx, const double *dt, int dt_on_device, const double *const lam_in[4],
                     double *const lam_out[4], int on_device, int flags);
 
+/* af_adjoint_step with the stage states of the forward step supplied instead
+ * of recomputed (same result, bit for bit).  U1 and U2 (and U3 = U^{n+1},
+ * needed only with AF_ADJ_DT, else may be NULL) are what af_get_stage returned
+ * after stages 0, 1 (and 2) of the forward step from the current state U^n
+ * with this dt; they have the state layout and, like lam_in and lam_out, are
+ * device pointers when on_device = 1, host arrays otherwise.  Only the point
+ * data of U^n, U1 and U2 are formed, so the call cannot tell whether a
+ * positivity limiter acted in the forward stages: the caller establishes it
+ * from the forward step's counters (af_status).  The cell-centre limiter,
+ * which acts in the point data, is checked (AF_EINVAL).  kappa must be 0.
+ * The state is not advanced.  The call synchronises the stream once, at its
+ * end.  Not in the paper: it saves the adjoint two forward stages per step
+ * when the stage states are kept, e.g. during a checkpoint recomputation. */
+int af_adjoint_step_stages(af_ctx *ctx, const double *dt, int dt_on_device, const double *const U1[4],
+                           const double *const U2[4], const double *const U3[4], const double *const lam_in[4],
+                           double *const lam_out[4], int on_device, int flags);
+
 /* af_dt followed by the three stages.  *dt_used (host or device, may be NULL)
  * receives the step's dt. */
 int af_step(af_ctx *ctx, double *dt_used, int on_device);

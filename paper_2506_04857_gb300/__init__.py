@@ -21,7 +21,8 @@ import numpy as np
 
 __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
-    "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step", "af_sensor", "af_dt",
+    "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step",
+    "af_adjoint_step_stages", "af_sensor", "af_dt",
     "af_stage",
     "af_step", "af_step_host", "af_sync", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
     "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
@@ -89,6 +90,7 @@ def _lib():
             lib.af_rhs_vjp.argtypes = [vp, pp, pp, C.c_int]
             lib.af_divb.argtypes = [vp, vp, C.c_int]
             lib.af_adjoint_step.argtypes = [vp, vp, C.c_int, pp, pp, C.c_int, C.c_int]
+            lib.af_adjoint_step_stages.argtypes = [vp, vp, C.c_int, pp, pp, pp, pp, pp, C.c_int, C.c_int]
             lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
             lib.af_last_error.argtypes = [vp]
             lib.af_last_error.restype = C.c_char_p
@@ -340,6 +342,32 @@ def af_adjoint_step(ctx, dt, lam, out=None, device: bool = True, recorded: bool 
         rc = _lib().af_adjoint_step(ctx, C.cast(C.byref(v), C.c_void_p), 0, ptrs, optrs, dev, flags)
     _check(ctx, rc)
     del keep
+    return out
+
+
+def af_adjoint_step_stages(ctx, dt, U1, U2, lam, U3=None, out=None, device: bool = True,
+                           dt_sensitivity: bool = False):
+    """af_adjoint_step with the forward step's stage states U1, U2 (and U3 = U^{n+1} for
+    dt_sensitivity) given, as af_get_stage returned them, instead of recomputed.  The caller
+    has checked, from the forward step's counters, that no positivity limiter acted."""
+    ptrs, dev, keep = _marshal_in(ctx, lam)
+    p1, d1, k1 = _marshal_in(ctx, U1)
+    p2, d2, k2 = _marshal_in(ctx, U2)
+    if U3 is not None:
+        p3, d3, k3 = _marshal_in(ctx, U3)
+    else:
+        p3, d3, k3 = None, dev, None
+    out, optrs, odev = _outputs(ctx, out, device)
+    if len({dev, odev, d1, d2, d3}) != 1:
+        raise ValueError("lam, out and the stage states must all be on the device or all on the host")
+    flags = AF_ADJ_DT if dt_sensitivity else 0
+    if _is_tensor(dt) and dt.is_cuda:
+        dtp, dtd = dt.data_ptr(), 1
+    else:
+        v = C.c_double(float(dt))
+        dtp, dtd = C.cast(C.byref(v), C.c_void_p), 0
+    _check(ctx, _lib().af_adjoint_step_stages(ctx, dtp, dtd, p1, p2, p3, ptrs, optrs, dev, flags))
+    del keep, k1, k2, k3
     return out
 
 

@@ -4,7 +4,8 @@ AFSteps runs n SSP-RK3 steps through libaf, records every step's dt and keeps
 a checkpoint of the state every `checkpoint_every` steps.  It also records,
 from the limiter counters, whether every positivity limiter stayed inactive.
 Its backward pass recomputes each segment from its checkpoint (with the
-recorded dt) and applies af_adjoint_step in reverse, so gradients are those of
+recorded dt), keeping every step's stage states, and applies
+af_adjoint_step_stages in reverse, so gradients are those of
 the discrete scheme with dt held fixed, or, with dt_sensitivity=True, with
 every step's dt differentiated as the function of its state that af_step
 forms (dt = cfl / (max varrho_1/dx + max varrho_2/dy), a subgradient at the
@@ -22,8 +23,8 @@ from typing import List
 
 import torch
 
-from . import (AF_BC_PERIODIC, AF_OK, AFError, Solver, af_adjoint_step, af_get_state, af_last_error, af_set_state,
-               af_stage, af_status, af_step)
+from . import (AF_BC_PERIODIC, AF_OK, AFError, Solver, af_adjoint_step_stages, af_get_stage, af_get_state,
+               af_last_error, af_set_state, af_stage, af_status, af_step)
 
 # counters of the positivity limiters (and of non-admissible states)
 LIMITER_COUNTERS = ("src_limited", "lambda_lt1", "face_theta_lt1", "shrink", "point_limited", "center_limited",
@@ -102,18 +103,23 @@ class AFSteps(torch.autograd.Function):
         for seg in reversed(range(len(ctx.checkpoints))):
             n0 = seg * ctx.every
             n1 = min(ctx.nsteps, n0 + ctx.every)
-            states = []
+            states = []   # per step: U^n and the stage states U1, U2 (and U3 = U^{n+1})
             af_set_state(s.ctx, ctx.checkpoints[seg])
             for n in range(n0, n1):
-                states.append(af_get_state(s.ctx))
+                Un = af_get_state(s.ctx)
                 dt = ctx.dts[n:n + 1]
                 af_stage(s.ctx, 0, dt)
+                U1 = af_get_stage(s.ctx)
                 af_stage(s.ctx, 1, dt)
+                U2 = af_get_stage(s.ctx)
                 af_stage(s.ctx, 2, dt)
+                U3 = af_get_stage(s.ctx) if ctx.dt_sensitivity else None
+                states.append((Un, U1, U2, U3))
             for n in reversed(range(n0, n1)):
-                af_set_state(s.ctx, states[n - n0])
-                lam = af_adjoint_step(s.ctx, ctx.dts[n:n + 1], lam, recorded=True,
-                                      dt_sensitivity=ctx.dt_sensitivity)
+                Un, U1, U2, U3 = states[n - n0]
+                af_set_state(s.ctx, Un)
+                lam = af_adjoint_step_stages(s.ctx, ctx.dts[n:n + 1], U1, U2, lam, U3=U3,
+                                             dt_sensitivity=ctx.dt_sensitivity)
         return (None, None, None, None) + tuple(lam)
 
 

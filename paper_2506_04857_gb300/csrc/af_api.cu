@@ -460,11 +460,23 @@ void bind_pd(af_ctx *c, int set) {
   for (int k = 1; k <= 4; ++k) { c->dev.pd[k] = w; w += AF_NQP * PS; }
   c->dev.uc = w;
 }
-// Transposed operator at the state in buffer `buf` whose point data is in set
-// `set`: the last kernel writes e.out1 (and e.out2), see AfAdjEpi.
-void vjp_at(af_ctx *c, int buf, int set, const AfAdjEpi &e) {
+// State pointers of every pass to the classes U[4] (the point-data pass and
+// the transposed kernels read them and write nothing through them).
+void bind_cls(af_ctx *c, const double *const U[4]) {
+  for (int cls = 0; cls < 4; ++cls) {
+    c->dev.un[cls] = U[cls];
+    c->dev.us[cls] = U[cls];
+    c->dev.uo[cls] = const_cast<double *>(U[cls]);
+  }
+}
+void buf_cls(const af_ctx *c, const double *base, const double *out[4]) {
+  for (int cls = 0; cls < 4; ++cls) out[cls] = base + c->class_off[cls];
+}
+// Transposed operator at the state U (class pointers) whose point data is in
+// set `set`: the last kernel writes e.out1 (and e.out2), see AfAdjEpi.
+void vjp_at(af_ctx *c, const double *const U[4], int set, const AfAdjEpi &e) {
   bind_pd(c, set);
-  bind_states(c, buf, buf, buf);
+  bind_cls(c, U);
   double *tp[4];
   class_ptrs(c, abuf(c, 1), tp);
   const size_t PS = (size_t)c->g.nxa * c->g.nya;
@@ -527,29 +539,93 @@ int af_rhs_vjp(af_ctx *c, const double *const v[4], double *const out[4], int on
   }
   bind_states(c, c->cur, c->cur, c->cur);
   af_launch_pointdata(c->dev, c->g, 0, c->stream);
-  vjp_at(c, c->cur, 2, epi(vp, op, 0.0, 1.0, nullptr));
+  const double *Ucur[4];
+  buf_cls(c, c->state[c->cur], Ucur);
+  vjp_at(c, Ucur, 2, epi(vp, op, 0.0, 1.0, nullptr));
   CK(cudaGetLastError(), "vjp launch");
   c->next_stage = 0;
   if (on_device) return AF_OK;
   return copy_out_buf(c, abuf(c, 2), out, 0);
 }
 
-int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double *const lam_in[4],
-                    double *const lam_out[4], int on_device, int flags) {
-  if (!c || !dt || !lam_in || !lam_out) return AF_EINVAL;
+namespace {
+// Reverse sweep of one SSP-RK3 step, shared by af_adjoint_step and
+// af_adjoint_step_stages.  S[0..2] are the class pointers of the stage states
+// U0, U1, U2, whose point data are in the sets 0, 1 and 2; S[3] is U3 =
+// U^{n+1} (read only with_dt).  dt is on the device (c->sc->dt).
+int adjoint_sweep(af_ctx *c, const double *const S[4][4], const double *const lam_in[4], double *const lam_out[4],
+                  int on_device, bool with_dt) {
+  const double *dtp = &c->sc->dt;
+  int rc = AF_OK;
+  // reverse of U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1), U3 = 1/3 U0 + 2/3 FE(U2), FE(U) = U + dt L(U):
+  //   L2 = 2/3 (L3 + dt T(U2) L3),  L1 = 1/4 (L2 + dt T(U1) L2),  W = 3/4 L2 + 1/3 L3,
+  //   L0 = L1 + dt T(U0) L1 + W,    T(U) = (dL/dU)^T
+  double *L3b[4], *L2[4], *L1[4], *W[4], *L0b[4];
+  class_ptrs(c, abuf(c, 0), L3b);
+  class_ptrs(c, abuf(c, 2), L2);
+  class_ptrs(c, abuf(c, 3), L1);
+  class_ptrs(c, abuf(c, 4), W);
+  class_ptrs(c, abuf(c, 1), L0b);   // the scratch of the last VJP; L3 stays readable
+  if (!on_device) {
+    rc = copy_in_buf(c, abuf(c, 0), lam_in, 0);
+    if (rc) return rc;
+  }
+  const double *L3[4];
+  double *L0[4];
+  for (int cls = 0; cls < 4; ++cls) {
+    L3[cls] = on_device ? lam_in[cls] : L3b[cls];
+    L0[cls] = on_device ? lam_out[cls] : L0b[cls];
+  }
+  vjp_at(c, S[2], 2, epi(L3, L2, 2.0 / 3.0, 2.0 / 3.0, dtp));
+  AfAdjEpi e1 = epi(L2, L1, 0.25, 0.25, dtp);
+  for (int cls = 0; cls < 4; ++cls) {
+    e1.out2[cls] = W[cls];
+    e1.z2[cls] = L3[cls];
+  }
+  e1.e = 0.75;
+  e1.f = 1.0 / 3.0;
+  vjp_at(c, S[1], 1, e1);
+  if (with_dt) {   // mu dt from L3, L2, L1 and the stage states, before the last VJP may overwrite L3
+    af_launch_dt_dot(c->g, L3, L2, L1, S[0], S[1], S[2], S[3], c->dts, c->stream);
+  }
+  AfAdjEpi e0 = epi(L1, L0, 1.0, 1.0, dtp);
+  for (int cls = 0; cls < 4; ++cls) e0.z1[cls] = W[cls];
+  e0.c = 1.0;
+  vjp_at(c, S[0], 0, e0);
+  if (with_dt) {
+    bind_pd(c, 0);
+    bind_cls(c, S[0]);
+    af_launch_dt_apply(c->dev, c->g, L0, c->dts, c->dts + 5 * (size_t)af_dt_sens_nblocks(), c->stream);
+    bind_pd(c, 2);
+  }
+  CK(cudaGetLastError(), "adjoint launch");
+  return AF_OK;
+}
+
+// Shared argument checks of the two adjoint steps.
+int adjoint_args(af_ctx *c, const double *dt, const double *const lam_in[4], double *const lam_out[4], int flags) {
+  if (!dt || !lam_in || !lam_out) return fail(c, AF_EINVAL, "NULL argument");
   for (int cls = 0; cls < 4; ++cls)
     if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
   if (flags & ~(AF_ADJ_RECORDED | AF_ADJ_DT)) return fail(c, AF_EINVAL, "unknown flags %d", flags);
   if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
   if (c->g.upwind) return fail(c, AF_EINVAL, "the transpose covers the central point source only");
-  const bool with_dt = (flags & AF_ADJ_DT) != 0;
   if (c->g.kappa != 0.0)
-    return fail(c, AF_EINVAL, "af_adjoint_step differentiates the scheme with the shock sensor off (kappa = 0)");
+    return fail(c, AF_EINVAL, "the adjoint differentiates the scheme with the shock sensor off (kappa = 0)");
+  return AF_OK;
+}
+}  // namespace
+
+int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double *const lam_in[4],
+                    double *const lam_out[4], int on_device, int flags) {
+  if (!c) return AF_EINVAL;
+  int rc = adjoint_args(c, dt, lam_in, lam_out, flags);
+  if (rc) return rc;
+  const bool with_dt = (flags & AF_ADJ_DT) != 0;
   CK(cudaSetDevice(c->device), "set device");
-  int rc = ensure_adjoint(c);
+  rc = ensure_adjoint(c);
   if (!rc) rc = set_dt(c, dt, dt_on_device);
   if (rc) return rc;
-  const double *dtp = &c->sc->dt;
   const size_t cnt_bytes = sizeof(unsigned long long) * 16;
   CK(cudaMemcpyAsync(c->cnt_pin, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
   // recompute U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1) with the recorded dt, each
@@ -573,53 +649,13 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
   }
   CK(cudaGetLastError(), "stage recompute");
   CK(cudaMemcpyAsync(c->cnt_pin + 16, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
-  // reverse of U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1), U3 = 1/3 U0 + 2/3 FE(U2), FE(U) = U + dt L(U):
-  //   L2 = 2/3 (L3 + dt T(U2) L3),  L1 = 1/4 (L2 + dt T(U1) L2),  W = 3/4 L2 + 1/3 L3,
-  //   L0 = L1 + dt T(U0) L1 + W,    T(U) = (dL/dU)^T
-  double *L3b[4], *L2[4], *L1[4], *W[4], *L0b[4];
-  class_ptrs(c, abuf(c, 0), L3b);
-  class_ptrs(c, abuf(c, 2), L2);
-  class_ptrs(c, abuf(c, 3), L1);
-  class_ptrs(c, abuf(c, 4), W);
-  class_ptrs(c, abuf(c, 1), L0b);   // the scratch of the last VJP; L3 stays readable
-  if (!on_device) {
-    rc = copy_in_buf(c, abuf(c, 0), lam_in, 0);
-    if (rc) return rc;
-  }
-  const double *L3[4];
-  double *L0[4];
-  for (int cls = 0; cls < 4; ++cls) {
-    L3[cls] = on_device ? lam_in[cls] : L3b[cls];
-    L0[cls] = on_device ? lam_out[cls] : L0b[cls];
-  }
-  vjp_at(c, b2, 2, epi(L3, L2, 2.0 / 3.0, 2.0 / 3.0, dtp));
-  AfAdjEpi e1 = epi(L2, L1, 0.25, 0.25, dtp);
-  for (int cls = 0; cls < 4; ++cls) {
-    e1.out2[cls] = W[cls];
-    e1.z2[cls] = L3[cls];
-  }
-  e1.e = 0.75;
-  e1.f = 1.0 / 3.0;
-  vjp_at(c, b1, 1, e1);
-  if (with_dt) {   // mu dt from L3, L2, L1 and the stage states, before the last VJP may overwrite L3
-    double *U[4][4];
-    class_ptrs(c, c->state[n], U[0]);
-    class_ptrs(c, c->state[b1], U[1]);
-    class_ptrs(c, c->state[b2], U[2]);
-    class_ptrs(c, abuf(c, 5), U[3]);
-    af_launch_dt_dot(c->g, L3, L2, L1, U[0], U[1], U[2], U[3], c->dts, c->stream);
-  }
-  AfAdjEpi e0 = epi(L1, L0, 1.0, 1.0, dtp);
-  for (int cls = 0; cls < 4; ++cls) e0.z1[cls] = W[cls];
-  e0.c = 1.0;
-  vjp_at(c, n, 0, e0);
-  if (with_dt) {
-    bind_pd(c, 0);
-    bind_states(c, n, n, n);
-    af_launch_dt_apply(c->dev, c->g, L0, c->dts, c->dts + 5 * (size_t)af_dt_sens_nblocks(), c->stream);
-    bind_pd(c, 2);
-  }
-  CK(cudaGetLastError(), "adjoint launch");
+  const double *S[4][4];
+  buf_cls(c, c->state[n], S[0]);
+  buf_cls(c, c->state[b1], S[1]);
+  buf_cls(c, c->state[b2], S[2]);
+  buf_cls(c, abuf(c, 5), S[3]);
+  rc = adjoint_sweep(c, S, lam_in, lam_out, on_device, with_dt);
+  if (rc) return rc;
   c->next_stage = 0;
   if (!on_device) {
     rc = copy_out_buf(c, abuf(c, 1), lam_out, 0);
@@ -632,6 +668,63 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
     if (c->cnt_pin[16 + k] != c->cnt_pin[k])
       return fail(c, AF_EINVAL, "af_adjoint_step: a limiter was active in this step (counter %d); the transpose "
                   "covers the branch on which every limiter is inactive", k);
+  return AF_OK;
+}
+
+int af_adjoint_step_stages(af_ctx *c, const double *dt, int dt_on_device, const double *const U1[4],
+                           const double *const U2[4], const double *const U3[4], const double *const lam_in[4],
+                           double *const lam_out[4], int on_device, int flags) {
+  if (!c) return AF_EINVAL;
+  int rc = adjoint_args(c, dt, lam_in, lam_out, flags);
+  if (rc) return rc;
+  const bool with_dt = (flags & AF_ADJ_DT) != 0;
+  if (!U1 || !U2 || (with_dt && !U3)) return fail(c, AF_EINVAL, "stage states missing");
+  for (int cls = 0; cls < 4; ++cls)
+    if (!U1[cls] || !U2[cls] || (with_dt && !U3[cls])) return fail(c, AF_EINVAL, "stage class %d is NULL", cls);
+  CK(cudaSetDevice(c->device), "set device");
+  rc = ensure_adjoint(c);
+  if (!rc) rc = set_dt(c, dt, dt_on_device);
+  if (rc) return rc;
+  const int n = c->cur, b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+  const double *S[4][4];
+  buf_cls(c, c->state[n], S[0]);
+  if (on_device) {
+    for (int cls = 0; cls < 4; ++cls) {
+      S[1][cls] = U1[cls];
+      S[2][cls] = U2[cls];
+      S[3][cls] = with_dt ? U3[cls] : nullptr;
+    }
+  } else {   // host stage states go to the context's stage buffers (and the spare one)
+    rc = copy_in_buf(c, c->state[b1], U1, 0);
+    if (!rc) rc = copy_in_buf(c, c->state[b2], U2, 0);
+    if (!rc && with_dt) rc = copy_in_buf(c, abuf(c, 5), U3, 0);
+    if (rc) return rc;
+    buf_cls(c, c->state[b1], S[1]);
+    buf_cls(c, c->state[b2], S[2]);
+    buf_cls(c, abuf(c, 5), S[3]);
+  }
+  const size_t cnt_bytes = sizeof(unsigned long long) * 16;
+  CK(cudaMemcpyAsync(c->cnt_pin, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
+  for (int set = 0; set < 3; ++set) {   // point data (and limited centre values) of U0, U1, U2
+    bind_pd(c, set);
+    bind_cls(c, S[set]);
+    af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  }
+  CK(cudaGetLastError(), "point data");
+  CK(cudaMemcpyAsync(c->cnt_pin + 16, c->st->cnt, cnt_bytes, cudaMemcpyDeviceToHost, c->stream), "read status");
+  rc = adjoint_sweep(c, S, lam_in, lam_out, on_device, with_dt);
+  bind_pd(c, 2);
+  bind_states(c, c->cur, c->cur, (c->cur + 1) % 3);
+  if (rc) return rc;
+  c->next_stage = 0;
+  if (!on_device) {
+    rc = copy_out_buf(c, abuf(c, 1), lam_out, 0);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
+  if (c->cnt_pin[16 + ST_CENTER_LIMITED] != c->cnt_pin[ST_CENTER_LIMITED])
+    return fail(c, AF_EINVAL, "af_adjoint_step_stages: the cell-centre limiter acted on a stage state; the transpose "
+                "covers the branch on which every limiter is inactive");
   return AF_OK;
 }
 
