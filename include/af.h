@@ -372,6 +372,9 @@ int af1d_stage(af1d_ctx *ctx, int s, const double *dt, int on_device);
 int af1d_step(af1d_ctx *ctx, double *dt_used, int on_device);
 int af1d_status(af1d_ctx *ctx, long long *counters, int reset);
 const char *af1d_last_error(const af1d_ctx *ctx);
+/* Per-kernel device timing of the 1D stages, as af_timing (the AF_K_* ids name
+ * the 1D kernels of the same passes). */
+int af1d_timing(af1d_ctx *ctx, int enable, double *ms, long long *launches);
 void af1d_destroy(af1d_ctx *ctx);
 
 #ifdef __cplusplus

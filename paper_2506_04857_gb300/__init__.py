@@ -129,6 +129,7 @@ def _lib():
             lib.af1d_stage.argtypes = [vp, C.c_int, vp, C.c_int]
             lib.af1d_step.argtypes = [vp, vp, C.c_int]
             lib.af1d_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
+            lib.af1d_timing.argtypes = [vp, C.c_int, vp, vp]
             lib.af1d_last_error.argtypes = [vp]
             lib.af1d_last_error.restype = C.c_char_p
             lib.af1d_destroy.argtypes = [vp]
@@ -779,6 +780,17 @@ def af1d_status(ctx, reset: bool = False):
     return rc, dict(zip(STAT_NAMES, [int(v) for v in cnt]))
 
 
+def af1d_timing(ctx, enable: bool):
+    """Per-kernel event timing of the 1D stages, as af_timing (names k1_* and k_dt)."""
+    if enable:
+        _check1d(ctx, _lib().af1d_timing(ctx, 1, None, None))
+        return None
+    ms = (C.c_double * len(KERNEL_NAMES))()
+    n = (C.c_longlong * len(KERNEL_NAMES))()
+    _check1d(ctx, _lib().af1d_timing(ctx, 0, C.cast(ms, C.c_void_p), C.cast(n, C.c_void_p)))
+    return {(k if k == "k_dt" else k.replace("k_", "k1_")): (ms[i], int(n[i])) for i, k in enumerate(KERNEL_NAMES)}
+
+
 def af1d_last_error(ctx) -> str:
     return _lib().af1d_last_error(ctx).decode()
 
@@ -819,6 +831,9 @@ class Solver1D:
 
     def status(self, reset: bool = False):
         return af1d_status(self.ctx, reset)
+
+    def timing(self, enable: bool):
+        return af1d_timing(self.ctx, enable)
 
     def close(self):
         if self.ctx:

@@ -28,7 +28,6 @@ struct af_ctx {
   AfScalars *sc;
   AfStatus *st;
   AfDev dev;              // work-array pointers (state pointers set per stage)
-  // per-kernel event timing (af_timing)
   // adjoint workspace (allocated on first use)
   double *adj;            // af_adj_nslots() + 8 arrays per index point
   double *abuf;           // 6 state-sized buffers: lambda copies, VJP scratch, extra stage output
@@ -46,11 +45,7 @@ struct af_ctx {
   int pipe_slot;
   const char *recent_out[3][4];   // host output ranges of the last three af_step_host calls
   size_t recent_len[4];
-  int timing;
-  int nev;                // event pairs in use
-  int evcap;
-  cudaEvent_t *ev;        // 2 * evcap events
-  unsigned char *evk;     // kernel id of each pair
+  AfEventTimer tm;        // per-kernel event timing (af_timing)
   char msg[512];
 };
 
@@ -148,37 +143,11 @@ void bind_ptrs(af_ctx *c, const double *n, const double *st, double *o) {
   }
 }
 
-// Event pair around one launch when timing is on (events are created lazily in chunks).
-bool timing_begin(af_ctx *c, int kernel) {
-  if (!c->timing) return false;
-  if (c->nev == c->evcap) {
-    const int cap = c->evcap ? 2 * c->evcap : 256;
-    cudaEvent_t *ev = (cudaEvent_t *)realloc(c->ev, sizeof(cudaEvent_t) * 2 * cap);
-    unsigned char *evk = (unsigned char *)realloc(c->evk, cap);
-    if (!ev || !evk) {
-      if (ev) c->ev = ev;
-      if (evk) c->evk = evk;
-      return false;
-    }
-    c->ev = ev;
-    c->evk = evk;
-    for (int k = 2 * c->evcap; k < 2 * cap; ++k) cudaEventCreate(&c->ev[k]);
-    c->evcap = cap;
-  }
-  c->evk[c->nev] = (unsigned char)kernel;
-  cudaEventRecord(c->ev[2 * c->nev], c->stream);
-  return true;
-}
-void timing_end(af_ctx *c, bool on) {
-  if (!on) return;
-  cudaEventRecord(c->ev[2 * c->nev + 1], c->stream);
-  c->nev++;
-}
-#define TIMED(kernel, call)                    \
-  do {                                         \
-    bool on_ = timing_begin(c, (kernel));      \
-    call;                                      \
-    timing_end(c, on_);                        \
+#define TIMED(kernel, call)                      \
+  do {                                           \
+    bool on_ = c->tm.begin((kernel), c->stream); \
+    call;                                        \
+    c->tm.end(on_, c->stream);                   \
   } while (0)
 
 // One stage: P1..P5 on the bound buffers.
@@ -892,25 +861,13 @@ int af_timing(af_ctx *c, int enable, double *ms, long long *launches) {
   if (!c) return AF_EINVAL;
   CK(cudaSetDevice(c->device), "set device");
   if (enable) {
-    c->nev = 0;
-    c->timing = 1;
+    c->tm.nev = 0;
+    c->tm.on = 1;
     return AF_OK;
   }
-  c->timing = 0;
+  c->tm.on = 0;
   CK(cudaStreamSynchronize(c->stream), "synchronise");
-  double acc[AF_NKERNEL] = {0};
-  long long cnt[AF_NKERNEL] = {0};
-  for (int p = 0; p < c->nev; ++p) {
-    float t = 0.f;
-    CK(cudaEventElapsedTime(&t, c->ev[2 * p], c->ev[2 * p + 1]), "event time");
-    acc[c->evk[p]] += t;
-    cnt[c->evk[p]]++;
-  }
-  for (int k = 0; k < AF_NKERNEL; ++k) {
-    if (ms) ms[k] = acc[k];
-    if (launches) launches[k] = cnt[k];
-  }
-  c->nev = 0;
+  CK(c->tm.collect(AF_NKERNEL, ms, launches), "event time");
   return AF_OK;
 }
 
@@ -942,9 +899,7 @@ void af_destroy(af_ctx *c) {
   }
   if (c->h2d) cudaStreamDestroy(c->h2d);
   if (c->d2h) cudaStreamDestroy(c->d2h);
-  for (int k = 0; k < 2 * c->evcap; ++k) cudaEventDestroy(c->ev[k]);
-  free(c->ev);
-  free(c->evk);
+  c->tm.destroy();
   delete c;
 }
 

@@ -24,6 +24,7 @@ struct af1d_ctx {
   AfScalars *sc;
   AfStatus *st;
   AfDev dev;
+  AfEventTimer tm;    // per-kernel event timing (af1d_timing)
   char msg[512];
 };
 
@@ -118,7 +119,7 @@ int stage1(af1d_ctx *c, int s, int reduce_dt) {
   if (s == 0) bind1(c, n, n, b1);
   else if (s == 1) bind1(c, n, b1, b2);
   else bind1(c, n, b2, b1);
-  af_launch_stage1d(c->dev, c->g, RK1_A[s], RK1_B[s], reduce_dt, c->stream);
+  af_launch_stage1d(c->dev, c->g, RK1_A[s], RK1_B[s], reduce_dt, c->stream, &c->tm);
   CK1(cudaGetLastError(), "stage launch");
   c->last_out = s == 1 ? b2 : b1;
   if (s == 2) c->cur = b1;
@@ -297,6 +298,20 @@ int af1d_status(af1d_ctx *c, long long *counters, int reset) {
 
 const char *af1d_last_error(const af1d_ctx *c) { return c ? c->msg : "null context"; }
 
+int af1d_timing(af1d_ctx *c, int enable, double *ms, long long *launches) {
+  if (!c) return AF_EINVAL;
+  CK1(cudaSetDevice(c->device), "set device");
+  if (enable) {
+    c->tm.nev = 0;
+    c->tm.on = 1;
+    return AF_OK;
+  }
+  c->tm.on = 0;
+  CK1(cudaStreamSynchronize(c->stream), "synchronise");
+  CK1(c->tm.collect(AF_NKERNEL, ms, launches), "event time");
+  return AF_OK;
+}
+
 void af1d_destroy(af1d_ctx *c) {
   if (!c) return;
   cudaSetDevice(c->device);
@@ -305,6 +320,7 @@ void af1d_destroy(af1d_ctx *c) {
   if (c->work) cudaFree(c->work);
   if (c->sc) cudaFree(c->sc);
   if (c->st) cudaFree(c->st);
+  c->tm.destroy();
   delete c;
 }
 

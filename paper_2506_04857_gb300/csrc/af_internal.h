@@ -10,6 +10,7 @@
 // nxa = nx (+1 for outflow), nya = ny (+1 for outflow).
 #pragma once
 #include <cuda_runtime.h>
+#include <cstdlib>
 #include <stdint.h>
 
 #define AF_NQP 20   // per point value: F1 (7), F2 (7), varrho_1, varrho_2, v (3), v.B
@@ -112,7 +113,64 @@ void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, dou
                         cudaStream_t s);
 // the 1D scheme (af_kernels1d.cuh) on the 2D structures with ny = 1: one stage
 // out = a U^n + b FE(U^s) (the dt pass first when reduce_dt), and the dt pass alone
-void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s);
+// Per-kernel CUDA-event timing of a context's launches (af_timing, af1d_timing):
+// an event pair around every launch while enabled; events are created lazily in
+// chunks and kept until destroy().
+struct AfEventTimer {
+  int on = 0, nev = 0, cap = 0;
+  cudaEvent_t *ev = nullptr;      // 2 * cap events
+  unsigned char *kid = nullptr;   // kernel id of each pair
+  bool begin(int kernel, cudaStream_t s) {
+    if (!on) return false;
+    if (nev == cap) {
+      const int nc = cap ? 2 * cap : 256;
+      cudaEvent_t *e = (cudaEvent_t *)realloc(ev, sizeof(cudaEvent_t) * 2 * nc);
+      if (e) ev = e;
+      unsigned char *k = (unsigned char *)realloc(kid, nc);
+      if (k) kid = k;
+      if (!e || !k) return false;
+      for (int q = 2 * cap; q < 2 * nc; ++q) cudaEventCreate(&ev[q]);
+      cap = nc;
+    }
+    kid[nev] = (unsigned char)kernel;
+    cudaEventRecord(ev[2 * nev], s);
+    return true;
+  }
+  void end(bool started, cudaStream_t s) {
+    if (!started) return;
+    cudaEventRecord(ev[2 * nev + 1], s);
+    nev++;
+  }
+  // Sums per kernel id (nk ids) after the caller synchronised the stream; clears the record.
+  cudaError_t collect(int nk, double *ms, long long *launches) {
+    for (int k = 0; k < nk; ++k) {
+      if (ms) ms[k] = 0.0;
+      if (launches) launches[k] = 0;
+    }
+    for (int p = 0; p < nev; ++p) {
+      float t = 0.f;
+      const cudaError_t e = cudaEventElapsedTime(&t, ev[2 * p], ev[2 * p + 1]);
+      if (e != cudaSuccess) return e;
+      if (kid[p] < nk) {
+        if (ms) ms[kid[p]] += t;
+        if (launches) launches[kid[p]]++;
+      }
+    }
+    nev = 0;
+    return cudaSuccess;
+  }
+  void destroy() {
+    for (int q = 0; q < 2 * cap; ++q) cudaEventDestroy(ev[q]);
+    free(ev);
+    free(kid);
+    ev = nullptr;
+    kid = nullptr;
+    cap = nev = on = 0;
+  }
+};
+// One 1D stage; t (may be NULL) times each launch.
+void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s,
+                       AfEventTimer *t);
 void af_launch_dt1d(const AfDev &d, const AfGrid &g, cudaStream_t s);
 // divergence measures of Example 4.4 of the state bound in d.us into out[2]
 // (device); partials: 2 * af_divb_nblocks(g) doubles

@@ -925,6 +925,28 @@ __device__ __noinline__ void flux_limiter_box(const double *L1, const double (*H
   }
 }
 
+// Certificate that every vertex of the Sec. 3.2 box around L1 is in S_p with
+// room to spare and needs no density scaling, so that the full procedure
+// would return Lambda = 1 exactly: with V = L1 + d, |d_k| <= D_k = sum_I
+// |H_I,k|, q(V) >= q(L1) - T, T bounding the linear, quadratic and cubic terms.
+__device__ __forceinline__ bool box_certified(const double *L1, const double *D, const AfGrid &g) {
+  const double rho = L1[0], E = L1[7];
+  const double bb = fma(L1[4], L1[4], fma(L1[5], L1[5], L1[6] * L1[6]));
+  const double mm = fma(L1[1], L1[1], fma(L1[2], L1[2], L1[3] * L1[3]));
+  const double q0 = fma(rho, E, -0.5 * mm) - rho * fma(0.5, bb, g.c13);
+  const double bD = fma(absd(L1[4]), D[4], fma(absd(L1[5]), D[5], absd(L1[6]) * D[6]));
+  const double mD = fma(absd(L1[1]), D[1], fma(absd(L1[2]), D[2], absd(L1[3]) * D[3]));
+  const double DB2 = fma(D[4], D[4], fma(D[5], D[5], D[6] * D[6]));
+  const double DM2 = fma(D[1], D[1], fma(D[2], D[2], D[3] * D[3]));
+  const double T1 = fma(absd(E - fma(0.5, bb, g.c13)), D[0], fma(rho, D[7], fma(rho, bD, mD)));
+  const double T2 = fma(D[0], D[7], fma(0.5, DM2, fma(0.5 * rho, DB2, D[0] * bD)));
+  const double T3 = 0.5 * D[0] * DB2;
+  const double T = T1 + T2 + T3;
+  const double scale = fma(rho, absd(E), fma(0.5, mm, fma(0.5 * rho, bb, T)));
+  // density rectangle: Lambda^rho = 1 when rho(L1) - 1e-13 >= 1e-12 + sum |rho(H)|
+  return (q0 - T >= 1e-12 * scale) && (rho - 1e-13 >= (1e-12 + D[0]) * (1.0 + 1e-10));
+}
+
 // Full Sec. 3.2 steps (1)-(2) for one cell (slow path).
 __device__ __noinline__ void cell_limiter_full(const double *Ullf, const double *dS, double dtts, const double (*H)[8],
                                                const AfGrid &g, double *L1, double *Lam, int &srclim, NewtonLog &nl) {
@@ -1099,27 +1121,10 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           fast = L1[0] >= 1e-13 && qform(L1, g.c13) >= 0.0;
         }
         if (fast) {
-          // Certificate that every vertex of [0,1]^4 is in S_p with room to
-          // spare: with V = L1 + d, |d_k| <= D_k = sum_I |H_I,k|,
-          // q(V) >= q(L1) - T, T bounding the linear, quadratic and cubic terms.
           double D[8];
 #pragma unroll
           for (int k = 0; k < 8; ++k) D[k] = fma(cxf, absd(Gf[0][k]) + absd(Gf[1][k]), cyf * (absd(Gf[2][k]) + absd(Gf[3][k])));
-          const double rho = L1[0], E = L1[7];
-          const double bb = fma(L1[4], L1[4], fma(L1[5], L1[5], L1[6] * L1[6]));
-          const double mm = fma(L1[1], L1[1], fma(L1[2], L1[2], L1[3] * L1[3]));
-          const double q0 = fma(rho, E, -0.5 * mm) - rho * fma(0.5, bb, g.c13);
-          const double bD = fma(absd(L1[4]), D[4], fma(absd(L1[5]), D[5], absd(L1[6]) * D[6]));
-          const double mD = fma(absd(L1[1]), D[1], fma(absd(L1[2]), D[2], absd(L1[3]) * D[3]));
-          const double DB2 = fma(D[4], D[4], fma(D[5], D[5], D[6] * D[6]));
-          const double DM2 = fma(D[1], D[1], fma(D[2], D[2], D[3] * D[3]));
-          const double T1 = fma(absd(E - fma(0.5, bb, g.c13)), D[0], fma(rho, D[7], fma(rho, bD, mD)));
-          const double T2 = fma(D[0], D[7], fma(0.5, DM2, fma(0.5 * rho, DB2, D[0] * bD)));
-          const double T3 = 0.5 * D[0] * DB2;
-          const double T = T1 + T2 + T3;
-          const double scale = fma(rho, absd(E), fma(0.5, mm, fma(0.5 * rho, bb, T)));
-          // density rectangle: Lambda^rho = 1 when rho(L1) - 1e-13 >= 1e-12 + sum |rho(H)|
-          fast = (q0 - T >= 1e-12 * scale) && (rho - 1e-13 >= (1e-12 + D[0]) * (1.0 + 1e-10));
+          fast = box_certified(L1, D, g);
         }
         if (fast) {
           Lam[0] = Lam[1] = Lam[2] = Lam[3] = 1.0;
@@ -1324,6 +1329,16 @@ __device__ void b_repair(const AfDev &d, const AfGrid &g, double a, double b) {
 // persistent grid walking a (run, tile) work list; tiles are blockDim-sized).
 // ---------------------------------------------------------------------------
 #define AF_IJ blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y
+
+// On grids with reflective or inflow sides, a thread block whose whole tile
+// lies at least kFrame indices inside [0, nx) x [0, ny) touches no ghost (the
+// stencils of the point, face and cell passes reach 2 indices), so it runs the
+// plain code; only the blocks of the boundary frame resolve ghosts.
+constexpr int kFrame = 4;
+__device__ __forceinline__ bool interior_block(int nx, int ny) {
+  const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
+  return i0 >= kFrame && j0 >= kFrame && i0 + (int)blockDim.x + kFrame <= nx && j0 + (int)blockDim.y + kFrame <= ny;
+}
 #define AF_BATCH_LOOP(call)                                       \
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {       \
     const int4 w = items[it];                                     \
@@ -1354,7 +1369,8 @@ __global__ void kb_dt(const AfRun *__restrict__ runs, int nruns) {
 template <bool GB, bool UP>
 __global__ void __launch_bounds__(128, 4) k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                 double a, double b, int mode) {
-  b_points<GB, UP>(d, g, AF_IJ, a, b, mode);
+  if (GB && interior_block(g.nx, g.ny)) b_points<false, UP>(d, g, AF_IJ, a, b, mode);
+  else b_points<GB, UP>(d, g, AF_IJ, a, b, mode);
 }
 template <bool UP>
 __global__ void __launch_bounds__(256, 2) kb_points(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
@@ -1364,7 +1380,8 @@ __global__ void __launch_bounds__(256, 2) kb_points(const AfRun *__restrict__ ru
 template <bool GB>
 __global__ void __launch_bounds__(128) k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                int mode) {
-  b_faces<GB>(d, g, AF_IJ, mode);
+  if (GB && interior_block(g.nx, g.ny)) b_faces<false>(d, g, AF_IJ, mode);
+  else b_faces<GB>(d, g, AF_IJ, mode);
 }
 __global__ void __launch_bounds__(256) kb_faces(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                 int nitems) {
@@ -1373,7 +1390,8 @@ __global__ void __launch_bounds__(256) kb_faces(const AfRun *__restrict__ runs, 
 template <bool GB>
 __global__ void __launch_bounds__(128) k_cells(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                double a, double b, int mode) {
-  b_cells<GB>(d, g, AF_IJ, a, b, mode);
+  if (GB && interior_block(g.nx, g.ny)) b_cells<false>(d, g, AF_IJ, a, b, mode);
+  else b_cells<GB>(d, g, AF_IJ, a, b, mode);
 }
 __global__ void __launch_bounds__(256, 2) kb_cells(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                 int nitems, double a, double b) {

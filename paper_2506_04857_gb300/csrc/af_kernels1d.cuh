@@ -217,11 +217,23 @@ __device__ __forceinline__ void b1_cells(const AfDev &d, const AfGrid &g, int i,
       }
     } else {
       if (dt * ((FX(i, 0, QF_AL) + FX(ip, 0, QF_AL)) * g.rdx) > 1.0 + 1e-12) ncfl = 1;   // Lemma 3.1 (count only)
-      const double eps_rho = fmin(1e-13, Ullf[0]);
-      const double eps_p = fmin(1e-13, pressure(Ullf, g.gm1));
       double Lam[4];
-      flux_limiter_box(Ullf, H, eps_rho, eps_p, g.gm1, Lam, nl);
-      nlam = lt_one(Lam[0]) || lt_one(Lam[1]);
+      // fast path: where the box provably needs no limiting, Lambda = 1 exactly
+      bool fast = Ullf[0] >= 1e-13 && qform(Ullf, g.c13) >= 0.0;
+      if (fast) {
+        double D[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) D[k] = absd(H[0][k]) + absd(H[1][k]);
+        fast = box_certified(Ullf, D, g);
+      }
+      if (fast) {
+        Lam[0] = Lam[1] = 1.0;
+      } else {
+        const double eps_rho = fmin(1e-13, Ullf[0]);
+        const double eps_p = fmin(1e-13, pressure(Ullf, g.gm1));
+        flux_limiter_box(Ullf, H, eps_rho, eps_p, g.gm1, Lam, nl);
+        nlam = lt_one(Lam[0]) || lt_one(Lam[1]);
+      }
 #pragma unroll
       for (int k = 0; k < 8; ++k) d.lim1[k * PS + i] = Ullf[k];
       d.lam[0 * PS + i] = Lam[0];
@@ -369,17 +381,24 @@ __global__ void k1_repair(const __grid_constant__ AfDev d, const __grid_constant
 
 }  // namespace
 
-// One 1D stage: P1 (with the dt pass when reduce_dt), P2..P5 and the repair pass.
-void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s) {
+// One 1D stage: P1 (with the dt pass when reduce_dt), P2..P5 and the repair
+// pass; t (may be NULL) brackets each launch with an event pair.
+void af_launch_stage1d(const AfDev &d, const AfGrid &g, double a, double b, int reduce_dt, cudaStream_t s,
+                       AfEventTimer *t) {
   const unsigned nb = (unsigned)((g.nxa + 127) / 128);
-  k1_pointdata<<<nb, 128, 0, s>>>(d, g, reduce_dt);
-  if (reduce_dt) k_dt<<<1, 32, 0, s>>>(d, g);
-  k1_points<<<nb, 128, 0, s>>>(d, g, a, b);
-  k1_faces<<<nb, 128, 0, s>>>(d, g);
-  k1_cells<<<nb, 128, 0, s>>>(d, g, a, b);
+  auto timed = [&](int k, auto launch) {
+    const bool on = t && t->begin(k, s);
+    launch();
+    if (t) t->end(on, s);
+  };
+  timed(AF_K_POINTDATA, [&] { k1_pointdata<<<nb, 128, 0, s>>>(d, g, reduce_dt); });
+  if (reduce_dt) timed(AF_K_DT, [&] { k_dt<<<1, 32, 0, s>>>(d, g); });
+  timed(AF_K_POINTS, [&] { k1_points<<<nb, 128, 0, s>>>(d, g, a, b); });
+  timed(AF_K_FACES, [&] { k1_faces<<<nb, 128, 0, s>>>(d, g); });
+  timed(AF_K_CELLS, [&] { k1_cells<<<nb, 128, 0, s>>>(d, g, a, b); });
   if (g.pp_on) {
-    k1_final<<<nb, 128, 0, s>>>(d, g, a, b);
-    k1_repair<<<1, 32, 0, s>>>(d, g, a, b);
+    timed(AF_K_FINAL, [&] { k1_final<<<nb, 128, 0, s>>>(d, g, a, b); });
+    timed(AF_K_REPAIR, [&] { k1_repair<<<1, 32, 0, s>>>(d, g, a, b); });
   }
 }
 void af_launch_dt1d(const AfDev &d, const AfGrid &g, cudaStream_t s) {
