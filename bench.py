@@ -45,18 +45,29 @@ WORKLOADS = {
                     lambda: ai.orszag_tang(64)),
     "adjoint256": ("discrete adjoint: 256x256 perturbed vortex, kappa=0, 200 steps, checkpoints every 20",
                    lambda: ai.perturbed_vortex(256, seed=0)),
+    "jets1024": ("MHD jets (Example 4.8) 1024x3072: left half, reflective at x=0, Mach-800 inflow jet at the "
+                 "bottom, B_a=sqrt(20000), kappa=2", lambda: ai.jets(1024)),
+    "blast1d": ("1D strong blast (p = 1000 / 0.1, B = (100/sqrt(4pi))(1,1,0)/sqrt(2)) on 4,194,304 cells, "
+                "outflow, kappa=1", lambda: ai.blast1d(1 << 22)),
+    "divb2048": ("divergence measures (Example 4.4) of the 2048x2048 low-beta blast after 3 steps",
+                 lambda: ai.blast(2048)),
 }
 
 # Algorithmic FP64 flops per cell-stage of each kernel: the arithmetic of the
 # scheme as the paper writes it, with the PP limiters off (their tests and
 # occasional blends are extra work, not counted), counted by the counting
-# build of the oracle: python -m oracle.count_flops (64x64 grids; +, -, *, /,
-# sqrt, exp, min/max, |.| one flop each).
+# build of the oracle: python -m oracle.count_flops (64x64 grids, the jets on
+# 256x768, the 1D blast on 4096 cells; +, -, *, /, sqrt, exp, min/max, |.| one
+# flop each).
 ALGO_FLOPS = {
     "blast_low_beta": {"k_pointdata": 714.9, "k_points": 1294.8, "k_faces": 253.9, "k_cells": 628.0, "k_final": 16.3},
     "orszag_tang": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 250.0, "k_cells": 628.0, "k_final": 16.0},
     "vortex": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 234.0, "k_cells": 468.0, "k_final": 16.0},
+    "jets": {"k_pointdata": 720.7, "k_points": 1271.6, "k_faces": 250.7, "k_cells": 628.0, "k_final": 16.1},
+    "blast1d": {"k1_pointdata": 432.4, "k1_points": 332.1, "k1_faces": 93.0, "k1_cells": 96.0, "k1_final": 16.0},
 }
+# Flops per cell of the two divergence measures (af_divb), same counter.
+ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
@@ -162,6 +173,9 @@ def window_problem(pb, i0, j0, w):
 
 def cpu_sample_problem(key, pb, w):
     """The bounded CPU sample of a workload: a w x w window on its most active region."""
+    if key.startswith("jets"):
+        sub = ai.jets(128)
+        return sub, "the jets problem at %dx%d with its own sides" % (sub.nx, sub.ny)
     if key.startswith("blast"):
         # window straddling the blast front (radius 0.1 = 204.8 cells from the centre)
         c = pb.nx // 2
@@ -198,16 +212,44 @@ def run_oracle_steps(sub, steps, budget_s=None):
     return done, time.perf_counter() - t0
 
 
-def cpu_baseline(key, pb, budget_s=12.0, w=512):
-    """The oracle, as it stands, timed on the host cores on a bounded sample."""
+def cpu_unit(key, pb, w):
+    """The oracle's bounded sample of a workload: (one call, units per call,
+    metric, unit, description)."""
     import oracle
     oracle.build()
-    sub, desc = cpu_sample_problem(key, pb, w)
-    run_oracle_steps(sub, 1)   # warm-up (first-touch, thread pool)
-    n, t = run_oracle_steps(sub, 1000, budget_s=budget_s)
-    cs = sub.nx * sub.ny * 3 * n
-    return {"value": cs / t, "unit": "cell-stage updates/s", "cores": threads_used(), "kind": "oracle",
-            "sample": "%s, %d SSP-RK3 steps in %.1f s" % (desc, n, t)}
+    if key == "blast1d":
+        sub = ai.blast1d(1 << 16, kappa=pb.kappa)
+        st = [ai.dofs1(sub)]
+
+        def run():
+            st[0], _ = oracle.step1(sub, st[0])
+        return (run, sub.n * 3, "FP64 AF-MHD 1D cell-stage updates/s", "cell-stage updates/s",
+                "the same blast on %d cells, one SSP-RK3 step per call" % sub.n)
+    if key == "divb2048":
+        sub, d = cpu_sample_problem("blast", pb, w)
+        V = ai.dofs(sub)
+        return (lambda: oracle.divb(sub, V), sub.nx * sub.ny, "FP64 divergence-measure cell evaluations/s",
+                "cell evaluations/s", d + " (initial state), both measures per call")
+    sub, d = cpu_sample_problem(key, pb, w)
+    st = [ai.dofs(sub)]
+
+    def run():
+        st[0], _ = oracle.step(sub, st[0])
+    return run, sub.nx * sub.ny * 3, "FP64 AF-MHD cell-stage updates/s", "cell-stage updates/s", \
+        d + ", one SSP-RK3 step per call"
+
+
+def cpu_baseline(key, pb, budget_s=12.0, w=512):
+    """The oracle, as it stands, timed on the host cores on a bounded sample."""
+    run, units, _, unit, desc = cpu_unit(key, pb, w)
+    run()   # warm-up (first-touch, thread pool)
+    t0, n = time.perf_counter(), 0
+    while n < 1000 and time.perf_counter() - t0 < budget_s:
+        run()
+        n += 1
+    t = time.perf_counter() - t0
+    return {"value": units * n / t, "unit": unit, "cores": threads_used(), "kind": "oracle",
+            "sample": "%s: %d calls in %.1f s" % (desc, n, t)}
 
 
 def reference_arm(args, key, desc, pb):
@@ -215,22 +257,25 @@ def reference_arm(args, key, desc, pb):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    import oracle
-    oracle.build()
-    sub, sdesc = cpu_sample_problem(key, pb, 128)
+    run, units, metric, unit, sdesc = cpu_unit(key, pb, 128)
     for _ in range(args.warmup):
-        run_oracle_steps(sub, 1)
-    n, t = run_oracle_steps(sub, args.steps)
-    value = sub.nx * sub.ny * 3 * n / t
-    line = {"metric": "FP64 AF-MHD cell-stage updates/s", "value": value, "unit": "cell-stage updates/s",
+        run()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run()
+    t = time.perf_counter() - t0
+    value = units * args.steps / t
+    cells = pb.n if hasattr(pb, "n") else pb.nx * pb.ny
+    line = {"metric": metric, "value": value, "unit": unit,
             "impl": "reference", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t / n, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "nx": pb.nx, "ny": pb.ny, "cells": pb.nx * pb.ny, "sample": sdesc},
-            "cpu_baseline": {"value": value, "unit": "cell-stage updates/s", "cores": threads_used(),
-                             "kind": "oracle", "sample": "%s, one SSP-RK3 step per timed step" % sdesc},
-            "e2e": {"value": value, "unit": "cell-stage updates/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": desc, "cells": cells, "sample": sdesc},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": threads_used(),
+                             "kind": "oracle", "sample": "%s, one call per timed step" % sdesc},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if hasattr(pb, "nx"):
+        line["config"]["nx"], line["config"]["ny"] = pb.nx, pb.ny
     print(json.dumps(line), flush=True)
     return 0
 
@@ -373,6 +418,179 @@ def adjoint_bench(args, desc):
     return 0
 
 
+def l2_note(state_bytes):
+    if state_bytes > 129e6:
+        return "state %.2f GB per buffer > 129 MB L2 (no flush needed)" % (state_bytes * 1e-9)
+    return "no L2 flush; state (%.0f MB) smaller than L2" % (state_bytes * 1e-6)
+
+
+def fp64_peak(torch, local, clk):
+    props = torch.cuda.get_device_properties(local)
+    max_mhz = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
+    peak = FP64_FLOPS_PER_SM_CYCLE * props.multi_processor_count * max_mhz * 1e6 * 1e-12
+    return peak, "derived: 2 DFMA/SM/cycle x %d SMs x %.0f MHz x 2 flops" % (props.multi_processor_count, max_mhz)
+
+
+def setup_ranks(torch):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local, dist
+
+
+def oned_bench(args, desc):
+    """The 1D scheme (af1d_*) on one long grid: every rank runs its own replica
+    (weak scaling); per-kernel times from af1d_timing."""
+    import torch
+    import paper_2506_04857_gb300 as af
+
+    world, rank, local, dist = setup_ranks(torch)
+    stream = torch.cuda.current_stream()
+    pb = WORKLOADS[args.workload][1]()
+    U0 = ai.dofs1(pb)
+    s = af.Solver1D(pb.n, pb.gamma, pb.bc, domain=(pb.x0, pb.x1), cfl=pb.cfl, kappa=pb.kappa, stream=stream)
+    s.set_state([torch.from_numpy(u).cuda() for u in U0])
+    for _ in range(args.warmup):
+        s.step(dt_out=False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.step(dt_out=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ktimes = s.timing(False)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    clk = clocks.stop()
+    rc, cnt = s.status(reset=True)
+    if rc != af.AF_OK:
+        raise SystemExit("libaf reported %s after the timed region" % af.af1d_last_error(s.ctx))
+    value = pb.n * 3 * args.steps * world / (ms * 1e-3)
+    flops = ALGO_FLOPS[pb.name]
+    dom = max((k for k in ktimes if k in flops), key=lambda k: ktimes[k][0])
+    avg_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
+    peak, peak_src = fp64_peak(torch, local, clk)
+    achieved = flops[dom] * pb.n / (avg_ms * 1e-3) * 1e-12
+    step_tf = sum(flops.values()) * pb.n * 3 * args.steps / (ms * 1e-3) * 1e-12 / world
+    tot = sum(v[0] for v in ktimes.values())
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "algorithmic_flops_per_cell_stage": flops[dom], "step_achieved_tflops": step_tf,
+                "step_frac": step_tf / peak,
+                "kernel_time_share": {k: round(v[0] / tot, 4) for k, v in ktimes.items() if v[1]}}
+    # end to end through the C ABI with host buffers (blocking copies)
+    host = [np.ascontiguousarray(u) for u in U0]
+    out = [np.empty_like(u) for u in host]
+    nbytes = sum(u.nbytes for u in host)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        s.set_state(host)
+        s.step(dt_out=False)
+        s.get_state(out=out, device=False)
+    te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": pb.n * 3 * 3 * world / te, "unit": "cell-stage updates/s", "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": 3, "api": "af1d_set_state + af1d_step + af1d_get_state"}
+    if rank == 0:
+        line = {"metric": "FP64 AF-MHD 1D cell-stage updates/s", "value": value, "unit": "cell-stage updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (analytic initial condition, af_inputs)",
+                "config": {"workload": desc, "cells": pb.n, "gamma": pb.gamma, "cfl": pb.cfl, "kappa": pb.kappa,
+                           "bc": "outflow", "per_rank_replica": world > 1, "l2": l2_note(nbytes)},
+                "gpu_launches": sum(n for _, n in ktimes.values()), "roofline": roofline, "e2e": e2e,
+                "clocks": clk, "limiter_counters": cnt}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload, pb, budget_s=10.0)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def divb_bench(args, desc):
+    """The divergence measures (af_divb) of one state, repeatedly: the state after
+    3 steps of the 2048x2048 low-beta blast; one call = k_divb + k_divb_sum."""
+    import torch
+    import paper_2506_04857_gb300 as af
+
+    world, rank, local, dist = setup_ranks(torch)
+    stream = torch.cuda.current_stream()
+    pb = WORKLOADS[args.workload][1]()
+    s = af.Solver(pb.nx, pb.ny, pb.gamma, pb.bc, domain=(pb.x0, pb.x1, pb.y0, pb.y1), cfl=pb.cfl, kappa=pb.kappa,
+                  stream=stream)
+    s.set_state([torch.from_numpy(u).cuda() for u in ai.dofs(pb)])
+    for _ in range(3):
+        s.step(dt_out=False)
+    res = torch.empty(2, dtype=torch.float64, device="cuda")
+    calls = max(args.steps, 10)
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        s.divb(out=res)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(calls):
+        s.divb(out=res)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    clk = clocks.stop()
+    cells = pb.nx * pb.ny
+    value = cells * calls * world / (ms * 1e-3)
+    peak, peak_src = fp64_peak(torch, local, clk)
+    fl = ALGO_FLOPS_DIVB[pb.name]
+    achieved = fl * cells / (ms / calls * 1e-3) * 1e-12
+    state_bytes = cells * 32 * 8   # the four classes, read once per call
+    roofline = {"bound": "alu", "kernel": "k_divb + k_divb_sum (one call)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "algorithmic_flops_per_cell": fl,
+                "hbm_bound_cells_per_s": measured_peaks().get("hbm_gbs", 6775.6) * 1e9 / (32 * 8)}
+    # end to end: host state in, the two measures out
+    host = [torch.from_numpy(u).pin_memory() for u in s.get_state(device=False)]
+    t0 = time.perf_counter()
+    for _ in range(3):
+        s.set_state(host)
+        s.divb()
+    te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e = {"value": cells * 3 * world / te, "unit": "cell evaluations/s", "h2d_bytes_per_step": state_bytes,
+           "d2h_bytes_per_step": 16, "steps": 3, "api": "af_set_state (pinned host) + af_divb (host result)"}
+    if rank == 0:
+        line = {"metric": "FP64 divergence-measure cell evaluations/s", "value": value,
+                "unit": "cell evaluations/s", "n_gpus": world, "steps": calls, "warmup": warm,
+                "ms_per_step": ms / calls, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (analytic initial condition, af_inputs, 3 steps)",
+                "config": {"workload": desc, "nx": pb.nx, "ny": pb.ny, "cells": cells,
+                           "per_rank_replica": world > 1, "l2": l2_note(state_bytes)},
+                "gpu_launches": 2 * calls, "roofline": roofline, "e2e": e2e, "clocks": clk,
+                "measures": [float(v) for v in res.cpu()]}
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload, pb, budget_s=10.0)
+        print(json.dumps(line), flush=True)
+    s.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +609,10 @@ def main():
         return ensemble_bench(args, desc)
     if key == "adjoint256" and args.impl == "ours":
         return adjoint_bench(args, desc)
+    if key == "blast1d" and args.impl == "ours":
+        return oned_bench(args, desc)
+    if key == "divb2048" and args.impl == "ours":
+        return divb_bench(args, desc)
     pb = make()
     if args.impl == "reference":
         return reference_arm(args, key, desc, pb)
@@ -409,8 +631,11 @@ def main():
     stream = torch.cuda.current_stream()
 
     U0 = ai.dofs(pb)
+    sides = {}
+    if any(pb.sides):   # reflective / inflow sides (the jets)
+        sides = dict(sides=pb.sides, inflow=(pb.inflow_lo, pb.inflow_hi, pb.inflow_U))
     s = af.Solver(pb.nx, pb.ny, pb.gamma, pb.bc, domain=(pb.x0, pb.x1, pb.y0, pb.y1), cfl=pb.cfl, kappa=pb.kappa,
-                  stream=stream)
+                  stream=stream, **sides)
     dev_state = [torch.from_numpy(u).cuda() for u in U0]
     s.set_state(dev_state)
     peak_fp64 = af.af_probe_fp64(stream)
@@ -509,8 +734,7 @@ def main():
                 "config": {"workload": desc, "nx": pb.nx, "ny": pb.ny, "cells": cells, "gamma": pb.gamma,
                            "cfl": pb.cfl, "kappa": pb.kappa, "bc": "outflow" if pb.bc == ai.OUTFLOW else "periodic",
                            "per_rank_replica": world > 1,
-                           "l2": "state 1.07 GB per buffer >> 129 MB L2 (no flush needed)" if key == "blast2048"
-                           else "no L2 flush; state smaller than L2"},
+                           "l2": l2_note(sum(u.nbytes for u in U0))},
                 "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "clocks": clk,
                 "limiter_counters": cnt}
         if not args.no_adjoint and world == 1:

@@ -194,13 +194,13 @@ def sensor(pb, U, **kw):
     return tx, ty
 
 
-def divb(pb, U, **kw):
+def divb(pb, U, count=False, **kw):
     """(divB_1, divB_2): the two discrete divergence measures of Example 4.4 (node
     divergences of the bi-parabola; Simpson edge integral of B.n per cell)."""
     P = params_for(pb, **kw)
     U = _check(U, pb.nx, pb.ny, pb.bc)
     out = np.zeros(2)
-    _lib().or_divb(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(out))
+    _lib(count).or_divb(C.byref(P), pb.nx, pb.ny, _ptrs(U), _dp(out))
     return float(out[0]), float(out[1])
 
 
@@ -214,17 +214,17 @@ def _check1(U, pb):
     return [A, P]
 
 
-def dt1(pb, U, **kw) -> float:
+def dt1(pb, U, count=False, **kw) -> float:
     P = params_for(pb, **kw)
-    return _lib().or1d_dt(C.byref(P), pb.n, _ptrs(_check1(U, pb)))
+    return _lib(count).or1d_dt(C.byref(P), pb.n, _ptrs(_check1(U, pb)))
 
 
-def stage1(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, **kw):
+def stage1(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, count=False, **kw):
     P = params_for(pb, **kw)
     Un, Us = _check1(Un, pb), _check1(Us, pb)
     out = [np.zeros_like(Un[0]), np.zeros_like(Un[1])]
     st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
-    _lib().or1d_stage(C.byref(P), pb.n, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
+    _lib(count).or1d_stage(C.byref(P), pb.n, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
                       st.ctypes.data_as(C.POINTER(C.c_longlong)))
     return out
 
