@@ -93,6 +93,36 @@ def test_fe_stage_parity(case):
 
 
 @pytest.mark.parametrize("case", ["jets", "blast_reflect"])
+def test_fe_stage_parity_with_interior_blocks(case):
+    """Grids wide enough (>= 68 indices) that the thread blocks of the interior run
+    the plain kernels and only the boundary frame resolves ghosts: limited stages
+    on the oracle's stage inputs of one step, <= 1e-12 with equal counters."""
+    pb = ai.jets(80) if case == "jets" else blast_b2(72, 80, 0.0)
+    if case == "blast_reflect":
+        pb.kappa = 1.0
+    assert pb.nx >= 68 and pb.ny >= 12
+    Un = ai.dofs(pb)
+    dt = oracle.dt(pb, Un)
+    Us = Un
+    for a, b in [(0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)]:
+        st = np.zeros(oracle.NSTATS, dtype=np.int64)
+        R = oracle.stage(pb, Us, Us, dt, 0.0, 1.0, stats=st)
+        s = solver(pb)
+        s.set_state(Us)
+        s.stage(0, dt)
+        G = s.get_stage(device=False)
+        rc, cnt = s.status()
+        assert rc == af.AF_OK, af.af_last_error(s.ctx)
+        assert rel_err(G, R, pb) <= 1e-12, case
+        for q, name in enumerate(oracle.STAT_NAMES):
+            if name in ("center_limited", "point_limited", "sensor_lt099", "lambda_lt1", "src_limited",
+                        "face_theta_lt1", "shrink", "nonadmissible", "newton_solves", "cell_shrink"):
+                assert cnt[name] == st[q], (case, name, cnt[name], st[q])
+        s.close()
+        Us = oracle.stage(pb, Un, Us, dt, a, b)
+
+
+@pytest.mark.parametrize("case", ["jets", "blast_reflect"])
 def test_chained_steps_sensor_off(case):
     pb = ai.jets(16) if case == "jets" else blast_b2(12, 20, 0.0)
     pb.kappa = 0.0
