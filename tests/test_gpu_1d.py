@@ -206,3 +206,25 @@ def test_1d_reduction_of_the_2d_path():
             for k in range(8):
                 ref = G1[c][k]
                 assert np.abs(G2[c][k, j] - ref).max() <= 1e-13 * max(np.abs(ref).max(), 1.0), (c, j, k)
+
+
+def test_kernel_timing_counts_every_launch():
+    """af1d_timing brackets every launch of the 1D stages: over two steps with the
+    positivity limiters on, each pass runs 6 times, the dt pass twice, and the
+    timed steps give the same state as untimed ones."""
+    pb = ai.blast1d(400)
+    U = ai.dofs1(pb)
+    s, r = solver(pb), solver(pb)
+    s.set_state(U)
+    r.set_state(U)
+    s.timing(True)
+    for _ in range(2):
+        s.step(dt_out=False)
+        r.step(dt_out=False)
+    t = s.timing(False)
+    for k in ("k1_pointdata", "k1_points", "k1_faces", "k1_cells", "k1_final", "k1_repair"):
+        assert t[k][1] == 6 and t[k][0] > 0.0, (k, t[k])
+    assert t["k_dt"][1] == 2
+    for a, b in zip(s.get_state(), r.get_state()):
+        assert torch.equal(a, b)
+    assert s.timing(False)["k1_points"][1] == 0   # the record is cleared
