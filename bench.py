@@ -239,8 +239,7 @@ def cpu_unit(key, pb, w):
         d + ", one SSP-RK3 step per call"
 
 
-def cpu_baseline(key, pb, budget_s=12.0, w=512):
-    """The oracle, as it stands, timed on the host cores on a bounded sample."""
+def cpu_rate(key, pb, budget_s, w):
     run, units, _, unit, desc = cpu_unit(key, pb, w)
     run()   # warm-up (first-touch, thread pool)
     t0, n = time.perf_counter(), 0
@@ -250,6 +249,21 @@ def cpu_baseline(key, pb, budget_s=12.0, w=512):
     t = time.perf_counter() - t0
     return {"value": units * n / t, "unit": unit, "cores": threads_used(), "kind": "oracle",
             "sample": "%s: %d calls in %.1f s" % (desc, n, t)}
+
+
+def cpu_baseline(key, pb, budget_s=12.0, w=512):
+    """The oracle, as it stands, timed on the host cores on a bounded sample,
+    and on one core (a child process with OMP_NUM_THREADS=1, a 128-cell-wide
+    sample for about 8 s)."""
+    res = cpu_rate(key, pb, budget_s, w)
+    try:
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", key, "--cpu-rate-only"],
+                             env=env, capture_output=True, text=True, timeout=120)
+        res["single_thread"] = json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:   # the multi-core figure stands alone
+        res["single_thread"] = {"unavailable": str(e)[:200]}
+    return res
 
 
 def reference_arm(args, key, desc, pb):
@@ -602,9 +616,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--cpu-rate-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     key = args.workload
     desc, make = WORKLOADS[key]
+    if args.cpu_rate_only:   # child of cpu_baseline: the oracle on the cores it was given
+        print(json.dumps(cpu_rate(key, make(), 8.0, 128)), flush=True)
+        return 0
     if key == "ensemble256" and args.impl == "ours":
         return ensemble_bench(args, desc)
     if key == "adjoint256" and args.impl == "ours":
