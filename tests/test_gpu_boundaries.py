@@ -196,3 +196,41 @@ def test_jets_paper_size():
           % (n, t, cnt["shrink"], cnt["cell_shrink"], cnt["point_limited"], cnt["lambda_lt1"], cnt["nonadmissible"]))
     assert cnt["nonadmissible"] == 0
     assert 3000 < n < 15000
+
+
+def test_full_size_jets_sampled():
+    """The benchmark's size and launch configuration (jets, 1024x3072, reflective
+    at x = 0, inflow at the bottom): one limited stage of the whole grid on the
+    GPU, checked on sampled 48x48 windows run by the oracle as sub-problems that
+    keep the true sides they touch (cells within 4 of an artificial window edge
+    are not compared)."""
+    import dataclasses
+    pb = ai.jets(1024)
+    nx, ny, w, pad = pb.nx, pb.ny, 48, 4
+    U = ai.dofs(pb)
+    dt = oracle.dt(pb, U)
+    s = solver(pb)
+    s.set_state(U)
+    s.stage(0, dt)
+    G = s.get_stage(device=False)
+    rc, cnt = s.status()
+    assert rc == af.AF_OK, af.af_last_error(s.ctx)
+    edge = int(round((pb.inflow_lo - pb.x0) / pb.dx))   # column of the jet's edge x = inflow_lo
+    starts = [(nx - w, 0), (edge - w // 2, 0), (0, 0), (nx - w, ny - w), (500, 1500), (nx - w, 1500)]
+    ext = [(w, w), (w + 1, w), (w, w + 1), (w + 1, w + 1)]
+    for i0, j0 in starts:
+        sides = (pb.sides[0] if i0 == 0 else 0, pb.sides[1] if i0 + w == nx else 0,
+                 pb.sides[2] if j0 == 0 else 0, pb.sides[3] if j0 + w == ny else 0)
+        sub = dataclasses.replace(pb, nx=w, ny=w, x0=pb.x0 + i0 * pb.dx, x1=pb.x0 + (i0 + w) * pb.dx,
+                                  y0=pb.y0 + j0 * pb.dy, y1=pb.y0 + (j0 + w) * pb.dy, sides=sides)
+        V = [np.ascontiguousarray(U[c][:, j0:j0 + e[1], i0:i0 + e[0]]) for c, e in enumerate(ext)]
+        R = oracle.stage(sub, V, V, dt, 0.0, 1.0)
+        lo_i, hi_i = (0 if i0 == 0 else pad), (w if i0 + w == nx else w - pad)
+        lo_j, hi_j = (0 if j0 == 0 else pad), (w if j0 + w == ny else w - pad)
+        A, B = [], []
+        for c in range(4):
+            ex, ey = (1 if c in (1, 3) else 0), (1 if c in (2, 3) else 0)
+            hic, hjc = hi_i + (ex if hi_i == w else 0), hi_j + (ey if hi_j == w else 0)
+            A.append(G[c][:, j0 + lo_j:j0 + hjc, i0 + lo_i:i0 + hic])
+            B.append(R[c][:, lo_j:hjc, lo_i:hic])
+        assert rel_err(A, B, pb) <= 1e-12, (i0, j0)
