@@ -86,7 +86,9 @@ typedef struct af_params {
                         point source); the discrete adjoint rejects it (AF_EINVAL). */
 } af_params;
 
-/* Create a context for an nx x ny grid (nx, ny >= 4), ratio of specific heats
+/* Create a context for an nx x ny grid (nx, ny >= 4, ny < 262140 and
+ * (nx+1)(ny+1) < 2^28, else AF_EINVAL; larger grids would not fit in device
+ * memory in any case), ratio of specific heats
  * gamma > 1, boundary condition bc (AF_BC_PERIODIC or AF_BC_OUTFLOW; outflow
  * mirrors the DoFs across the boundary, the paper names the condition only).
  * Uses the current CUDA device.  The domain defaults to [0,1]^2 and the
@@ -280,7 +282,8 @@ int af_math_check(int op, const double *x, const double *y, double *out, long lo
  * persistent kernel launch over a (run, tile) work list for all runs, dt is
  * computed per run, and each run's result is bitwise identical to stepping it
  * alone with an af_ctx.  Device memory: one arena, about 360 doubles per cell
- * of every run.  State layout per run: as for af_ctx (af_sizes). */
+ * of every run.  State layout per run: as for af_ctx (af_sizes); grid
+ * limits per run as for af_create. */
 typedef struct af_batch af_batch;
 int af_batch_create(int nruns, const int *nx, const int *ny, const double *gamma, const int *bc, af_batch **out);
 int af_batch_set_domain(af_batch *b, int run, double x0, double x1, double y0, double y1);

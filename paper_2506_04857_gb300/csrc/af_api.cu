@@ -195,7 +195,7 @@ extern "C" {
 int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   if (!out) return AF_EINVAL;
   *out = nullptr;
-  if (nx < 4 || ny < 4 || !(gamma > 1.0) || (bc != AF_BC_PERIODIC && bc != AF_BC_OUTFLOW)) return AF_EINVAL;
+  if (!af_grid_fits(nx, ny) || !(gamma > 1.0) || (bc != AF_BC_PERIODIC && bc != AF_BC_OUTFLOW)) return AF_EINVAL;
   af_ctx *c = new (std::nothrow) af_ctx();
   if (!c) return AF_ENOMEM;
   c->nx = nx;

@@ -222,7 +222,7 @@ int af_batch_create(int nruns, const int *nx, const int *ny, const double *gamma
   if (!out || nruns <= 0 || !nx || !ny || !gamma || !bc) return AF_EINVAL;
   *out = nullptr;
   for (int r = 0; r < nruns; ++r)
-    if (nx[r] < 4 || ny[r] < 4 || !(gamma[r] > 1.0) || (bc[r] != AF_BC_PERIODIC && bc[r] != AF_BC_OUTFLOW))
+    if (!af_grid_fits(nx[r], ny[r]) || !(gamma[r] > 1.0) || (bc[r] != AF_BC_PERIODIC && bc[r] != AF_BC_OUTFLOW))
       return AF_EINVAL;
   af_batch *b = new (std::nothrow) af_batch();
   if (!b) return AF_ENOMEM;

@@ -113,6 +113,13 @@ void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, dou
                         cudaStream_t s);
 // the 1D scheme (af_kernels1d.cuh) on the 2D structures with ny = 1: one stage
 // out = a U^n + b FE(U^s) (the dt pass first when reduce_dt), and the dt pass alone
+// Largest grids: the launch shape (32 x 4 thread blocks, at most 65535 block
+// rows) bounds ny, and the adjoint's DoF ids (class << 28 | index) bound the
+// points of a class.  Either bound lies far beyond what fits in device memory.
+inline bool af_grid_fits(int nx, int ny) {
+  return nx >= 4 && ny >= 4 && (long long)ny + 1 <= 4LL * 65535 && ((long long)nx + 1) * ((long long)ny + 1) < (1LL << 28);
+}
+
 // Per-kernel CUDA-event timing of a context's launches (af_timing, af1d_timing):
 // an event pair around every launch while enabled; events are created lazily in
 // chunks and kept until destroy().
