@@ -16,6 +16,13 @@
 // Citations are to sections / equations of the paper.  Where the paper is
 // silent or ambiguous the reading taken is marked "Reading:".
 //
+// Parity unpinned: the values that the positivity limiters (theta, Lambda of
+// Sec. 3.2, theta* and theta** of Sec. 3.3) take on shocked data.  The paper
+// prints none, so only their invariants are pinned (ranges in [0,1], the
+// limited states in the admissible set, Lambda = 1 on smooth data, brute force
+// on tiny boxes); the GPU path is compared with this file where both take the
+// same branch.
+//
 // Data layout of every user array: one DoF class is [8][nyp][nxp] doubles,
 // conserved variables U = (rho, rho v1, rho v2, rho v3, B1, B2, B3, E), x
 // fastest.  Classes: 0 cell average, 1 x-face (vertical face) value, 2 y-face
