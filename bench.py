@@ -391,12 +391,12 @@ def adjoint_cost(stream, nsteps=200, every=20):
                   stream=stream)
     U0 = [torch.from_numpy(u).cuda() for u in ai.dofs(pb)]
 
-    def once(n):
+    def once(n, sens=False):
         X0 = [t.clone().requires_grad_(True) for t in U0]
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         torch.cuda.synchronize()
         ev[0].record(stream)
-        out = af_steps(s, X0, n, checkpoint_every=every)
+        out = af_steps(s, X0, n, checkpoint_every=every, dt_sensitivity=sens)
         ev[1].record(stream)
         J = magnetic_energy(out, pb.dx, pb.dy, pb.bc)
         ev[2].record(stream)
@@ -407,12 +407,15 @@ def adjoint_cost(stream, nsteps=200, every=20):
 
     once(2 * every)                   # warm-up (first adjoint call allocates its workspace)
     fwd, bwd = once(nsteps)
+    fwd_s, bwd_s = once(nsteps, sens=True)   # dt differentiated through its formula
     s.close()
     return {"workload": "256x256 perturbed MHD vortex (random Fourier |k|<=4, amplitude 1e-3 of rho and B), "
                         "kappa=0, %d steps, checkpoints every %d steps, objective total magnetic energy" % (nsteps, every),
             "forward_ms": fwd, "backward_ms": bwd, "forward_ms_per_step": fwd / nsteps,
             "adjoint_ms_per_step": bwd / nsteps, "ratio": bwd / fwd,
-            "target": "<= 4", "includes": "segment recompute from checkpoints (stage states kept) + point data of 3 stage states + 3 VJPs"}
+            "target": "<= 4", "includes": "segment recompute from checkpoints (stage states kept) + point data of 3 stage states + 3 VJPs",
+            "dt_sensitivity": {"forward_ms": fwd_s, "backward_ms": bwd_s, "ratio": bwd_s / fwd_s,
+                               "includes": "as above + U3 kept + the mu dt reduction and the argmax gradient"}}
 
 
 def adjoint_bench(args, desc):
