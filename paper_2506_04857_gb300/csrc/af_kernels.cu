@@ -612,9 +612,13 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double divv = fma(A(e, cj, QA_V1) - A(w, cj, QA_V1), hx, (A(ci, n, QA_V2) - A(ci, s, QA_V2)) * hy);
   const double curl = fma(A(e, cj, QA_V2) - A(w, cj, QA_V2), hx, -(A(ci, n, QA_V1) - A(ci, s, QA_V1)) * hy);
-  const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
-  const double ph2 = ddiv(-divv, den);
-  phi[2] = ph2 > 0.0 ? ph2 : 0.0;
+  if (is_zero(divv)) {   // -0 / den gives 0: no square root or quotient needed
+    phi[2] = 0.0;
+  } else {
+    const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
+    const double ph2 = ddiv(-divv, den);
+    phi[2] = ph2 > 0.0 ? ph2 : 0.0;
+  }
   const double num = (Ub(e, cj, 4) - Ub(w, cj, 4)) + (Ub(ci, n, 5) - Ub(ci, s, 5));
   phi[3] = ddiv(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
 }
@@ -760,7 +764,8 @@ __device__ __forceinline__ double theta_s(const AfDev &d, const AfGrid &g, int d
   get_phi<GB>(d, g, ia, ja, pa);
   get_phi<GB>(d, g, ib, jb, pb);
   const double p1 = maxnn(pa[dir], pb[dir]), p2 = maxnn(pa[2], pb[2]), p3 = maxnn(pa[3], pb[3]);
-  return exp(-g.kappa * fma(p1, p2, p3));
+  const double arg = -g.kappa * fma(p1, p2, p3);
+  return is_zero(arg) ? 1.0 : exp(arg);   // quiet data: exp(-0) = 1 without the call
 }
 
 // One face in direction L between cell averages ca, cb (mapped indices),

@@ -20,6 +20,9 @@ namespace afm {
 
 __device__ __forceinline__ unsigned hi32(double x) { return (unsigned)__double2hiint(x); }
 
+// x == +0 or -0, on the integer pipe
+__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
 // true when the FP32 seed path is valid: 2^-123 <= |x| < 2^124
 __device__ __forceinline__ bool seed_ok(double x) {
   unsigned e = (hi32(x) >> 20) & 0x7ffu;
@@ -75,7 +78,7 @@ __device__ __forceinline__ double ddiv(double a, double b) {
 // sqrt(x): s = x * rsqrt-seed, then two Heron corrections s <- s + (x - s^2)/(2 s)
 // with 1/(2 s) taken from the seed.
 __device__ __forceinline__ double dsqrt(double x) {
-  if (!seed_ok(x)) return sqrt(x);
+  if (!seed_ok(x)) return is_zero(x) ? x : sqrt(x);   // sqrt(+-0) = +-0
   float yf = rsqrt_approx_f32(seed_f32(x));
   double y = widen_f32(yf), h = widen_f32(0.5f * yf);
   double s = x * y;
