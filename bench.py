@@ -74,10 +74,10 @@ ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
 FP64_FLOPS_PER_SM_CYCLE = 4.0
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one k_points
 # launch per cell, from one ncu capture of the 1024x1024 low-beta blast
-# (1.035 GB read + 0.254 GB written for 1,048,576 cells); the 2048x2048 launch
+# (1.031 GB read + 0.255 GB written for 1,048,576 cells); the 2048x2048 launch
 # is taken as 4x that (the kernel's traffic is per cell: its own and its
 # neighbours' point data).
-DRAM_BYTES_PER_CELL = {"k_points": 1229.4}
+DRAM_BYTES_PER_CELL = {"k_points": 1226.0}
 # Algorithmic bytes per cell-stage: read U^(s) (32 doubles), read U^n on stages
 # 2 and 3, write U^(s+1): (512 + 768 + 768)/3 B.
 ALGO_BYTES_PER_CS = (512.0 + 768.0 + 768.0) / 3.0
