@@ -1002,39 +1002,52 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           double dx1, dy2;
-          // D^-, D, D^+ of B1 along row m and of B2 along column l (Sec. 2.1)
-          if (l == 0) dx1 = fma(4.0, b1[1][m], -3.0 * b1[0][m]) - b1[2][m];
+          // D^-, D, D^+ of B1 along row m and of B2 along column l (Sec. 2.1), the
+          // one-sided ones as 3 (b1 - b0) - (b2 - b1): exactly 0 on constant data
+          if (l == 0) dx1 = fma(3.0, b1[1][m] - b1[0][m], -(b1[2][m] - b1[1][m]));
           else if (l == 1) dx1 = b1[2][m] - b1[0][m];
-          else dx1 = fma(3.0, b1[2][m], fma(-4.0, b1[1][m], b1[0][m]));
-          if (m == 0) dy2 = fma(4.0, b2[l][1], -3.0 * b2[l][0]) - b2[l][2];
+          else dx1 = fma(3.0, b1[2][m] - b1[1][m], -(b1[1][m] - b1[0][m]));
+          if (m == 0) dy2 = fma(3.0, b2[l][1] - b2[l][0], -(b2[l][2] - b2[l][1]));
           else if (m == 1) dy2 = b2[l][2] - b2[l][0];
-          else dy2 = fma(3.0, b2[l][2], fma(-4.0, b2[l][1], b2[l][0]));
+          else dy2 = fma(3.0, b2[l][2] - b2[l][1], -(b2[l][1] - b2[l][0]));
           wd[l][m] = (w[l] * w[m]) * fma(dx1, rdx, dy2 * rdy);
         }
       // Psi at the nodes: B from the DoFs, v and v.B from the point data
       // node (l,m): corners (l,m even), x-faces (l even, m = 1), y-faces (l = 1, m even), centre (1,1)
       S[0] = 0.0;
       const int ni[3] = {i, i, ip}, nj[3] = {j, j, jp};
+      // quiet data: every node divergence exactly 0 gives S = +0 exactly (each
+      // fma(+-0, Psi, +0) of the sum is +0), without the Psi loads
+      unsigned long long nz = 0;
 #pragma unroll
-      for (int k = 1; k < 8; ++k) {
-        double s = 0.0;
+      for (int l = 0; l < 3; ++l)
 #pragma unroll
-        for (int l = 0; l < 3; ++l)
+        for (int m = 0; m < 3; ++m) nz |= (unsigned long long)__double_as_longlong(wd[l][m]) << 1;
+      if (nz == 0) {
 #pragma unroll
-          for (int m = 0; m < 3; ++m) {
-            double psi;
-            if (k == 1) psi = b1[l][m];
-            else if (k == 2) psi = b2[l][m];
-            else {
-              const int q = k == 3 ? -1 : QP_V1 + (k - 4);
-              if (l == 1 && m == 1) psi = q < 0 ? ZU(i, j, 6) : PZ(i, j, q);
-              else if (l == 1) psi = q < 0 ? Y(i, nj[m], 6) : PY(i, nj[m], q);
-              else if (m == 1) psi = q < 0 ? X(ni[l], j, 6) : PX(ni[l], j, q);
-              else psi = q < 0 ? C(ni[l], nj[m], 6) : PC(ni[l], nj[m], q);
+        for (int k = 1; k < 8; ++k) S[k] = 0.0;
+      } else {
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+          double s = 0.0;
+#pragma unroll
+          for (int l = 0; l < 3; ++l)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+              double psi;
+              if (k == 1) psi = b1[l][m];
+              else if (k == 2) psi = b2[l][m];
+              else {
+                const int q = k == 3 ? -1 : QP_V1 + (k - 4);
+                if (l == 1 && m == 1) psi = q < 0 ? ZU(i, j, 6) : PZ(i, j, q);
+                else if (l == 1) psi = q < 0 ? Y(i, nj[m], 6) : PY(i, nj[m], q);
+                else if (m == 1) psi = q < 0 ? X(ni[l], j, 6) : PX(ni[l], j, q);
+                else psi = q < 0 ? C(ni[l], nj[m], 6) : PC(ni[l], nj[m], q);
+              }
+              s = fma(wd[l][m], psi, s);
             }
-            s = fma(wd[l][m], psi, s);
-          }
-        S[k] = s;
+          S[k] = s;
+        }
       }
       if (!g.src_cell_on)
         for (int k = 0; k < 8; ++k) S[k] = 0.0;
