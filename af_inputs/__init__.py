@@ -273,6 +273,36 @@ def rotor(n: int = 400, kappa: float = 2.0) -> Problem:
     return Problem("rotor", n, n, 0.0, 1.0, 0.0, 1.0, PERIODIC, 5.0 / 3.0, prim, kappa=kappa)
 
 
+def quadrants_hydro(n: int = 48, kappa: float = 1.0) -> Problem:
+    """A degenerate case: pure hydrodynamics (B = 0) on [0,1]^2, outflow, gamma
+    = 1.4, at rest, with four constant quadrants around (0.5, 0.5):
+    (rho, p) = (1, 1) top right, (0.25, 0.1) top left, (0.5, 0.4) bottom left,
+    (2, 2) bottom right.  With B = 0 the fast speed is the sound speed, the
+    sensor's phi_3 is 0 / 1e-40 and the Powell source vanishes; B must stay
+    exactly zero."""
+    def prim(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        z = 0.0 * x
+        right, top = x > 0.5, y > 0.5
+        rho = np.where(top, np.where(right, 1.0, 0.25), np.where(right, 2.0, 0.5))
+        p = np.where(top, np.where(right, 1.0, 0.1), np.where(right, 2.0, 0.4))
+        return (rho + z, z, z, z, z, z, z, p + z)
+    return Problem("quadrants_hydro", n, n, 0.0, 1.0, 0.0, 1.0, OUTFLOW, 1.4, prim, kappa=kappa)
+
+
+def double_rarefaction(n: int = 48, speed: float = 2.5, kappa: float = 1.0) -> Problem:
+    """A degenerate case: two rarefactions moving apart (v1 = -speed for x <
+    0.5, +speed beyond) in rho = 1, p = 0.4, B = (0, 0.5, 0), gamma = 1.4,
+    outflow on [0,1]^2.  The centre is driven towards vacuum, where the
+    positivity limiters and the 1e-13 floors act."""
+    def prim(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        z = 0.0 * x
+        v1 = np.where(x < 0.5, -speed, speed) + z
+        return (z + 1.0, v1, z, z, z, z + 0.5, z, z + 0.4)
+    return Problem("double_rarefaction", n, n, 0.0, 1.0, 0.0, 1.0, OUTFLOW, 1.4, prim, kappa=kappa)
+
+
 def shock_cloud(n: int = 400, kappa: float = 1.0) -> Problem:
     """Shock-cloud interaction (Example 4.7) on [0,1]^2, gamma = 5/3, outflow
     boundaries.  Reading: the printed state vectors list (rho, v1, v2, v3, p, B1,
