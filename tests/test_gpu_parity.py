@@ -400,3 +400,34 @@ def test_full_size_blast_2048_sampled():
                     assert np.abs(a[k]).max() == 0
                     continue
                 assert np.abs(a[k] - b[k]).max() / scale[c][k] <= 1e-12, (i0, j0, c, k)
+
+
+def test_near_vacuum_double_rarefaction():
+    """Rarefactions pulling apart at 6 (beyond the cavitation speed of the
+    state): after 20 oracle steps rho_min ~ 7e-3 and p_min ~ 5e-5, with every
+    limiter of Sec. 3.2-3.3 active and Newton up to 9 iterations.  One limited
+    stage on each stage input of the next oracle step agrees with the oracle to
+    1e-12 with equal counters; 60 GPU steps from the start stay admissible."""
+    pb = ai.double_rarefaction(48, speed=6.0)
+    Un = ai.dofs(pb)
+    for _ in range(20):
+        Un, _ = oracle.step(pb, Un)
+    assert min(u[0].min() for u in Un) < 1e-2
+    dt = oracle.dt(pb, Un)
+    Us = Un
+    for a, b in [(0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)]:
+        st = np.zeros(oracle.NSTATS, dtype=np.int64)
+        R = oracle.stage(pb, Us, Us, dt, 0.0, 1.0, stats=st)
+        G, cnt = fe_on(pb, Us, dt)
+        assert rel_err(G, R) <= 1e-12
+        for q, name in enumerate(oracle.STAT_NAMES):
+            if name in ("center_limited", "point_limited", "lambda_lt1", "src_limited", "face_theta_lt1",
+                        "newton_solves", "newton_maxit", "shrink", "nonadmissible"):
+                assert cnt[name] == st[q], (name, cnt[name], st[q])
+        Us = oracle.stage(pb, Un, Us, dt, a, b)
+    s = solver_for(pb)
+    s.set_state(ai.dofs(pb))
+    for _ in range(60):
+        s.step(dt_out=False)
+    rc, cnt = s.status()
+    assert rc == af.AF_OK and cnt["nonadmissible"] == 0, af.af_last_error(s.ctx)
