@@ -391,6 +391,7 @@ int af_dt(af_ctx *c, double *dt_out, int on_device) {
 }
 
 int af_stage(af_ctx *c, int s, const double *dt, int on_device) {
+  AfNvtxRange nvtx_("af_stage");
   if (!c || s < 0 || s > 2) return AF_EINVAL;
   if (s != c->next_stage) return fail(c, AF_EINVAL, "stage %d called, stage %d expected", s, c->next_stage);
   CK(cudaSetDevice(c->device), "set device");
@@ -486,6 +487,7 @@ int copy_out_buf(af_ctx *c, const double *src, double *const U[4], int on_device
 }  // namespace
 
 int af_rhs_vjp(af_ctx *c, const double *const v[4], double *const out[4], int on_device) {
+  AfNvtxRange nvtx_("af_rhs_vjp");
   if (!c || !v || !out) return AF_EINVAL;
   if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
   if (c->g.upwind) return fail(c, AF_EINVAL, "the transpose covers the central point source only");
@@ -587,6 +589,7 @@ int adjoint_args(af_ctx *c, const double *dt, const double *const lam_in[4], dou
 
 int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double *const lam_in[4],
                     double *const lam_out[4], int on_device, int flags) {
+  AfNvtxRange nvtx_("af_adjoint_step");
   if (!c) return AF_EINVAL;
   int rc = adjoint_args(c, dt, lam_in, lam_out, flags);
   if (rc) return rc;
@@ -643,6 +646,7 @@ int af_adjoint_step(af_ctx *c, const double *dt, int dt_on_device, const double 
 int af_adjoint_step_stages(af_ctx *c, const double *dt, int dt_on_device, const double *const U1[4],
                            const double *const U2[4], const double *const U3[4], const double *const lam_in[4],
                            double *const lam_out[4], int on_device, int flags) {
+  AfNvtxRange nvtx_("af_adjoint_step_stages");
   if (!c) return AF_EINVAL;
   int rc = adjoint_args(c, dt, lam_in, lam_out, flags);
   if (rc) return rc;
@@ -698,6 +702,7 @@ int af_adjoint_step_stages(af_ctx *c, const double *dt, int dt_on_device, const 
 }
 
 int af_divb(af_ctx *c, double *out, int on_device) {
+  AfNvtxRange nvtx_("af_divb");
   if (!c || !out) return AF_EINVAL;
   CK(cudaSetDevice(c->device), "set device");
   const int nb = af_divb_nblocks(c->g);
@@ -723,6 +728,7 @@ int af_get_stage(af_ctx *c, double *const U[4], int on_device) {
 }
 
 int af_step(af_ctx *c, double *dt_used, int on_device) {
+  AfNvtxRange nvtx_("af_step");
   if (!c) return AF_EINVAL;
   if (c->next_stage != 0) return fail(c, AF_EINVAL, "af_step called in the middle of a step (stage %d next)", c->next_stage);
   CK(cudaSetDevice(c->device), "set device");
@@ -788,6 +794,7 @@ int sync_copies(af_ctx *c) {
 extern "C" {
 
 int af_step_host(af_ctx *c, const double *const in[4], double *const out[4]) {
+  AfNvtxRange nvtx_("af_step_host");
   if (!c || !in || !out) return AF_EINVAL;
   for (int cls = 0; cls < 4; ++cls)
     if (!in[cls] || !out[cls]) return fail(c, AF_EINVAL, "state class %d is NULL", cls);

@@ -257,6 +257,7 @@ int af1d_dt(af1d_ctx *c, double *dt_out, int on_device) {
 }
 
 int af1d_stage(af1d_ctx *c, int s, const double *dt, int on_device) {
+  AfNvtxRange nvtx_("af1d_stage");
   if (!c || s < 0 || s > 2) return AF_EINVAL;
   if (s != c->next_stage) return fail1(c, AF_EINVAL, "stage %d called, stage %d expected", s, c->next_stage);
   CK1(cudaSetDevice(c->device), "set device");
@@ -266,6 +267,7 @@ int af1d_stage(af1d_ctx *c, int s, const double *dt, int on_device) {
 }
 
 int af1d_step(af1d_ctx *c, double *dt_used, int on_device) {
+  AfNvtxRange nvtx_("af1d_step");
   if (!c) return AF_EINVAL;
   if (c->next_stage != 0) return fail1(c, AF_EINVAL, "af1d_step called in the middle of a step");
   CK1(cudaSetDevice(c->device), "set device");

@@ -335,6 +335,7 @@ int af_batch_get_state(af_batch *b, int run, double *const U[4], int on_device) 
 }
 
 int af_batch_step(af_batch *b, int nsteps) {
+  AfNvtxRange nvtx_("af_batch_step");
   if (!b || nsteps < 0) return AF_EINVAL;
   BCK(cudaSetDevice(b->device), "set device");
   int rc = upload(b);

@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdlib>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #define AF_NQP 20   // per point value: F1 (7), F2 (7), varrho_1, varrho_2, v (3), v.B
@@ -113,6 +114,15 @@ void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, dou
                         cudaStream_t s);
 // the 1D scheme (af_kernels1d.cuh) on the 2D structures with ny = 1: one stage
 // out = a U^n + b FE(U^s) (the dt pass first when reduce_dt), and the dt pass alone
+// A named NVTX range around one library call (visible in nsys timelines; the
+// header-only NVTX3 costs nothing when no tool is attached).
+struct AfNvtxRange {
+  explicit AfNvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~AfNvtxRange() { nvtxRangePop(); }
+  AfNvtxRange(const AfNvtxRange &) = delete;
+  AfNvtxRange &operator=(const AfNvtxRange &) = delete;
+};
+
 // Largest grids: the launch shape (32 x 4 thread blocks, at most 65535 block
 // rows) bounds ny, and the adjoint's DoF ids (class << 28 | index) bound the
 // points of a class.  Either bound lies far beyond what fits in device memory.

@@ -498,3 +498,43 @@ def test_sine_wave_third_order_on_gpu():
         errs.append(np.array([np.abs(U[c][0] - E[c][0]).mean() for c in range(4)]))
     rates = np.log2(np.array(errs[1]) / np.array(errs[2]))
     assert (rates > 2.8).all(), rates
+
+
+@pytest.mark.parametrize("bc,nx,ny", [(ai.PERIODIC, 4, 4), (ai.OUTFLOW, 4, 4), (ai.OUTFLOW, 5, 7),
+                                      (ai.PERIODIC, 4, 33)])
+def test_smallest_grids(bc, nx, ny):
+    """The smallest grids the library accepts (4 cells per side) and thin ragged
+    ones: right-hand side and two limited steps with the sensor on against the
+    oracle (the 5-point lines and the sensor's neighbours wrap or mirror more
+    than once)."""
+    pb = ai.random_smooth(nx, ny, seed=11, amp=0.2, bc=bc)
+    pb.kappa = 1.0
+    U = ai.dofs(pb)
+    s = solver_for(pb)
+    s.set_state(U)
+    assert rel_err(s.rhs(), oracle.rhs(pb, U)) <= 1e-12
+    G, R, cnt, st = one_step(pb, nsteps=2)
+    assert rel_err(G, R) <= 1e-12
+
+
+def test_poisoned_states_are_reported():
+    """Host-side fault injection: a state with a NaN, or with a negative
+    pressure, is stepped without any device fault, and af_status reports
+    AF_ENONPHYS; after a reset the context steps a good state normally."""
+    pb = ai.orszag_tang(16)
+    good = ai.dofs(pb)
+    s = solver_for(pb)
+    for poison in ("nan", "negative_p"):
+        U = [u.copy() for u in good]
+        if poison == "nan":
+            U[3][7, 5, 6] = float("nan")
+        else:
+            U[0][7, 8, 8] = 0.5 * (U[0][1, 8, 8] ** 2 + U[0][2, 8, 8] ** 2) / U[0][0, 8, 8] - 1.0
+        s.set_state(U)
+        s.step(dt_out=False)
+        rc, cnt = s.status(reset=True)
+        assert rc == af.AF_ENONPHYS, (poison, rc)
+        s.set_state(good)
+        s.step(dt_out=False)
+        rc, cnt = s.status(reset=True)
+        assert rc == af.AF_OK, poison
