@@ -238,7 +238,7 @@ int af_batch_create(int nruns, const int *nx, const int *ny, const double *gamma
   b->gamma.assign(gamma, gamma + nruns);
   b->x0.assign(nruns, 0.0); b->x1.assign(nruns, 1.0);
   b->y0.assign(nruns, 0.0); b->y1.assign(nruns, 1.0);
-  af_params p0 = {0.2, 0.0, 1, 1, 1};
+  af_params p0 = {0.2, 0.0, 1, 1, 1, 0};
   b->prm.assign(nruns, p0);
   b->grid.resize(nruns);
   for (int c = 0; c < 4; ++c) b->class_off[c].resize(nruns);
