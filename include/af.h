@@ -162,6 +162,16 @@ int af_stage(af_ctx *ctx, int s, const double *dt, int on_device);
  * stage 1, U^{n+1} after stage 2 (same layout as the state). */
 int af_get_stage(af_ctx *ctx, double *const U[4], int on_device);
 
+/* Run diagnostics of the current state (not in the paper; for monitoring the
+ * positivity that Sec. 3 preserves), written to out[9] (host or device
+ * pointer): out[c] = min rho and out[4+c] = min p over the DoFs of class c
+ * (0 averages, 1 x-faces, 2 y-faces, 3 corners), p = (gamma-1)(E - |rho v|^2
+ * /(2 rho) - |B|^2/2); out[8] = dx dy sum of the cell-average densities (the
+ * total mass).  A NaN anywhere in a class makes its minima NaN.  The sums and
+ * minima are formed in a fixed order (deterministic).  With on_device = 0 the
+ * call synchronises the stream.  Allocates a small workspace on first use. */
+int af_diagnostics(af_ctx *ctx, double *out, int on_device);
+
 /* The two discrete divergence measures of Example 4.4 for the current state,
  * written to out[0], out[1] (host or device pointer):
  *   out[0] = sum over cells and the 3x3 nodes of eq. (semi_av_src) of

@@ -204,6 +204,20 @@ def divb(pb, U, count=False, **kw):
     return float(out[0]), float(out[1])
 
 
+def diagnostics(pb, U):
+    """Run diagnostics of a state by their plain definitions: the minimum density
+    and pressure p = (gamma-1)(E - |rho v|^2/(2 rho) - |B|^2/2) of each DoF class,
+    and the total mass dx dy sum(rho_bar)."""
+    U = _check(U, pb.nx, pb.ny, pb.bc)
+    g = pb.gamma
+    min_rho, min_p = [], []
+    for u in U:
+        p = (g - 1.0) * (u[7] - 0.5 * (u[1] ** 2 + u[2] ** 2 + u[3] ** 2) / u[0] - 0.5 * (u[4] ** 2 + u[5] ** 2 + u[6] ** 2))
+        min_rho.append(float(u[0].min()))
+        min_p.append(float(p.min()))
+    return {"min_rho": min_rho, "min_p": min_p, "mass": float(U[0][0].sum()) * pb.dx * pb.dy}
+
+
 # ---- the 1D scheme: states are [averages [8, n], point values [8, nf]] ----------
 def _check1(U, pb):
     nf = pb.n if pb.bc == 0 else pb.n + 1

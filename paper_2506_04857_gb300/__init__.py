@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
     "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step",
-    "af_adjoint_step_stages", "af_sensor", "af_dt",
+    "af_adjoint_step_stages", "af_diagnostics", "af_sensor", "af_dt",
     "af_stage",
     "af_step", "af_step_host", "af_sync", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
     "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
@@ -89,6 +89,7 @@ def _lib():
             lib.af_get_stage.argtypes = [vp, pp, C.c_int]
             lib.af_rhs_vjp.argtypes = [vp, pp, pp, C.c_int]
             lib.af_divb.argtypes = [vp, vp, C.c_int]
+            lib.af_diagnostics.argtypes = [vp, vp, C.c_int]
             lib.af_adjoint_step.argtypes = [vp, vp, C.c_int, pp, pp, C.c_int, C.c_int]
             lib.af_adjoint_step_stages.argtypes = [vp, vp, C.c_int, pp, pp, pp, pp, pp, C.c_int, C.c_int]
             lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
@@ -301,6 +302,19 @@ def af_get_stage(ctx, out=None, device: bool = True):
     out, ptrs, dev = _outputs(ctx, out, device)
     _check(ctx, _lib().af_get_stage(ctx, ptrs, dev))
     return out
+
+
+def af_diagnostics(ctx, out=None):
+    """Run diagnostics of the current state: {"min_rho": [4 classes], "min_p": [4 classes],
+    "mass": dx dy sum of the cell-average densities}.  With out (a 9-element CUDA float64
+    tensor) the raw values are written on the device without synchronising."""
+    if out is not None:
+        _check(ctx, _lib().af_diagnostics(ctx, out.data_ptr(), 1))
+        return out
+    res = (C.c_double * 9)()
+    _check(ctx, _lib().af_diagnostics(ctx, C.cast(res, C.c_void_p), 0))
+    v = [float(x) for x in res]
+    return {"min_rho": v[0:4], "min_p": v[4:8], "mass": v[8]}
 
 
 def af_divb(ctx, out=None):
@@ -634,6 +648,9 @@ class Solver:
 
     def divb(self, out=None):
         return af_divb(self.ctx, out)
+
+    def diagnostics(self, out=None):
+        return af_diagnostics(self.ctx, out)
 
     def sensor(self, device: bool = True):
         return af_sensor(self.ctx, device)

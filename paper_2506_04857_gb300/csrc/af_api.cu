@@ -35,6 +35,7 @@ struct af_ctx {
   double *dts;            // dt-sensitivity work (5 * af_dt_sens_nblocks() doubles) and mu
   unsigned long long *cnt_pin;   // pinned host copy of the counters before / after a recomputation
   double *divb_buf;       // divergence measures: 2 per block, then the 2 results (allocated on first use)
+  double *diag_buf;       // diagnostics: AF_NDIAG per block, then the AF_NDIAG results (allocated on first use)
   // pipelined host-buffer steps (af_step_host), created on first use: two input
   // and two output staging states, one copy stream per direction, and per slot
   // the events "input arrived", "step done with the slot", "output copied"
@@ -701,6 +702,26 @@ int af_adjoint_step_stages(af_ctx *c, const double *dt, int dt_on_device, const 
   return AF_OK;
 }
 
+int af_diagnostics(af_ctx *c, double *out, int on_device) {
+  if (!c || !out) return AF_EINVAL;
+  AfNvtxRange nvtx_("af_diagnostics");
+  CK(cudaSetDevice(c->device), "set device");
+  const int nb = af_diag_nblocks(c->g);
+  if (!c->diag_buf && cudaMalloc(&c->diag_buf, sizeof(double) * AF_NDIAG * ((size_t)nb + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AF_ENOMEM, "diagnostics workspace");
+  }
+  bind_states(c, c->cur, c->cur, c->cur);
+  double *res = c->diag_buf + (size_t)AF_NDIAG * nb;
+  af_launch_diag(c->dev, c->g, c->diag_buf, res, c->stream);
+  CK(cudaGetLastError(), "diagnostics launch");
+  CK(cudaMemcpyAsync(out, res, sizeof(double) * AF_NDIAG, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream),
+     "copy diagnostics");
+  if (!on_device) CK(cudaStreamSynchronize(c->stream), "synchronise");
+  return AF_OK;
+}
+
 int af_divb(af_ctx *c, double *out, int on_device) {
   AfNvtxRange nvtx_("af_divb");
   if (!c || !out) return AF_EINVAL;
@@ -894,6 +915,7 @@ void af_destroy(af_ctx *c) {
   if (c->adj_pd) cudaFree(c->adj_pd);
   if (c->dts) cudaFree(c->dts);
   if (c->divb_buf) cudaFree(c->divb_buf);
+  if (c->diag_buf) cudaFree(c->diag_buf);
   if (c->inflow_dev) cudaFree(c->inflow_dev);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);

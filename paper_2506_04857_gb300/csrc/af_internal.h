@@ -192,6 +192,10 @@ void af_launch_dt1d(const AfDev &d, const AfGrid &g, cudaStream_t s);
 // divergence measures of Example 4.4 of the state bound in d.us into out[2]
 // (device); partials: 2 * af_divb_nblocks(g) doubles
 int af_divb_nblocks(const AfGrid &g);
+// run diagnostics (af_diagnostics): AF_NDIAG partials per block of af_diag_nblocks(g), then out[AF_NDIAG]
+#define AF_NDIAG 9
+int af_diag_nblocks(const AfGrid &g);
+void af_launch_diag(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s);
 void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s);
 // persistent batched launch of one pass (AF_K_* id) over a (run, i0, j0) tile
 // list; flag: reduce_dt for the point-data pass, "some run uses the upwind

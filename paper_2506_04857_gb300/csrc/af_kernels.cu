@@ -1527,6 +1527,69 @@ __global__ void __launch_bounds__(128) k_divb(const __grid_constant__ AfDev d, c
   }
 }
 
+// Run diagnostics: per block, the minimum density and pressure of each DoF
+// class and the sum of the cell-average densities (AF_NDIAG partials).
+__device__ __forceinline__ double nan_min(double a, double b) { return (a != a || a < b) ? a : b; }
+__global__ void __launch_bounds__(128) k_diag(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                              double *partials) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double v[AF_NDIAG];
+  for (int q = 0; q < 8; ++q) v[q] = inf;
+  v[8] = 0.0;
+#pragma unroll 1
+  for (int c = 0; c < 4; ++c) {
+    if (i < g.ex[c] && j < g.ey[c]) {
+      double U[8];
+      load8(sview(d.us[c], g, c), i, j, U);
+      v[c] = U[0];
+      v[4 + c] = pressure(U, g.gm1);
+      if (c == 0) v[8] = U[0];
+    }
+  }
+  __shared__ double sh[AF_NDIAG][128];
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int q = 0; q < AF_NDIAG; ++q) sh[q][t] = v[q];
+  __syncthreads();
+  for (int h = 64; h > 0; h >>= 1) {
+    if (t < h) {
+      for (int q = 0; q < 8; ++q) sh[q][t] = nan_min(sh[q][t], sh[q][t + h]);
+      sh[8][t] += sh[8][t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    for (int q = 0; q < AF_NDIAG; ++q) partials[AF_NDIAG * b + q] = sh[q][0];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_diag_sum(const double *partials, int nblocks, double cell_area, double *out) {
+  __shared__ double sh[AF_NDIAG][256];
+  const int t = threadIdx.x;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  double v[AF_NDIAG];
+  for (int q = 0; q < 8; ++q) v[q] = inf;
+  v[8] = 0.0;
+  for (int k = t; k < nblocks; k += 256) {
+    for (int q = 0; q < 8; ++q) v[q] = nan_min(v[q], partials[AF_NDIAG * k + q]);
+    v[8] += partials[AF_NDIAG * k + 8];
+  }
+  for (int q = 0; q < AF_NDIAG; ++q) sh[q][t] = v[q];
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (t < h) {
+      for (int q = 0; q < 8; ++q) sh[q][t] = nan_min(sh[q][t], sh[q][t + h]);
+      sh[8][t] += sh[8][t + h];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    for (int q = 0; q < 8; ++q) out[q] = sh[q][0];
+    out[8] = sh[8][0] * cell_area;
+  }
+}
+
 __global__ void __launch_bounds__(256) k_divb_sum(const double *partials, int nblocks, double *out) {
   __shared__ double sh[2][256];
   const int t = threadIdx.x;
@@ -1560,6 +1623,12 @@ void af_launch_pointdata(const AfDev &d, const AfGrid &g, int reduce_dt, cudaStr
 }
 void af_launch_dt(const AfDev &d, const AfGrid &g, cudaStream_t s) { k_dt<<<1, 32, 0, s>>>(d, g); }
 int af_divb_nblocks(const AfGrid &g) { const dim3 b = grid2(g.nx, g.ny); return (int)(b.x * b.y); }
+int af_diag_nblocks(const AfGrid &g) { const dim3 b = grid2(g.nxa, g.nya); return (int)(b.x * b.y); }
+void af_launch_diag(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s) {
+  const dim3 b = grid2(g.nxa, g.nya);
+  k_diag<<<b, dim3(32, 4), 0, s>>>(d, g, partials);
+  k_diag_sum<<<1, 256, 0, s>>>(partials, (int)(b.x * b.y), g.dx * g.dy, out);
+}
 void af_launch_divb(const AfDev &d, const AfGrid &g, double *partials, double *out, cudaStream_t s) {
   const dim3 b = grid2(g.nx, g.ny);
   k_divb<<<b, dim3(32, 4), 0, s>>>(d, g, partials);

@@ -885,3 +885,15 @@ def test_upwind_source_at_rest_is_the_central_scheme():
     U = ai.dofs(pb)
     for a, b in zip(oracle.rhs(pb, U, src_point_upwind=True), oracle.rhs(pb, U)):
         assert np.array_equal(a, b)
+
+
+def test_diagnostics_of_a_uniform_state():
+    """oracle.diagnostics on a uniform state: every class's minima are the state's
+    density and pressure, and the mass is density times the domain's area."""
+    w = (1.3, 0.4, -0.7, 0.2, 0.6, -0.3, 0.25, 2.1)   # rho, v, B, p
+    pb = ai.constant(10, 7, bc=ai.OUTFLOW, w=w)
+    d = oracle.diagnostics(pb, ai.dofs(pb))
+    for c in range(4):
+        assert d["min_rho"][c] == pytest.approx(w[0], rel=1e-15)
+        assert d["min_p"][c] == pytest.approx(w[7], rel=1e-13)
+    assert d["mass"] == pytest.approx(w[0] * 1.0 * 1.0, rel=1e-14)
