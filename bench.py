@@ -729,7 +729,8 @@ def main():
     # ---------------- end to end through the C ABI with host buffers --------
     # af_step_host: every step copies its input state from pinned host memory and
     # its result back; the copies of neighbouring steps overlap the step itself.
-    host_in = [torch.from_numpy(u).pin_memory() for u in U0]
+    # The input is the state the timed region ended with (the same flow regime).
+    host_in = [torch.from_numpy(u).pin_memory() for u in s.get_state(device=False)]
     host_out = [torch.empty_like(h).pin_memory() for h in host_in]
     bytes_state = sum(u.nbytes for u in U0)
     s.step_host(host_in, host_out)
