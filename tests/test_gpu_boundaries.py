@@ -234,3 +234,29 @@ def test_full_size_jets_sampled():
             A.append(G[c][:, j0 + lo_j:j0 + hjc, i0 + lo_i:i0 + hic])
             B.append(R[c][:, lo_j:hjc, lo_i:hic])
         assert rel_err(A, B, pb) <= 1e-12, (i0, j0)
+
+
+def test_upwind_source_with_reflective_and_inflow_sides():
+    """The velocity-upwind point source (Example 4.2 variant) on a grid with
+    reflective and inflow sides (the ghost-aware point kernel with the upwind
+    option), wide enough for interior blocks too: limited stages on the
+    oracle's stage inputs of one step, <= 1e-12 with equal counters."""
+    pb = ai.jets(80)
+    Un = ai.dofs(pb)
+    dt = oracle.dt(pb, Un, src_point_upwind=True)
+    Us = Un
+    for a, b in [(0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0)]:
+        st = np.zeros(oracle.NSTATS, dtype=np.int64)
+        R = oracle.stage(pb, Us, Us, dt, 0.0, 1.0, stats=st, src_point_upwind=True)
+        s = solver(pb, src_point_upwind=True)
+        s.set_state(Us)
+        s.stage(0, dt)
+        G = s.get_stage(device=False)
+        rc, cnt = s.status()
+        assert rc == af.AF_OK, af.af_last_error(s.ctx)
+        assert rel_err(G, R, pb) <= 1e-12
+        for q, name in enumerate(oracle.STAT_NAMES):
+            if name in ("center_limited", "point_limited", "sensor_lt099", "lambda_lt1", "shrink", "nonadmissible"):
+                assert cnt[name] == st[q], (name, cnt[name], st[q])
+        s.close()
+        Us = oracle.stage(pb, Un, Us, dt, a, b, src_point_upwind=True)
