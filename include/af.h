@@ -31,6 +31,9 @@
  *   - Device-side faults of the scheme (a degree of freedom left outside the
  *     admissible set after every safeguard, a non-finite time step) latch a
  *     device error word that the next af_status call reports as AF_ENONPHYS.
+ *   - A context is not thread-safe: calls on one context must not overlap in
+ *     time from several host threads.  Distinct contexts are independent (their
+ *     device work is ordered only by their streams).
  */
 #ifndef AF_H
 #define AF_H
