@@ -897,3 +897,25 @@ def test_diagnostics_of_a_uniform_state():
         assert d["min_rho"][c] == pytest.approx(w[0], rel=1e-15)
         assert d["min_p"][c] == pytest.approx(w[7], rel=1e-13)
     assert d["mass"] == pytest.approx(w[0] * 1.0 * 1.0, rel=1e-14)
+
+
+def test_upwind_source_closed_form_along_y():
+    """The same closed form along the corners' y-lines: B2 = eps (y - 1/2)^4 with
+    v2 changing sign across the columns, B1 constant.  At corners the
+    divergence changes by +-(3/4) eps dy^3 with the sign of v2; x-faces (whose
+    y-derivative is the two-point central one) do not change beyond rounding."""
+    eps = 1.0
+    pb = _upwind_problem(lambda x, y: 0.3 + 0 * x, lambda x, y: eps * (y - 0.5) ** 4,
+                         lambda x, y: 0.2 + 0 * x, lambda x, y: 0.4 * np.cos(np.pi * x) + 0 * y)
+    U = ai.dofs(pb)
+    rc = oracle.rhs(pb, U)
+    ru = oracle.rhs(pb, U, src_point_upwind=True)
+    corner = U[3]
+    v2 = corner[2] / corner[0]
+    d = 0.75 * eps * pb.dy ** 3 * np.sign(v2)
+    inner = (slice(2, -2), slice(2, -2))
+    for k, psi in ((5, v2), (4, 0.2 + 0 * v2)):     # B2 equation: Psi = v2; B1 equation: Psi = v1
+        got = (ru[3][k] - rc[3][k])[inner]
+        assert np.allclose(got, (-d * psi)[inner], rtol=1e-9, atol=1e-13), k
+    assert np.abs(ru[1] - rc[1]).max() <= 1e-13 * np.abs(rc[1]).max()
+    assert np.array_equal(ru[0], rc[0])
