@@ -1242,7 +1242,10 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     }
     double fe[8];
     limited_value(d, g, i, j, th, dt, fe);
-    bool ok = fe[0] > 0.0 && qform(fe, 0.0) > 0.0;   // rho > 0 and p > 0
+    // rho > 0 and p > 0 and all finite, on the integer pipe: for finite doubles
+    // x > 0 exactly when the bit pattern, read as a signed integer, is > 0
+    const double q = qform(fe, 0.0);
+    bool ok = __double_as_longlong(fe[0]) > 0 && __double_as_longlong(q) > 0 && finite_bits(q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) ok = ok && finite_bits(fe[k]);
     if (!ok) {
@@ -1251,9 +1254,13 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
       else atomicOr(&d.st->err, AFE_REPAIR_OVERFLOW);
     }
     const size_t cs0 = (size_t)g.nx * g.ny, o0 = (size_t)j * g.nx + i;
+    if (a == 0.0) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k)
-      d.uo[0][k * cs0 + o0] = a == 0.0 ? fe[k] : fma(a, __ldg(d.un[0] + k * cs0 + o0), b * fe[k]);
+      for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fe[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fma(a, __ldg(d.un[0] + k * cs0 + o0), b * fe[k]);
+    }
   }
   if (nface) atomicAdd(&d.st->cnt[ST_FACE_THETA_LT1], (unsigned long long)nface);
 }
