@@ -334,7 +334,11 @@ void af_batch_destroy(af_batch *b);
  * with ratio of specific heats gamma and boundary condition bc.  U[cls] and
  * dUdt[cls] are device arrays on the current device with the [8][nyp][nxp]
  * layout of af_sizes; stream is a cudaStream_t (NULL: legacy default stream);
- * the call is asynchronous in stream order and makes no allocation.
+ * the call is asynchronous in stream order and makes no allocation.  No
+ * dUdt[cls] may overlap any U[cls'] (the kernels read U while they write
+ * dUdt): overlapping buffers are rejected with AF_EINVAL.  The call cannot see
+ * the extents of the buffers it is given, so each must hold the full class
+ * array on the current device.
  *
  * Scratch: one fixed array in the library's static device memory, which every
  * GPU that loads the library holds until the process exits, sized for index

@@ -31,6 +31,38 @@ PHASES = ["dt", "pointdata", "center", "point_ho", "point_pp", "sensor_phi", "se
 KINDS = ["add", "mul", "div", "sqrt", "exp", "minmax", "cmp"]
 
 
+class Coeffs(C.Structure):
+    """or_coeffs: the limiter coefficients of one stage (see af_oracle.cpp)."""
+    _fields_ = [("ths_x", C.POINTER(C.c_double)), ("ths_y", C.POINTER(C.c_double)),
+                ("ths_c", C.POINTER(C.c_double)), ("th_src", C.POINTER(C.c_double)),
+                ("lam", C.POINTER(C.c_double)), ("th_x", C.POINTER(C.c_double)),
+                ("th_y", C.POINTER(C.c_double)), ("th_pt", C.POINTER(C.c_double) * 4)]
+
+
+COEFF_NAMES = ["ths_x", "ths_y", "ths_c", "th_src", "lam", "th_x", "th_y", "th_pt0", "th_pt1", "th_pt2", "th_pt3"]
+
+
+def coeff_shapes(nx, ny, bc):
+    """Array shapes of the stage coefficients (faces, cells, scaling-limiter theta*/theta** per class)."""
+    from af_inputs import class_extents
+    ext = class_extents(nx, ny, bc)
+    sh = {"ths_x": (ext[1][1], ext[1][0]), "ths_y": (ext[2][1], ext[2][0]), "ths_c": (ny, nx), "th_src": (ny, nx),
+          "lam": (4, ny, nx), "th_x": (ext[1][1], ext[1][0]), "th_y": (ext[2][1], ext[2][0])}
+    for c in range(4):
+        sh["th_pt%d" % c] = (2, ext[c][1], ext[c][0])
+    return sh
+
+
+def _coeffs_struct(arrs):
+    cs = Coeffs()
+    for name in COEFF_NAMES[:7]:
+        setattr(cs, name, _dp(arrs[name]) if name in arrs else None)
+    for c in range(4):
+        key = "th_pt%d" % c
+        cs.th_pt[c] = _dp(arrs[key]) if key in arrs else None
+    return cs
+
+
 class Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
                 ("y1", C.c_double), ("cfl", C.c_double), ("kappa", C.c_double), ("bc", C.c_int),
@@ -111,7 +143,12 @@ def _lib(count: bool = False, complex_step: bool = False):
             lib.or1d_stage.argtypes = [C.POINTER(Params), C.c_int, pp, pp, C.c_double, C.c_double, C.c_double, pp,
                                        C.POINTER(C.c_longlong)]
             lib.or1d_step.argtypes = [C.POINTER(Params), C.c_int, pp, C.c_double, dp, C.POINTER(C.c_longlong)]
+            lib.or_stage_rec.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double, C.c_double,
+                                         C.c_double, pp, C.POINTER(C.c_longlong), C.POINTER(Coeffs),
+                                         C.POINTER(Coeffs)]
             if key == "cs":
+                lib.or_stage_cs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, pp, pp, C.c_double,
+                                            C.c_double, C.c_double, pp, pp, C.POINTER(Coeffs)]
                 lib.or_step_cs.restype = C.c_int
                 lib.or_step_cs.argtypes = [C.POINTER(Params), C.c_int, C.c_int, pp, pp, C.c_double]
             lib.or_counts.restype = C.c_int
@@ -161,6 +198,44 @@ def stage(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, count=False
     _lib(count).or_stage(C.byref(P), pb.nx, pb.ny, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
                          st.ctypes.data_as(C.POINTER(C.c_longlong)))
     return out
+
+
+def stage_record(pb, Un, Us, dt_, a, b, stats: Optional[np.ndarray] = None, frozen: Optional[dict] = None, **kw):
+    """One stage (as stage()) that also returns the limiter coefficients it took, as a dict of
+    arrays (coeff_shapes).  With frozen (such a dict) the stage uses those coefficients instead
+    of forming them.  Entries a stage does not form (face theta with PP limiting off) stay NaN."""
+    P = params_for(pb, **kw)
+    Un = _check(Un, pb.nx, pb.ny, pb.bc)
+    Us = _check(Us, pb.nx, pb.ny, pb.bc)
+    out = _empty(pb.nx, pb.ny, pb.bc)
+    st = np.zeros(NSTATS, dtype=np.int64) if stats is None else stats
+    rec = {k: np.full(v, np.nan) for k, v in coeff_shapes(pb.nx, pb.ny, pb.bc).items()}
+    rs = _coeffs_struct(rec)
+    fz = None
+    if frozen is not None:
+        frozen = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in frozen.items()}
+        fz_struct = _coeffs_struct(frozen)
+        fz = C.byref(fz_struct)
+    _lib().or_stage_rec(C.byref(P), pb.nx, pb.ny, _ptrs(Un), _ptrs(Us), dt_, a, b, _ptrs(out),
+                        st.ctypes.data_as(C.POINTER(C.c_longlong)), C.byref(rs), fz)
+    return out, rec
+
+
+def stage_complex(pb, Un_re, Un_im, Us_re, Us_im, dt_, a, b, frozen: Optional[dict] = None, **kw):
+    """One stage a Un + b FE(Us) of complex states (complex-step differentiation) with the
+    limiter coefficients frozen at `frozen` (a stage_record dict) or formed from the complex
+    state (None).  Returns (re, im)."""
+    P = params_for(pb, **kw)
+    arrs = [_check(u, pb.nx, pb.ny, pb.bc) for u in (Un_re, Un_im, Us_re, Us_im)]
+    re, im = _empty(pb.nx, pb.ny, pb.bc), _empty(pb.nx, pb.ny, pb.bc)
+    fz = None
+    if frozen is not None:
+        frozen = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in frozen.items()}
+        fz_struct = _coeffs_struct(frozen)
+        fz = C.byref(fz_struct)
+    _lib(complex_step=True).or_stage_cs(C.byref(P), pb.nx, pb.ny, *[_ptrs(u) for u in arrs], dt_, a, b,
+                                        _ptrs(re), _ptrs(im), fz)
+    return re, im
 
 
 def step(pb, U, dt_in: float = 0.0, stats: Optional[np.ndarray] = None, count=False, **kw):

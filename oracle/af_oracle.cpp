@@ -184,6 +184,28 @@ enum {
   ST_CELL_SHRINK,       // the cell-average part of ST_SHRINK (Remark 4.1 for the averages)
   ST_NSTATS
 };
+
+// The limiter coefficients of one forward-Euler stage.  Every pointer may be
+// NULL.  A stage given a record writes the coefficients it took there; a stage
+// given a frozen record uses those values instead of forming them (the sensor,
+// the flux limiter and the scaling limiters are then plain blends, and the
+// Remark 4.1 shrink is already in the recorded values), so that its result is a
+// smooth function of the state along the recorded branch.  The LLF and FVS
+// coefficients alpha (maxima) are not recorded: they follow the state.
+// Layouts, row-major over the index set named:
+//   ths_x, th_x: [ny][nxf] x-faces; ths_y, th_y: [nyf][nx] y-faces;
+//   ths_c, th_src: [ny][nx] cells; lam: [4][ny][nx] cells (L, R, D, U);
+//   th_pt[cls]: [2][ey][ex] of class cls, theta* then theta** (Sec. 3.3);
+//     class 0 holds the cell-centre limiter (Remark 3.2), classes 1..3 the
+//     point values after Remark 4.1 (theta** = 0 for the LLF fallback).
+typedef struct {
+  double *ths_x, *ths_y;   // theta^s per face (Sec. 3.4)
+  double *ths_c;           // theta^s_ij, the minimum over the cell's four faces
+  double *th_src;          // theta_ij (Sec. 3.2 step 1)
+  double *lam;             // Lambda_I (Sec. 3.2 step 2); not read when frozen
+  double *th_x, *th_y;     // face theta (Sec. 3.2 step 3, after Remark 4.1)
+  double *th_pt[4];        // scaling-limiter theta*, theta**
+} or_coeffs;
 }
 
 static const int G = 2;  // ghost width (the shock sensor reaches two cells)
@@ -197,6 +219,10 @@ struct Ctx {
   int pp_on, src_cell_on, src_point_on, src_point_upwind;
   int P, R;          // padded extents (x, y)
   int ext[4][2];     // interior extents per DoF class
+  const or_coeffs *rec = nullptr;   // write the stage's limiter coefficients here
+  const or_coeffs *frz = nullptr;   // use these limiter coefficients (frozen branch)
+  size_t cid(int cls, int i, int j) const { return (size_t)j * ext[cls][0] + (size_t)i; }
+  size_t csz(int cls) const { return (size_t)ext[cls][0] * ext[cls][1]; }
   size_t plane() const { return (size_t)P * R; }
   size_t id(int i, int j) const { return (size_t)(j + G) * P + (size_t)(i + G); }
 };
@@ -221,6 +247,8 @@ static void make_ctx(const or_params *p, int nx, int ny, Ctx &C) {
   }
   C.in_lo = p->inflow_lo; C.in_hi = p->inflow_hi;
   for (int k = 0; k < 8; ++k) C.inU[k] = p->inflow_U[k];
+  C.rec = nullptr;
+  C.frz = nullptr;
 }
 
 // Axis kind of each class: 0 = cell-centred index, 1 = face/node index.
@@ -436,6 +464,14 @@ static void scaling_limiter(const real *UH, const real *UL, double gamma, real *
   for (int k = 0; k < 8; ++k) out[k] = theta2 * Us[k] + (real(1.0) - theta2) * UL[k];
 }
 
+// The scaling limiter's result for given theta* and theta** (frozen branch).
+static void scaling_blend(const real *UH, const real *UL, real theta1, real theta2, real *out) {
+  real Us[8];
+  for (int k = 0; k < 8; ++k) Us[k] = UH[k];
+  Us[0] = theta1 * UH[0] + (real(1.0) - theta1) * UL[0];
+  for (int k = 0; k < 8; ++k) out[k] = theta2 * Us[k] + (real(1.0) - theta2) * UL[k];
+}
+
 // ---------------------------------------------------------------------------
 // Sec. 3.2 step (2): the rectangle [0,Lambda_L]x...x[0,Lambda_U] for one cell,
 // from Lim1 = U^{Lim,1} and the anti-diffusive fluxes H[I], I = L,R,D,U.
@@ -647,7 +683,17 @@ static void compute_centers(const Ctx &C, State &S, Work &W, long long *st) {
       S.get(C, 3, i, j + 1, UL); S.get(C, 3, i + 1, j + 1, UR);
       center_value(avg, L, R, D, Uu, DL, DR, UL, UR, uc);
       real t1, t2;
-      scaling_limiter(uc, avg, C.gamma, out, t1, t2);
+      if (C.frz && C.frz->th_pt[0]) {
+        t1 = real(C.frz->th_pt[0][C.cid(0, i, j)]);
+        t2 = real(C.frz->th_pt[0][C.csz(0) + C.cid(0, i, j)]);
+        scaling_blend(uc, avg, t1, t2, out);
+      } else {
+        scaling_limiter(uc, avg, C.gamma, out, t1, t2);
+      }
+      if (C.rec && C.rec->th_pt[0]) {
+        C.rec->th_pt[0][C.cid(0, i, j)] = val(t1);
+        C.rec->th_pt[0][C.csz(0) + C.cid(0, i, j)] = val(t2);
+      }
       if (t1 < real(1.0) || t2 < real(1.0)) nlim++;
       for (int k = 0; k < 8; ++k) W.Uc.at(C, k, i, j) = out[k];
     }
@@ -793,8 +839,17 @@ static void point_limit(const Ctx &C, real dt, Work &W, long long *st) {
           if (C.src_point_on) UL[k] = UL[k] - dt * divB * Ps[k];
         }
         real out[8], t1, t2;
+        if (C.frz && C.frz->th_pt[cls]) {
+          t1 = real(C.frz->th_pt[cls][C.cid(cls, i, j)]);
+          t2 = real(C.frz->th_pt[cls][C.csz(cls) + C.cid(cls, i, j)]);
+          scaling_blend(UH, UL, t1, t2, out);
+          if (t1 < real(1.0) || t2 < real(1.0)) nlim++;
+          for (int k = 0; k < 8; ++k) W.FE[cls].at(C, k, i, j) = out[k];
+          continue;
+        }
         scaling_limiter(UH, UL, C.gamma, out, t1, t2);
         if (t1 < real(1.0) || t2 < real(1.0)) nlim++;
+        real t2_used = t2;
         if (!in_G(out, C.gamma)) {
           // Remark 4.1: shrink theta** by 2^m 1e-8, m = 0..9 (Reading: from
           // its first value, not cumulatively), else fall back to U^L.
@@ -807,9 +862,14 @@ static void point_limit(const Ctx &C, real dt, Work &W, long long *st) {
             real th = rmax(real(0.0), t2 - real(std::ldexp(1e-8, m)));
             for (int k = 0; k < 8; ++k) out[k] = th * Us[k] + (real(1.0) - th) * UL[k];
             ok = in_G(out, C.gamma);
+            t2_used = th;
           }
-          if (!ok) for (int k = 0; k < 8; ++k) out[k] = UL[k];
+          if (!ok) { for (int k = 0; k < 8; ++k) out[k] = UL[k]; t2_used = real(0.0); }
           if (!in_G(out, C.gamma)) nbad++;
+        }
+        if (C.rec && C.rec->th_pt[cls]) {
+          C.rec->th_pt[cls][C.cid(cls, i, j)] = val(t1);
+          C.rec->th_pt[cls][C.csz(cls) + C.cid(cls, i, j)] = val(t2_used);
         }
         for (int k = 0; k < 8; ++k) W.FE[cls].at(C, k, i, j) = out[k];
       }
@@ -885,7 +945,8 @@ static void compute_faces(const Ctx &C, Work &W, long long *st) {
       llf_flux(0, W.pd[0].at(C, f - 1, j), W.pd[0].at(C, f, j), Fl, &al);
       for (int k = 0; k < 8; ++k) W.fx.at(C, 8 + k, f, j) = Fl[k];
       set_phase(PH_SENSOR_THETA);
-      real ts = theta_s(C, W, 0, f - 1, j, f, j);
+      real ts = (C.frz && C.frz->ths_x) ? real(C.frz->ths_x[C.cid(1, f, j)]) : theta_s(C, W, 0, f - 1, j, f, j);
+      if (C.rec && C.rec->ths_x) C.rec->ths_x[C.cid(1, f, j)] = val(ts);
       set_phase(PH_FACE);
       W.fx.at(C, 16, f, j) = ts;
       W.fx.at(C, 17, f, j) = al;
@@ -902,7 +963,8 @@ static void compute_faces(const Ctx &C, Work &W, long long *st) {
       llf_flux(1, W.pd[0].at(C, i, g - 1), W.pd[0].at(C, i, g), Fl, &al);
       for (int k = 0; k < 8; ++k) W.fy.at(C, 8 + k, i, g) = Fl[k];
       set_phase(PH_SENSOR_THETA);
-      real ts = theta_s(C, W, 1, i, g - 1, i, g);
+      real ts = (C.frz && C.frz->ths_y) ? real(C.frz->ths_y[C.cid(2, i, g)]) : theta_s(C, W, 1, i, g - 1, i, g);
+      if (C.rec && C.rec->ths_y) C.rec->ths_y[C.cid(2, i, g)] = val(ts);
       set_phase(PH_FACE);
       W.fy.at(C, 16, i, g) = ts;
       W.fy.at(C, 17, i, g) = al;
@@ -979,6 +1041,7 @@ static void cell_update(const Ctx &C, real dt, Work &W, long long *st) {
         real tsD = W.fy.at(C, 16, i, j), tsU = W.fy.at(C, 16, i, j + 1);
         real tsc = rmin(rmin(tsL, tsR), rmin(tsD, tsU));   // theta^s_ij
         W.ths.at(C, 0, i, j) = tsc;
+        if (C.rec && C.rec->ths_c) C.rec->ths_c[C.cid(0, i, j)] = val(tsc);
         real Fss[4][8], Fll[4][8];
         const real tsf[4] = {tsL, tsR, tsD, tsU};
         for (int k = 0; k < 8; ++k) {
@@ -1019,8 +1082,14 @@ static void cell_update(const Ctx &C, real dt, Work &W, long long *st) {
         real eps_p = rmin(real(1e-13), pllf);
         // step (1): theta_ij.  Reading: theta_ij = 1 when p(U^src) >= eps_p.
         real th = real(1.0);
-        real psrc = pressure(Usrc, C.gamma);
-        if (psrc < eps_p) { th = rmin(real(1.0), (pllf - eps_p) / (pllf - psrc)); a_src++; }
+        if (C.frz && C.frz->th_src) {
+          th = real(C.frz->th_src[C.cid(0, i, j)]);
+          if (th < real(1.0)) a_src++;
+        } else {
+          real psrc = pressure(Usrc, C.gamma);
+          if (psrc < eps_p) { th = rmin(real(1.0), (pllf - eps_p) / (pllf - psrc)); a_src++; }
+        }
+        if (C.rec && C.rec->th_src) C.rec->th_src[C.cid(0, i, j)] = val(th);
         real L1[8];
         // Lim1 = theta U^src + (1-theta) U^LLF, written as U^LLF + theta (U^src - U^LLF)
         // so that its density equals that of U^LLF exactly (Psi_1 = 0).
@@ -1033,9 +1102,11 @@ static void cell_update(const Ctx &C, real dt, Work &W, long long *st) {
           H[2][k] = dt / real(dy) * (Fss[2][k] - Fll[2][k]);
           H[3][k] = real(0.0) - dt / real(dy) * (Fss[3][k] - Fll[3][k]);
         }
-        real Lam[4];
-        flux_limiter_box(L1, H, eps_rho, eps_p, C.gamma, Lam, nl);
+        real Lam[4] = {real(1.0), real(1.0), real(1.0), real(1.0)};
+        if (!(C.frz && C.frz->th_x && C.frz->th_y)) flux_limiter_box(L1, H, eps_rho, eps_p, C.gamma, Lam, nl);
         if (Lam[0] < real(1.0) || Lam[1] < real(1.0) || Lam[2] < real(1.0) || Lam[3] < real(1.0)) a_lam++;
+        if (C.rec && C.rec->lam)
+          for (int I = 0; I < 4; ++I) C.rec->lam[(size_t)I * C.csz(0) + C.cid(0, i, j)] = val(Lam[I]);
         for (int k = 0; k < 8; ++k) W.lim1.at(C, k, i, j) = L1[k];
         for (int I = 0; I < 4; ++I)
           for (int k = 0; k < 8; ++k) W.H.at(C, I * 8 + k, i, j) = H[I][k];
@@ -1086,14 +1157,15 @@ static void cell_final(const Ctx &C, Work &W, long long *st) {
   Arr thx, thy;
   thx.init(C, 1); thy.init(C, 1);
   long long nface = 0;
+  const bool frozen = C.frz && C.frz->th_x && C.frz->th_y;
   for (int j = 0; j < C.ext[1][1]; ++j)
     for (int f = 0; f < C.ext[1][0]; ++f) {
-      thx.at(C, 0, f, j) = face_theta_x(C, W, f, j);
+      thx.at(C, 0, f, j) = frozen ? real(C.frz->th_x[C.cid(1, f, j)]) : face_theta_x(C, W, f, j);
       if (val(thx.at(C, 0, f, j)) < 1.0) nface++;
     }
   for (int g = 0; g < C.ext[2][1]; ++g)
     for (int i = 0; i < C.ext[2][0]; ++i) {
-      thy.at(C, 0, i, g) = face_theta_y(C, W, i, g);
+      thy.at(C, 0, i, g) = frozen ? real(C.frz->th_y[C.cid(2, i, g)]) : face_theta_y(C, W, i, g);
       if (val(thy.at(C, 0, i, g)) < 1.0) nface++;
     }
   st[ST_FACE_THETA_LT1] += nface;
@@ -1118,7 +1190,7 @@ static void cell_final(const Ctx &C, Work &W, long long *st) {
   // max(0, theta - 2^m 1e-8), m = 0..9, else set to 0; the cells sharing a
   // lowered face are recomputed).
   long long nshrink = 0, nbad = 0;
-  for (int j = 0; j < C.ny; ++j)
+  for (int j = 0; j < C.ny && !frozen; ++j)
     for (int i = 0; i < C.nx; ++i) {
       real cur[8];
       for (int k = 0; k < 8; ++k) cur[k] = W.FE[0].at(C, k, i, j);
@@ -1154,6 +1226,12 @@ static void cell_final(const Ctx &C, Work &W, long long *st) {
         for (int k = 0; k < 8; ++k) W.FE[0].at(C, k, ii, jj) = o2[k];
       }
     }
+  if (C.rec && C.rec->th_x && C.rec->th_y) {
+    for (int j = 0; j < C.ext[1][1]; ++j)
+      for (int f = 0; f < C.ext[1][0]; ++f) C.rec->th_x[C.cid(1, f, j)] = val(thx.at(C, 0, f, j));
+    for (int g = 0; g < C.ext[2][1]; ++g)
+      for (int i = 0; i < C.ext[2][0]; ++i) C.rec->th_y[C.cid(2, i, g)] = val(thy.at(C, 0, i, g));
+  }
   st[ST_SHRINK] += nshrink;
   st[ST_CELL_SHRINK] += nshrink;
   st[ST_NONADMISSIBLE] += nbad;
@@ -1599,6 +1677,24 @@ int or_stage(const or_params *p, int nx, int ny, const double *const *Un, const 
   return 0;
 }
 
+// or_stage that also writes the limiter coefficients it took into *rec, or,
+// given *frz, takes them from there (either may be NULL; see or_coeffs).
+int or_stage_rec(const or_params *p, int nx, int ny, const double *const *Un, const double *const *Us, double dt,
+                 double a, double b, double *const *out, long long *st, const or_coeffs *rec, const or_coeffs *frz) {
+  Ctx C;
+  make_ctx(p, nx, ny, C);
+  C.rec = rec;
+  C.frz = frz;
+  State Sn, Ss, So;
+  load_state(C, Un, Sn);
+  load_state(C, Us, Ss);
+  long long loc[ST_NSTATS] = {0};
+  stage(C, Sn, Ss, real(dt), real(a), real(b), So, loc);
+  store_state(C, So, out);
+  if (st) for (int k = 0; k < ST_NSTATS; ++k) st[k] = (k == ST_NEWTON_MAXIT) ? std::max(st[k], loc[k]) : st[k] + loc[k];
+  return 0;
+}
+
 // One SSP-RK3 step in place.  dt_in > 0 fixes dt; otherwise dt comes from U^n.
 // The three stages use the Shu-Osher coefficients (a,b) = (0,1), (3/4,1/4), (1/3,2/3).
 int or_step(const or_params *p, int nx, int ny, double *const *U, double dt_in, double *dt_used, long long *st) {
@@ -1876,6 +1972,45 @@ int or_step_cs(const or_params *p, int nx, int ny, double *const *re, double *co
   for (int k = 0; k < ST_NSTATS; ++k)
     if (k != ST_NEWTON_MAXIT && k != ST_SENSOR_LT099 && k != ST_CFL_VIOLATIONS) act += loc[k];
   return (int)act;
+}
+#endif
+
+#ifdef AF_ORACLE_COMPLEX
+// One forward-Euler stage out = a Un + b FE(Us, dt) of complex states
+// (complex-step differentiation), with the limiter coefficients frozen at
+// *frz (NULL: formed from the complex state, branches by real part).
+int or_stage_cs(const or_params *p, int nx, int ny, const double *const *un_re, const double *const *un_im,
+                const double *const *us_re, const double *const *us_im, double dt, double a, double b,
+                double *const *out_re, double *const *out_im, const or_coeffs *frz) {
+  Ctx C;
+  make_ctx(p, nx, ny, C);
+  C.frz = frz;
+  State Sn, Ss, So;
+  Sn.init(C);
+  Ss.init(C);
+  for (int cls = 0; cls < 4; ++cls) {
+    int ex = C.ext[cls][0], ey = C.ext[cls][1];
+    for (int k = 0; k < 8; ++k)
+      for (int j = 0; j < ey; ++j)
+        for (int i = 0; i < ex; ++i) {
+          const size_t o = ((size_t)k * ey + j) * ex + i;
+          Sn.c[cls].at(C, k, i, j) = Cx(un_re[cls][o], un_im[cls][o]);
+          Ss.c[cls].at(C, k, i, j) = Cx(us_re[cls][o], us_im[cls][o]);
+        }
+  }
+  long long loc[ST_NSTATS] = {0};
+  stage(C, Sn, Ss, real(dt), real(a), real(b), So, loc);
+  for (int cls = 0; cls < 4; ++cls) {
+    int ex = C.ext[cls][0], ey = C.ext[cls][1];
+    for (int k = 0; k < 8; ++k)
+      for (int j = 0; j < ey; ++j)
+        for (int i = 0; i < ex; ++i) {
+          const size_t o = ((size_t)k * ey + j) * ex + i;
+          out_re[cls][o] = So.c[cls].at(C, k, i, j).re;
+          out_im[cls][o] = So.c[cls].at(C, k, i, j).im;
+        }
+  }
+  return 0;
 }
 #endif
 

@@ -477,6 +477,34 @@ def af_probe_fp64(stream=None) -> float:
 AF_NOALLOC_MAX_POINTS = 4225
 
 
+def _noalloc_check(nx: int, ny: int, bc: int, U, out) -> None:
+    """The C entry point cannot see extents: every class tensor must be a contiguous CUDA float64
+    tensor on the current device with the [8][ey][ex] layout of the grid, and no output may
+    overlap an input (the kernels read U while they write dUdt)."""
+    torch = _torch()
+    if len(U) != 4 or len(out) != 4:
+        raise ValueError("U and out each hold four DoF classes")
+    if nx < 4 or ny < 4 or bc not in (AF_BC_PERIODIC, AF_BC_OUTFLOW):
+        raise ValueError("af_rhs_noalloc: need nx, ny >= 4 and a periodic or outflow grid")
+    ex = [nx, nx + (bc == AF_BC_OUTFLOW), nx, nx + (bc == AF_BC_OUTFLOW)]
+    ey = [ny, ny, ny + (bc == AF_BC_OUTFLOW), ny + (bc == AF_BC_OUTFLOW)]
+    dev = torch.cuda.current_device()
+    spans = []
+    for name, group in (("U", U), ("out", out)):
+        for c, t in enumerate(group):
+            if not (_is_tensor(t) and t.is_cuda) or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("%s[%d] must be a contiguous CUDA float64 tensor" % (name, c))
+            if t.device.index != dev:
+                raise ValueError("%s[%d] is on cuda:%s, the current device is cuda:%d" % (name, c, t.device.index, dev))
+            if tuple(t.shape) != (8, ey[c], ex[c]):
+                raise ValueError("%s[%d] must have shape %s, got %s" % (name, c, (8, ey[c], ex[c]), tuple(t.shape)))
+            spans.append((name, t.data_ptr(), t.data_ptr() + t.numel() * 8))
+    for n1, a0, a1 in spans[4:]:
+        for n0, b0, b1 in spans:
+            if n0 == "U" and a0 < b1 and b0 < a1:
+                raise ValueError("an output of af_rhs_noalloc overlaps an input")
+
+
 def af_rhs_noalloc(nx: int, ny: int, gamma: float, bc: int, domain, U, out, stream=None) -> None:
     """af_rhs computed in the library's static scratch, with no device allocation.
 
@@ -485,6 +513,7 @@ def af_rhs_noalloc(nx: int, ny: int, gamma: float, bc: int, domain, U, out, stre
     (nx [+1 outflow]) x (ny [+1 outflow]) > AF_NOALLOC_MAX_POINTS are rejected
     (AF_EBOUNDS).  Calls share one scratch array: do not overlap them on the GPU."""
     handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _noalloc_check(int(nx), int(ny), int(bc), U, out)
     ins = _ptr_array([u.data_ptr() for u in U])
     outs = _ptr_array([o.data_ptr() for o in out])
     rc = _lib().af_rhs_noalloc(int(nx), int(ny), float(gamma), int(bc), *[float(v) for v in domain], ins, outs,

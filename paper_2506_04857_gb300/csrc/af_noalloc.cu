@@ -66,6 +66,15 @@ extern "C" int af_rhs_noalloc(int nx, int ny, double gamma, int bc, double x0, d
     if (!U[c] || !dUdt[c]) return AF_EINVAL;
   const int nxa = bc == AF_BC_OUTFLOW ? nx + 1 : nx, nya = bc == AF_BC_OUTFLOW ? ny + 1 : ny;
   if ((long long)nxa * nya > kMaxPoints) return AF_EBOUNDS;   // grid larger than the static scratch
+  // dUdt must not overlap U: the kernels read U while they write dUdt.
+  const size_t cls_bytes[4] = {8 * sizeof(double) * nx * ny, 8 * sizeof(double) * nxa * ny,
+                               8 * sizeof(double) * nx * nya, 8 * sizeof(double) * nxa * nya};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const char *o0 = (const char *)dUdt[a], *o1 = o0 + cls_bytes[a];
+      const char *i0 = (const char *)U[b], *i1 = i0 + cls_bytes[b];
+      if (o0 < i1 && i0 < o1) return AF_EINVAL;
+    }
   unsigned char *base = nullptr;
   int rc = scratch_address(&base);
   if (rc) return rc;

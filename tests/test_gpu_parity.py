@@ -212,6 +212,37 @@ def test_fe_stage_parity_limited(case):
     assert active > 0
 
 
+@pytest.mark.parametrize("case", ["orszag_tang", "blast", "shock_cloud"])
+def test_sensor_export_parity(case):
+    """af_sensor: theta^s at every x- and y-face (Sec. 3.4) against the oracle, element by
+    element, on the initial state and every stage input of one oracle step (kappa > 0; the
+    initial state of the blast is quiet away from the jump, its later stages are not)."""
+    pb = LIMITED[case]()
+    assert pb.kappa > 0
+    U = ai.dofs(pb)
+    dt = oracle.dt(pb, U)
+    inputs = [U]
+    Us = U
+    for a, b in [(0.0, 1.0), (0.75, 0.25)]:
+        Us = oracle.stage(pb, U, Us, dt, a, b)
+        inputs.append(Us)
+    s = solver_for(pb)
+    below = 0
+    for V in inputs:
+        s.set_state([torch.from_numpy(u).cuda() for u in V])
+        tx, ty = s.sensor(device=True)
+        rx, ry = oracle.sensor(pb, V)
+        assert tx.shape == rx.shape and ty.shape == ry.shape
+        assert np.abs(tx.cpu().numpy() - rx).max() <= 1e-12
+        assert np.abs(ty.cpu().numpy() - ry).max() <= 1e-12
+        # the host-output form of the call returns the same values
+        hx, hy = s.sensor(device=False)
+        assert np.array_equal(hx, tx.cpu().numpy()) and np.array_equal(hy, ty.cpu().numpy())
+        below += int((rx < 0.99).sum() + (ry < 0.99).sum())
+    s.close()
+    assert below > 0
+
+
 @pytest.mark.parametrize("case", ["blast", "blast_paper", "rotor", "shock_cloud", "quadrants_hydro",
                                   "double_rarefaction"])
 def test_step_parity_limited_no_sensor(case):

@@ -155,6 +155,104 @@ def test_llf_flux_consistency():
             assert a1 >= max(oracle.spectral_radius(l, U, g), oracle.spectral_radius(l, V, g))
 
 
+def test_llf_alpha_closed_form():
+    """Lemma 3.1 with equality.  The Roe-type speed is |a convex combination of v_l and
+    v~_l|, never above max(|v_l|, |v~_l|), and varrho = |v_l| + c_f is below either alpha_*;
+    so alpha^LLF = max(|v_l|, |v~_l|) + max(c_f, c~_f) + |B - B~| / (sqrt(rho) + sqrt(rho~)).
+
+    Hand-computed case (gamma = 5/3): U = (rho 1, v 0, B 0, p 3/5) has c_f = 1; U~ = (rho 4,
+    v (1,0,0), B (0,0,3), p 21/5) has c^2 = 7/4 and |B|^2/rho = 9/4 with B_1 = 0, so c_f = 2.
+    alpha_1 = 1 + 2 + 3/(1 + 2) = 4; without the magnetic-jump term it would be 3."""
+    g = 5.0 / 3.0
+    U = ai.prim_to_cons([1.0, 0, 0, 0, 0, 0, 0, 0.6], g)
+    V = ai.prim_to_cons([4.0, 1.0, 0, 0, 0, 0, 3.0, 4.2], g)
+    assert oracle.fast_speed(1, U, g) == pytest.approx(1.0, rel=1e-15)
+    assert oracle.fast_speed(1, V, g) == pytest.approx(2.0, rel=1e-15)
+    for a, b in ((U, V), (V, U)):
+        F, alpha = oracle.llf_flux(1, a, b, g)
+        assert alpha == pytest.approx(4.0, rel=1e-15)
+        expect = 0.5 * (oracle.flux(1, a, g) + oracle.flux(1, b, g) - 4.0 * (b - a))
+        assert np.allclose(F, expect, rtol=1e-15, atol=1e-15)
+    # the same pair seen along y: rotate x <-> y (v and B components swap)
+    perm = [0, 2, 1, 3, 5, 4, 6, 7]
+    _, alpha = oracle.llf_flux(2, U[perm], V[perm], g)
+    assert alpha == pytest.approx(4.0, rel=1e-15)
+    # random pairs, strongly magnetised and near vacuum included
+    rng = np.random.default_rng(21)
+    for _ in range(400):
+        st = []
+        for _ in range(2):
+            rho = 10 ** rng.uniform(-4, 1)
+            p = 10 ** rng.uniform(-6, 0.5)
+            v = rng.normal(size=3) * 10 ** rng.uniform(-1, 1)
+            B = rng.normal(size=3) * 10 ** rng.uniform(-1, 2)
+            st.append((ai.prim_to_cons([rho, *v, *B, p], g), rho, v, B))
+        (a, ra, va, Ba), (b, rb, vb, Bb) = st
+        for l in (1, 2):
+            expect = (max(abs(va[l - 1]), abs(vb[l - 1])) + max(oracle.fast_speed(l, a, g), oracle.fast_speed(l, b, g))
+                      + np.linalg.norm(Ba - Bb) / (math.sqrt(ra) + math.sqrt(rb)))
+            assert oracle.llf_flux(l, a, b, g)[1] == pytest.approx(expect, rel=1e-13)
+
+
+def _psi(U):
+    v = U[1:4] / U[0]
+    return np.array([0.0, *U[4:7], *v, v @ U[4:7]])
+
+
+def _llf_cell_update(C, Lc, Rc, Dc, Uc, h, g, alpha_scale=1.0):
+    """eq. (2d_llf) for one cell and its four neighbours with dt at the CFL bound of Lemma 3.1
+    (taken with equality); alpha_scale scales alpha^LLF (a deliberately wrong alpha)."""
+    def flux(l, a, b):
+        F, al = oracle.llf_flux(l, a, b, g)
+        if alpha_scale != 1.0:
+            al *= alpha_scale
+            F = 0.5 * (oracle.flux(l, a, g) + oracle.flux(l, b, g) - al * (b - a))
+        return F, al
+    FL, aL = flux(1, Lc, C)
+    FR, aR = flux(1, C, Rc)
+    FD, aD = flux(2, Dc, C)
+    FU, aU = flux(2, C, Uc)
+    divB = (Rc[4] - Lc[4]) / (2 * h) + (Uc[5] - Dc[5]) / (2 * h)
+    dt = 1.0 / ((aL + aR + aD + aU) / h + abs(divB) / math.sqrt(C[0]))
+    return C - dt / h * (FR - FL) - dt / h * (FU - FD) - dt * divB * _psi(C)
+
+
+def test_lemma_3_1_llf_scheme_stays_admissible():
+    """Lemma 3.1: the first-order LLF scheme with the Powell source keeps every cell average in
+    G at its CFL bound.  3,000 random five-cell stencils of admissible states (some neighbours
+    share the centre's state but not its B, which makes div B large), strongly magnetised and
+    near vacuum.  With alpha^LLF halved some of the same stencils leave G (about 1 in 600),
+    so the test can fail."""
+    g = 5.0 / 3.0
+    rng = np.random.default_rng(22)
+
+    def state():
+        rho = 10 ** rng.uniform(-4, 1)
+        p = 10 ** rng.uniform(-6, 0)
+        v = rng.normal(size=3) * 10 ** rng.uniform(-2, 1)
+        B = rng.normal(size=3) * 10 ** rng.uniform(-1, 2)
+        return ai.prim_to_cons([rho, *v, *B, p], g)
+
+    bad_half = 0
+    for _ in range(3000):
+        C = state()
+        nb = []
+        for _ in range(4):
+            if rng.random() < 0.15:
+                S = C.copy()
+                Bn = C[4:7] + rng.normal(size=3) * 10 ** rng.uniform(-1, 2)
+                S[7] += 0.5 * (Bn @ Bn - C[4:7] @ C[4:7])
+                S[4:7] = Bn
+            else:
+                S = state()
+            nb.append(S)
+        V = _llf_cell_update(C, *nb, 1.0, g)
+        assert V[0] > 0.0 and p_of(V, g) > 0.0
+        W = _llf_cell_update(C, *nb, 1.0, g, alpha_scale=0.5)
+        bad_half += not (W[0] > 0.0 and p_of(W, g) > 0.0)
+    assert bad_half >= 2
+
+
 # --------------------------------------------------------------------------
 # Godunov-Powell source (eq. gp_src) and the point-value discretisation
 # (Sec. 2.3): with the source, the system is symmetrised by the entropy
@@ -461,6 +559,44 @@ def test_flux_limiter_brute_force():
     assert maxit <= 12
 
 
+def test_flux_limiter_rho_rectangle_is_feasible_and_maximal():
+    """Sec. 3.2 step (2), first bullet, against the definition of R_rho rather than its
+    formula.  Lim1 is at rest and the H_I change only the density, so every vertex keeps the
+    pressure of Lim1 and the pressure step leaves the box alone: Lambda = Lambda^rho.  Then
+    (a) every vertex of [0, Lambda]^4 has rho >= eps_rho; (b) the box is maximal up to the
+    printed 1e-12 in the denominator, which leaves a margin of (rho(Lim1) - eps_rho) 1e-12 /
+    (1e-12 + |sum_neg|): with |sum_neg| >= 1, raising the negative Lambda_I by a factor
+    1 + 1e-11 takes the all-negative vertex below eps_rho; (c) Lambda_I = 1 where rho(H_I) >= 0,
+    and all negative directions share one value."""
+    g = 1.4
+    rng = np.random.default_rng(23)
+    n_cut = 0
+    for _ in range(400):
+        rho = 10 ** rng.uniform(-4, 0.5)
+        L1 = ai.prim_to_cons([rho, 0, 0, 0, *rng.normal(size=3), rng.uniform(0.1, 2)], g)
+        H = np.zeros((4, 8))
+        neg = rng.random(4) < 0.6
+        if not neg.any():
+            neg[rng.integers(4)] = True
+        H[:, 0] = np.where(neg, -10 ** rng.uniform(0, 1, 4), 10 ** rng.uniform(-2, 1, 4))
+        eps_rho = min(1e-13, L1[0])
+        eps_p = min(1e-13, p_of(L1, g))
+        lam, solves, _ = oracle.flux_limiter(L1, H, eps_rho, eps_p, g)
+        assert solves == 0
+        assert np.all(lam[~neg] == 1.0)
+        assert np.all(lam[neg] == lam[neg][0])
+        for k in range(16):
+            th = np.array([lam[I] if (k >> I) & 1 else 0.0 for I in range(4)])
+            assert L1[0] + th @ H[:, 0] >= eps_rho
+        sneg = H[neg, 0].sum()
+        if lam[neg][0] < 1.0:
+            n_cut += 1
+            assert L1[0] + lam[neg][0] * (1 + 1e-11) * sneg < eps_rho
+        else:
+            assert L1[0] + sneg >= eps_rho
+    assert n_cut > 100
+
+
 def test_scaling_limiter_invariants():
     rng = np.random.default_rng(12)
     g = 5.0 / 3.0
@@ -524,6 +660,43 @@ def test_sensor_divergence_uses_both_directions():
     # B1 jumps by 2 along x and B2 by 1 along y: |2 + 1| / |0.5 + 0.5|
     phi = oracle.sensor_phi(c, cons(1.5, 0.5), cons(-0.5, 0.5), cons(0.5, 1.0), cons(0.5, 0.0), g, 0.5, 0.5)
     assert phi[3] == pytest.approx(3.0, rel=1e-14)
+
+
+@pytest.mark.parametrize("kappa", [0.3, 1.0])
+def test_sensor_theta_at_faces_and_cells(kappa):
+    """Sec. 3.4: a face takes theta^s = exp(-kappa [phi_1 phi_2 + phi_3]) with each phi the larger
+    of its two cells' values (phi_1 differenced along the face normal), and theta^s_ij is the
+    smallest theta^s of the cell's four faces.  An 8x8 periodic grid of seeded, strongly varying
+    cell averages makes every phi differ between neighbours; the per-cell phi come from
+    sensor_phi, which the closed forms above pin.  Both the sensor export and the values a
+    limited stage takes are checked."""
+    n = 8
+    pb = ai.random_smooth(n, seed=41, modes=4, amp=0.45)
+    pb.kappa = kappa
+    U = ai.dofs(pb)
+    g, dx, dy = pb.gamma, pb.dx, pb.dy
+    A = U[0]
+    cell = lambda i, j: A[:, j % n, i % n]
+    phi = np.zeros((n, n, 4))
+    for j in range(n):
+        for i in range(n):
+            phi[j, i] = oracle.sensor_phi(cell(i, j), cell(i + 1, j), cell(i - 1, j), cell(i, j + 1),
+                                          cell(i, j - 1), g, dx, dy)
+    assert np.ptp(phi[..., 2]) > 0.1 and np.ptp(phi[..., 3]) > 0.1 and np.ptp(phi[..., 0]) > 1e-3
+
+    def face(pa, pb_, d):
+        return math.exp(-kappa * (max(pa[d], pb_[d]) * max(pa[2], pb_[2]) + max(pa[3], pb_[3])))
+
+    ex = np.array([[face(phi[j, (f - 1) % n], phi[j, f], 0) for f in range(n)] for j in range(n)])
+    ey = np.array([[face(phi[(q - 1) % n, i], phi[q, i], 1) for i in range(n)] for q in range(n)])
+    assert 0.0 < ex.min() < 0.9 and 0.0 < ey.min() < 0.9
+    tx, ty = oracle.sensor(pb, U)
+    assert np.allclose(tx, ex, rtol=1e-13, atol=0) and np.allclose(ty, ey, rtol=1e-13, atol=0)
+    # the values one limited stage takes
+    _, rec = oracle.stage_record(pb, U, U, oracle.dt(pb, U), 0.0, 1.0)
+    assert np.allclose(rec["ths_x"], ex, rtol=1e-13, atol=0) and np.allclose(rec["ths_y"], ey, rtol=1e-13, atol=0)
+    cellmin = np.minimum(np.minimum(ex, np.roll(ex, -1, axis=1)), np.minimum(ey, np.roll(ey, -1, axis=0)))
+    assert np.array_equal(rec["ths_c"], cellmin)
 
 
 # --------------------------------------------------------------------------
