@@ -303,6 +303,22 @@ def double_rarefaction(n: int = 48, speed: float = 2.5, kappa: float = 1.0) -> P
     return Problem("double_rarefaction", n, n, 0.0, 1.0, 0.0, 1.0, OUTFLOW, 1.4, prim, kappa=kappa)
 
 
+def rarefaction_lattice(n: int = 2048, periods: int = 64, speed: float = 6.0, kappa: float = 1.0) -> Problem:
+    """The double rarefaction's gas (rho = 1, p = 0.4, B = (0, 0.5, 0), gamma = 1.4) on the
+    periodic unit square with v = speed (sgn sin 2 pi m x, sgn sin 2 pi m y, 0), m = periods:
+    where both components diverge the flow opens towards vacuum (every limiter of Sec. 3.2-3.3
+    and the Newton solve act), where they collide it drives shocks.  A workload that keeps
+    the positivity limiters busy on a large grid."""
+    def prim(x, y):
+        x = np.asarray(x, dtype=np.float64)
+        y = np.asarray(y, dtype=np.float64) + 0.0 * x
+        z = 0.0 * x
+        v1 = np.where(np.sin(2.0 * math.pi * periods * x) < 0.0, -speed, speed) + z
+        v2 = np.where(np.sin(2.0 * math.pi * periods * y) < 0.0, -speed, speed) + z
+        return (z + 1.0, v1, v2, z, z, z + 0.5, z, z + 0.4)
+    return Problem("rarefaction_lattice", n, n, 0.0, 1.0, 0.0, 1.0, PERIODIC, 1.4, prim, kappa=kappa)
+
+
 def shock_cloud(n: int = 400, kappa: float = 1.0) -> Problem:
     """Shock-cloud interaction (Example 4.7) on [0,1]^2, gamma = 5/3, outflow
     boundaries.  Reading: the printed state vectors list (rho, v1, v2, v3, p, B1,

@@ -47,10 +47,16 @@ WORKLOADS = {
                    lambda: ai.perturbed_vortex(256, seed=0)),
     "jets1024": ("MHD jets (Example 4.8) 1024x3072: left half, reflective at x=0, Mach-800 inflow jet at the "
                  "bottom, B_a=sqrt(20000), kappa=2", lambda: ai.jets(1024)),
+    "jets512": ("MHD jets 512x1536 (profiling size of the jets)", lambda: ai.jets(512)),
     "blast1d": ("1D strong blast (p = 1000 / 0.1, B = (100/sqrt(4pi))(1,1,0)/sqrt(2)) on 4,194,304 cells, "
                 "outflow, kappa=1", lambda: ai.blast1d(1 << 22)),
     "divb2048": ("divergence measures (Example 4.4) of the 2048x2048 low-beta blast after 3 steps",
                  lambda: ai.blast(2048)),
+    "lattice2048": ("rarefaction lattice 2048x2048 periodic (v = 6 (sgn sin 128 pi x, sgn sin 128 pi y), rho = 1, "
+                    "p = 0.4, B = (0, 0.5, 0), gamma = 1.4), kappa=1: every positivity limiter and the Newton "
+                    "solve act in each stage", lambda: ai.rarefaction_lattice(2048, periods=64)),
+    "lattice512": ("rarefaction lattice 512x512, 16 periods (profiling size)",
+                   lambda: ai.rarefaction_lattice(512, periods=16)),
 }
 
 # Algorithmic FP64 flops per cell-stage of each kernel: the arithmetic of the
@@ -63,11 +69,32 @@ ALGO_FLOPS = {
     "blast_low_beta": {"k_pointdata": 714.9, "k_points": 1294.8, "k_faces": 253.9, "k_cells": 628.0, "k_final": 16.3},
     "orszag_tang": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 250.0, "k_cells": 628.0, "k_final": 16.0},
     "vortex": {"k_pointdata": 708.0, "k_points": 1267.0, "k_faces": 234.0, "k_cells": 468.0, "k_final": 16.0},
+    "rarefaction_lattice": {"k_pointdata": 708.5, "k_points": 1267.0, "k_faces": 250.0, "k_cells": 628.0,
+                            "k_final": 16.0},
     "jets": {"k_pointdata": 720.7, "k_points": 1271.6, "k_faces": 250.7, "k_cells": 628.0, "k_final": 16.1},
     "blast1d": {"k1_pointdata": 432.4, "k1_points": 332.1, "k1_faces": 93.0, "k1_cells": 96.0, "k1_final": 16.0},
 }
 # Flops per cell of the two divergence measures (af_divb), same counter.
 ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
+# Executed FP64 arithmetic per cell-stage of each stage kernel: DADD, DMUL and DFMA
+# thread instructions (ncu sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum)
+# of one captured step, divided by the cell-stages of that step.  Flops = DADD + DMUL +
+# 2 DFMA: the arithmetic the kernels execute, which is what the FP64 pipe is timed on.
+# The literal count of the paper's formulas (ALGO_FLOPS) is larger where a kernel uses
+# a cheaper algebraic form (the LLF-FVS line as one expression, products by 1/h), so it
+# is reported beside the roofline, never divided by the peak.  Each table names the
+# capture it comes from and a digest of the kernel sources it was taken on: once the
+# kernels change, the line says so ("counts_stale") until the capture is retaken.
+EXEC_FP64 = {
+    "blast_low_beta": {"source": "profiles/fp64ops_blast1024.md", "kernels": {
+        "k_pointdata": {"dadd": 88.03, "dmul": 142.11, "dfma": 237.18, "pipe": 479.33, "dram_bytes": 1167.5},
+        "k_points": {"dadd": 155.35, "dmul": 51.32, "dfma": 249.92, "pipe": 467.64, "dram_bytes": 1375.8},
+        "k_faces": {"dadd": 60.10, "dmul": 50.03, "dfma": 68.42, "pipe": 191.55, "dram_bytes": 744.6},
+        "k_cells": {"dadd": 67.04, "dmul": 58.04, "dfma": 165.20, "pipe": 297.28, "dram_bytes": 716.7},
+        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 329.3},
+    }},
+}
+EXEC_FP64_DIGEST = "b361fdf6777a1315868cd974e277b8db9fa1b03d"
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
@@ -84,6 +111,60 @@ WORK_DOUBLES_PER_CELL = 163
 # Algorithmic bytes per cell-stage: read U^(s) (32 doubles), read U^n on stages
 # 2 and 3, write U^(s+1): (512 + 768 + 768)/3 B.
 ALGO_BYTES_PER_CS = (512.0 + 768.0 + 768.0) / 3.0
+
+
+def kernel_digest() -> str:
+    """sha1 of the CUDA sources (csrc/*.cu, *.cuh, *.h), in name order."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2506_04857_gb300", "csrc")
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def exec_flops(name: str):
+    """{kernel: executed FP64 flops per cell-stage} of a workload, its source and whether
+    the kernels changed since the capture (None when no capture covers the workload)."""
+    t = EXEC_FP64.get(name)
+    if t is None:
+        return None, None, None
+    fl = {k: v["dadd"] + v["dmul"] + 2.0 * v["dfma"] for k, v in t["kernels"].items()}
+    return fl, t["source"], kernel_digest() != EXEC_FP64_DIGEST
+
+
+def fp64_roofline(name, ktimes, cells_per_launch, units_timed, ms_timed, peak, peak_src, probe, world=1):
+    """Roofline of the dominant stage kernel and of the whole step on executed FP64 flops
+    (bound: the FP64 ALU pipe).  ktimes: {kernel: (total ms, launches)} of the timed region."""
+    lit = ALGO_FLOPS.get(name, {})
+    fl, src, stale = exec_flops(name)
+    known = fl if fl is not None else lit
+    dom = max((k for k in ktimes if k in known), key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dom]
+    avg_s = dom_ms / max(dom_n, 1) * 1e-3
+    tot = sum(v[0] for v in ktimes.values())
+    r = {"bound": "alu", "kernel": dom, "unit": "TFLOP/s", "peak": peak, "peak_source": peak_src,
+         "probe_fp64_tflops": probe,
+         "kernel_time_share": {k: round(v[0] / tot, 4) for k, v in ktimes.items() if v[1]},
+         "literal_flops_per_cell_stage": lit.get(dom), "literal_flops_per_cell_stage_all_kernels": sum(lit.values()),
+         "literal_note": "the paper's formulas counted as written (oracle counting build, PP limiters off); "
+                         "context only, not divided by the peak"}
+    if fl is None:
+        r.update({"achieved": None, "frac": None, "executed_counts": None})
+        return r
+    achieved = fl[dom] * cells_per_launch / avg_s * 1e-12
+    step_tf = sum(fl.values()) * units_timed / (ms_timed * 1e-3) * 1e-12 / world
+    pipe = EXEC_FP64[name]["kernels"][dom].get("pipe")
+    if pipe is not None:   # FP64-pipe thread instructions per second against 2 per SM per cycle (= peak / 2 flops)
+        r["fp64_pipe_busy"] = pipe * cells_per_launch / avg_s / (peak * 1e12 / 2.0)
+    r.update({"achieved": achieved, "frac": achieved / peak, "frac_of_probe": achieved / probe if probe else None,
+              "executed_flops_per_cell_stage": fl[dom], "executed_flops_per_cell_stage_all_kernels": sum(fl.values()),
+              "executed_counts": src, "counts_stale": stale,
+              "step_achieved_tflops": step_tf, "step_frac": step_tf / peak,
+              "step_frac_of_probe": step_tf / probe if probe else None})
+    return r
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -304,6 +385,64 @@ def reference_arm(args, key, desc, pb):
     return 0
 
 
+def ensemble_cost(stream, steps=3, warm=3):
+    """The batched ensemble (256 seeded Orszag-Tang runs, nx, ny drawn from {64, 128, 256,
+    512}) against the plain per-run loop on the same GPU, one rank: aggregate cell-stage
+    updates/s of each, after the autotuner; the batch replays a 3-step CUDA graph."""
+    import torch
+    import paper_2506_04857_gb300 as af
+    every = ai.ot_ensemble(256, seed=0)
+    cells = sum(p.nx * p.ny for p in every)
+    states = [ai.dofs(p) for p in every]
+    with torch.cuda.stream(stream):
+        b = af.af_batch_create([p.nx for p in every], [p.ny for p in every], [p.gamma for p in every],
+                               [p.bc for p in every])
+        af.af_batch_set_stream(b, stream)
+        for r, (p, U) in enumerate(zip(every, states)):
+            af.af_batch_set_domain(b, r, p.x0, p.x1, p.y0, p.y1)
+            af.af_batch_set_params(b, r, cfl=p.cfl, kappa=p.kappa)
+            af.af_batch_set_state(b, r, U)
+        choice = af.af_batch_autotune(b, reps=2)
+        af.af_batch_graph(b, True)
+        af.af_batch_step(b, warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        af.af_batch_step(b, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1)
+        rc, cnt = af.af_batch_status(b, reset=True)
+        if rc != af.AF_OK:
+            raise SystemExit("batch: " + af.af_batch_last_error(b))
+        af.af_batch_destroy(b)
+        solvers = []
+        for p, U in zip(every, states):
+            sv = af.Solver(p.nx, p.ny, p.gamma, p.bc, domain=(p.x0, p.x1, p.y0, p.y1), cfl=p.cfl, kappa=p.kappa,
+                           stream=stream)
+            sv.set_state(U)
+            solvers.append(sv)
+        for _ in range(warm):
+            for sv in solvers:
+                sv.step(dt_out=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            for sv in solvers:
+                sv.step(dt_out=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_loop = e0.elapsed_time(e1)
+        for sv in solvers:
+            sv.close()
+    v_batch = cells * 3 * steps / (ms_batch * 1e-3)
+    v_loop = cells * 3 * steps / (ms_loop * 1e-3)
+    return {"workload": WORKLOADS["ensemble256"][0], "runs": len(every), "cells": cells, "steps": steps,
+            "warmup": warm, "batched": v_batch, "plain_loop": v_loop, "batched_over_loop": v_batch / v_loop,
+            "unit": "cell-stage updates/s", "autotune": choice, "graph": True,
+            "launches_per_step": {"batched": 19, "plain_loop": 19 * len(every)}}
+
+
 def ensemble_bench(args, desc):
     """The batched ensemble against the plain per-run loop on the same GPU.
     Under torchrun the runs are sharded over the ranks (shard_runs; no data
@@ -385,6 +524,52 @@ def ensemble_bench(args, desc):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def limiter_cost(s, pb, stream, cnt, steps, reps=6):
+    """What the positivity limiters cost while they act: the first stage of the current
+    state (the state the timed region ended with) run `reps` times with the PP limiters on
+    and `reps` times with them off (same input, same dt), per-kernel times from af_timing.
+    The difference is the limiter work (the point LLF states and scaling limiter in
+    k_points, the LLF update, source limiter, 16-vertex box and Newton solves in k_cells,
+    the face theta and admissibility test in k_final).  Per limited cell: the k_cells
+    difference over the cells with some Lambda_I < 1 in one such stage."""
+    import paper_2506_04857_gb300 as af
+    U = s.get_state()
+    dt = s.dt()
+    res = {}
+    for pp in (True, False):
+        af.af_set_params(s.ctx, pb.cfl, pb.kappa, pp)
+        s.set_state(U)
+        s.stage(0, dt)            # warm-up
+        s.status(reset=True)
+        s.timing(True)
+        for _ in range(reps):
+            s.set_state(U)
+            s.stage(0, dt)
+        kt = s.timing(False)
+        rc, c = s.status(reset=True)
+        res[pp] = ({k: v[0] / max(v[1], 1) for k, v in kt.items() if v[1]}, c)
+    af.af_set_params(s.ctx, pb.cfl, pb.kappa, True)
+    s.set_state(U)
+    on, c_on = res[True]
+    off, _ = res[False]
+    lam_cells = c_on["lambda_lt1"] / reps
+    out = {"stage_input": "the state after the timed region, first stage, %d repetitions each way" % reps,
+           "ms_per_launch_pp_on": {k: round(v, 4) for k, v in on.items()},
+           "ms_per_launch_pp_off": {k: round(v, 4) for k, v in off.items()},
+           "cells_lambda_lt1_per_stage": lam_cells,
+           "newton_solves_per_stage": c_on["newton_solves"] / reps,
+           "points_limited_per_stage": c_on["point_limited"] / reps,
+           "faces_theta_lt1_per_stage": c_on["face_theta_lt1"] / reps,
+           "timed_region_counters_per_stage": {k: v / (3 * steps) for k, v in cnt.items()
+                                               if k not in ("newton_maxit",)}}
+    stage_on = sum(v for k, v in on.items() if k not in ("k_dt",))
+    stage_off = sum(v for k, v in off.items() if k not in ("k_dt",))
+    out["limiter_share_of_stage"] = (stage_on - stage_off) / stage_on
+    if lam_cells > 0:
+        out["k_cells_extra_ns_per_limited_cell"] = (on["k_cells"] - off["k_cells"]) * 1e6 / lam_cells
+    return out
 
 
 def adjoint_cost(stream, nsteps=200, every=20):
@@ -488,6 +673,7 @@ def oned_bench(args, desc):
     U0 = ai.dofs1(pb)
     s = af.Solver1D(pb.n, pb.gamma, pb.bc, domain=(pb.x0, pb.x1), cfl=pb.cfl, kappa=pb.kappa, stream=stream)
     s.set_state([torch.from_numpy(u).cuda() for u in U0])
+    probe = af.af_probe_fp64(stream)
     for _ in range(args.warmup):
         s.step(dt_out=False)
     torch.cuda.synchronize()
@@ -511,18 +697,9 @@ def oned_bench(args, desc):
     if rc != af.AF_OK:
         raise SystemExit("libaf reported %s after the timed region" % af.af1d_last_error(s.ctx))
     value = pb.n * 3 * args.steps * world / (ms * 1e-3)
-    flops = ALGO_FLOPS[pb.name]
-    dom = max((k for k in ktimes if k in flops), key=lambda k: ktimes[k][0])
-    avg_ms = ktimes[dom][0] / max(ktimes[dom][1], 1)
     peak, peak_src = fp64_peak(torch, local, clk)
-    achieved = flops[dom] * pb.n / (avg_ms * 1e-3) * 1e-12
-    step_tf = sum(flops.values()) * pb.n * 3 * args.steps / (ms * 1e-3) * 1e-12 / world
-    tot = sum(v[0] for v in ktimes.values())
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic_flops_per_cell_stage": flops[dom], "step_achieved_tflops": step_tf,
-                "step_frac": step_tf / peak,
-                "kernel_time_share": {k: round(v[0] / tot, 4) for k, v in ktimes.items() if v[1]}}
+    roofline = fp64_roofline(pb.name, ktimes, pb.n, pb.n * 3 * args.steps * world, ms, peak, peak_src, probe, world)
+    roofline["traffic"] = None
     # end to end through the C ABI with host buffers (blocking copies)
     host = [np.ascontiguousarray(u) for u in U0]
     out = [np.empty_like(u) for u in host]
@@ -634,6 +811,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--cpu-rate-only", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -708,28 +886,16 @@ def main():
     launches = sum(n for _, n in ktimes.values())
 
     # ---------------- roofline of the dominant kernel -----------------------
-    flops = ALGO_FLOPS[pb.name]
-    dom = max((k for k in ktimes if k in flops), key=lambda k: ktimes[k][0])
-    dom_ms, dom_n = ktimes[dom]
-    avg_ms = dom_ms / max(dom_n, 1)
-    achieved = flops[dom] * cells / (avg_ms * 1e-3) * 1e-12
-    kernel_share = {k: round(v[0] / sum(x[0] for x in ktimes.values()), 4) for k, v in ktimes.items() if v[1]}
-    stage_flops = sum(flops.values()) * cells * 3 * args.steps
-    props = torch.cuda.get_device_properties(local)
-    max_mhz = (clk or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz", 2070.0)
-    peak = FP64_FLOPS_PER_SM_CYCLE * props.multi_processor_count * max_mhz * 1e6 * 1e-12
-    traffic = DRAM_BYTES_PER_CELL[dom] * cells if dom in DRAM_BYTES_PER_CELL and pb.name == "blast_low_beta" else None
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": "ncu capture of the 1024x1024 blast, scaled by cells" if traffic else None,
-                "peak_source": "derived: 2 DFMA/SM/cycle x %d SMs x %.0f MHz x 2 flops" % (props.multi_processor_count,
-                                                                                         max_mhz),
-                "probe_fp64_tflops": peak_fp64,
-                "algorithmic_flops_per_cell_stage": flops[dom],
-                "step_achieved_tflops": stage_flops / (ms * 1e-3) * 1e-12 / world,
-                "step_frac": stage_flops / (ms * 1e-3) * 1e-12 / world / peak,
-                "hbm_bound_cell_stages_per_s": measured_peaks().get("hbm_gbs", 6775.6) * 1e9 / ALGO_BYTES_PER_CS,
-                "kernel_time_share": kernel_share}
+    peak, peak_src = fp64_peak(torch, local, clk)
+    roofline = fp64_roofline(pb.name, ktimes, cells, units, ms, peak, peak_src, peak_fp64, world)
+    fl, src, stale = exec_flops(pb.name)
+    dram = EXEC_FP64.get(pb.name, {}).get("kernels", {}).get(roofline["kernel"], {}).get("dram_bytes")
+    roofline["traffic"] = dram * cells if dram is not None and not stale else None
+    roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of the capture, "
+                                  "times the cells of one launch") if roofline["traffic"] else None
+    roofline["hbm_bound_cell_stages_per_s"] = measured_peaks().get("hbm_gbs", 6775.6) * 1e9 / ALGO_BYTES_PER_CS
+
+    limiter = limiter_cost(s, pb, stream, cnt, args.steps) if key.startswith("lattice") else None
 
     # ---------------- end to end through the C ABI with host buffers --------
     # af_step_host: every step copies its input state from pinned host memory and
@@ -775,8 +941,13 @@ def main():
                            "l2": l2_note(sum(u.nbytes for u in U0), WORK_DOUBLES_PER_CELL * 8 * cells)},
                 "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "clocks": clk,
                 "limiter_counters": cnt}
+        if limiter is not None:
+            line["limiter_cost"] = limiter
         if not args.no_adjoint and world == 1:
             line["adjoint"] = adjoint_cost(stream)
+        if not args.no_ensemble and world == 1 and key == "blast2048":
+            s.close()
+            line["ensemble"] = ensemble_cost(stream)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(key, pb)
         print(json.dumps(line), flush=True)

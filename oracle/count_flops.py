@@ -122,6 +122,8 @@ def main():
     args = ap.parse_args()
     res = {"blast_low_beta": count(ai.blast(args.n)), "orszag_tang": count(ai.orszag_tang(args.n)),
            "vortex": count(ai.vortex(args.n)),
+           # 32 cells per period, as in the 2048x2048, 64-period workload
+           "rarefaction_lattice": count(ai.rarefaction_lattice(args.n, periods=max(1, args.n // 32))),
            # the jets' ghost point data (reflective and inflow sides) is formed per
            # ghost, so a wider grid keeps that overhead small
            "jets": count(ai.jets(4 * args.n)),
