@@ -236,6 +236,55 @@ int af_adjoint_step_stages(af_ctx *ctx, const double *dt, int dt_on_device, cons
                            const double *const U2[4], const double *const U3[4], const double *const lam_in[4],
                            double *const lam_out[4], int on_device, int flags);
 
+/* ---------------------------------------------------------------------------
+ * The limited branch: limiter coefficients recorded, frozen and transposed.
+ * Along a recorded branch the limiters of Sec. 3 are blends with fixed
+ * coefficients: theta^s per face and theta^s_ij per cell (Sec. 3.4), theta_ij
+ * (Sec. 3.2 step 1), the face theta of step (3) after the Remark 4.1 shrink,
+ * and the scaling-limiter theta*, theta** of every point value (Sec. 3.3,
+ * after Remark 4.1; 0 for the fall-back to the LLF state) and of every cell
+ * centre (Remark 3.2).  With them held at the values a forward stage took,
+ * the stage is a smooth function of its input (up to the maxima inside the
+ * alpha of the LLF fluxes and of the FVS lines, differentiated along the
+ * branch they take), and its transpose is what the discrete adjoint of a
+ * limited run needs.  Not in the paper.
+ *
+ * Coefficient block of one stage: AF_NCOEF arrays [nyp][nxp] (nxp, nyp: the
+ * index grid, nx or nx + 1 for outflow), at the index of the face, cell or
+ * point they belong to: 0 theta^s of x-faces, 1 of y-faces, 2 face theta of
+ * x-faces, 3 of y-faces, 4 theta_ij, 5-6 theta*, theta** of the cell centres,
+ * 7-8 of the x-face values, 9-10 of the y-face values, 11-12 of the corners.
+ * A buffer for a step holds three blocks (stage s at s * af_coeff_len).  The
+ * buffers are the caller's device memory, on the context's device. */
+#define AF_NCOEF 13
+/* *n = doubles in one stage block. */
+int af_coeff_len(const af_ctx *ctx, long long *n);
+/* buf (device, 3 blocks) or NULL: while set, every af_stage / af_step writes
+ * its coefficients into the block of its stage index.  Not while frozen. */
+int af_record_coeffs(af_ctx *ctx, double *buf);
+/* buf (device, 3 blocks) or NULL: while set, every af_stage / af_step uses the
+ * coefficients of its stage index from buf instead of forming them (the
+ * frozen branch: no limiter test, no shrink; AF_EINVAL with the PP limiters
+ * off).  Not while recording. */
+int af_freeze_coeffs(af_ctx *ctx, const double *buf);
+/* out = (d FE(U)/dU)^T lam for the forward-Euler stage FE of the current
+ * state U with time step dt (host or device pointer) along the branch frozen
+ * at coeffs (one stage block, device): lam and out have the state layout
+ * (device pointers when on_device = 1, host arrays otherwise; they must not
+ * alias).  Periodic or outflow sides, central point source.  The state is not
+ * advanced. */
+int af_stage_vjp(af_ctx *ctx, const double *dt, int dt_on_device, const double *coeffs, const double *const lam[4],
+                 double *const out[4], int on_device);
+/* af_adjoint_step_stages along the recorded branch: lam_out = (dU^{n+1}/dU^n)^T
+ * lam_in for the step from the current state U^n whose stage states were U1,
+ * U2 (and U3 = U^{n+1} with AF_ADJ_DT) and whose coefficients af_record_coeffs
+ * wrote into coeffs (three blocks, device).  Any kappa; the limiters may have
+ * acted.  AF_ADJ_DT as for af_adjoint_step, with the coefficients held fixed.
+ * The state is not advanced.  The call synchronises the stream at its end. */
+int af_adjoint_step_frozen(af_ctx *ctx, const double *dt, int dt_on_device, const double *const U1[4],
+                           const double *const U2[4], const double *const U3[4], const double *coeffs,
+                           const double *const lam_in[4], double *const lam_out[4], int on_device, int flags);
+
 /* af_dt followed by the three stages.  *dt_used (host or device, may be NULL)
  * receives the step's dt. */
 int af_step(af_ctx *ctx, double *dt_used, int on_device);
@@ -268,7 +317,8 @@ int af_sync(af_ctx *ctx);
 int af_status(af_ctx *ctx, long long *counters, int reset);
 
 /* Kernels of one stage, in the order af_timing reports them. */
-enum { AF_K_POINTDATA = 0, AF_K_DT, AF_K_POINTS, AF_K_FACES, AF_K_CELLS, AF_K_FINAL, AF_K_REPAIR, AF_NKERNEL };
+enum { AF_K_POINTDATA = 0, AF_K_DT, AF_K_POINTS, AF_K_FACES, AF_K_CELLS, AF_K_FINAL, AF_K_REPAIR,
+       AF_K_POINTS_SLOW, AF_K_CELLS_SLOW, AF_NKERNEL };
 
 /* Per-kernel device timing for measurement tools.  enable = 1 clears the
  * record and starts bracketing every kernel launch of this context with a

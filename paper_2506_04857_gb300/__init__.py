@@ -22,7 +22,8 @@ import numpy as np
 __all__ = [
     "AF_BC_PERIODIC", "AF_BC_OUTFLOW", "AF_OK", "AFError", "af_create", "af_set_domain", "af_set_params",
     "af_get_params", "af_set_stream", "af_sizes", "af_set_state", "af_get_state", "af_get_stage", "af_rhs", "af_rhs_vjp", "af_adjoint_step",
-    "af_adjoint_step_stages", "af_diagnostics", "af_sensor", "af_dt",
+    "af_adjoint_step_stages", "af_diagnostics", "af_sensor", "af_dt", "af_coeff_len", "af_record_coeffs",
+    "af_freeze_coeffs", "af_stage_vjp", "af_adjoint_step_frozen", "AF_NCOEF",
     "af_stage",
     "af_step", "af_step_host", "af_sync", "af_status", "af_timing", "af_probe_fp64", "af_rhs_noalloc", "af_batch_create",
     "af_batch_set_domain", "af_batch_set_params", "af_batch_set_stream", "af_batch_set_state", "af_batch_get_state",
@@ -36,6 +37,11 @@ AF_NSTAT = 12
 AF_ADJ_RECORDED = 1
 AF_ADJ_DT = 2
 AF_SIDE_OUTFLOW, AF_SIDE_REFLECTIVE, AF_SIDE_INFLOW = 0, 1, 2
+AF_NCOEF = 13
+# slots of a stage's coefficient block (af.h): theta^s and face theta of x- and y-faces, theta_ij,
+# and the scaling-limiter theta*, theta** of the cell centres and of the three point classes
+COEFF_SLOTS = ["ths_x", "ths_y", "th_x", "th_y", "th_src", "thc_1", "thc_2", "thp1_1", "thp1_2", "thp2_1",
+               "thp2_2", "thp3_1", "thp3_2"]
 STAT_NAMES = ["src_limited", "lambda_lt1", "face_theta_lt1", "sensor_lt099", "newton_solves", "newton_maxit",
               "shrink", "point_limited", "cfl_violations", "center_limited", "nonadmissible", "cell_shrink"]
 _CODES = {AF_EINVAL: "AF_EINVAL", AF_ECUDA: "AF_ECUDA", AF_ENOMEM: "AF_ENOMEM", AF_ENONPHYS: "AF_ENONPHYS",
@@ -92,6 +98,11 @@ def _lib():
             lib.af_diagnostics.argtypes = [vp, vp, C.c_int]
             lib.af_adjoint_step.argtypes = [vp, vp, C.c_int, pp, pp, C.c_int, C.c_int]
             lib.af_adjoint_step_stages.argtypes = [vp, vp, C.c_int, pp, pp, pp, pp, pp, C.c_int, C.c_int]
+            lib.af_coeff_len.argtypes = [vp, C.POINTER(C.c_longlong)]
+            lib.af_record_coeffs.argtypes = [vp, vp]
+            lib.af_freeze_coeffs.argtypes = [vp, vp]
+            lib.af_stage_vjp.argtypes = [vp, vp, C.c_int, vp, pp, pp, C.c_int]
+            lib.af_adjoint_step_frozen.argtypes = [vp, vp, C.c_int, pp, pp, pp, vp, pp, pp, C.c_int, C.c_int]
             lib.af_status.argtypes = [vp, C.POINTER(C.c_longlong), C.c_int]
             lib.af_last_error.argtypes = [vp]
             lib.af_last_error.restype = C.c_char_p
@@ -386,6 +397,76 @@ def af_adjoint_step_stages(ctx, dt, U1, U2, lam, U3=None, out=None, device: bool
     return out
 
 
+def _dt_arg(dt):
+    if _is_tensor(dt) and dt.is_cuda:
+        return dt.data_ptr(), 1, None
+    v = C.c_double(float(dt))
+    return C.cast(C.byref(v), C.c_void_p), 0, v
+
+
+def af_coeff_len(ctx) -> int:
+    """Doubles in one stage's block of limiter coefficients (AF_NCOEF index grids)."""
+    n = C.c_longlong()
+    _check(ctx, _lib().af_coeff_len(ctx, C.byref(n)))
+    return n.value
+
+
+def _coeff_ptr(ctx, buf, blocks: int):
+    torch = _torch()
+    if buf is None:
+        return None
+    if not (_is_tensor(buf) and buf.is_cuda) or buf.dtype != torch.float64 or not buf.is_contiguous():
+        raise ValueError("coefficients: a contiguous CUDA float64 tensor")
+    if buf.numel() < blocks * af_coeff_len(ctx):
+        raise ValueError("coefficients: need %d doubles" % (blocks * af_coeff_len(ctx)))
+    return buf.data_ptr()
+
+
+def af_record_coeffs(ctx, buf) -> None:
+    """buf: a CUDA float64 tensor of 3 * af_coeff_len(ctx) doubles, or None to stop recording."""
+    _check(ctx, _lib().af_record_coeffs(ctx, _coeff_ptr(ctx, buf, 3)))
+
+
+def af_freeze_coeffs(ctx, buf) -> None:
+    """buf: recorded coefficients (3 stage blocks), or None to return to the limiters."""
+    _check(ctx, _lib().af_freeze_coeffs(ctx, _coeff_ptr(ctx, buf, 3)))
+
+
+def af_stage_vjp(ctx, dt, coeffs, lam, out=None, device: bool = True):
+    """(d FE(U)/dU)^T lam of the forward-Euler stage of the current state along the branch
+    frozen at coeffs (one stage block, CUDA float64 tensor)."""
+    ptrs, dev, keep = _marshal_in(ctx, lam)
+    out, optrs, odev = _outputs(ctx, out, device)
+    if dev != odev:
+        raise ValueError("lam and out must both be on the device or both on the host")
+    dtp, dtd, dtk = _dt_arg(dt)
+    _check(ctx, _lib().af_stage_vjp(ctx, dtp, dtd, _coeff_ptr(ctx, coeffs, 1), ptrs, optrs, dev))
+    del keep, dtk
+    return out
+
+
+def af_adjoint_step_frozen(ctx, dt, U1, U2, coeffs, lam, U3=None, out=None, device: bool = True,
+                           dt_sensitivity: bool = False):
+    """The adjoint of one step along its recorded branch (af.h): U1, U2 (and U3) the forward
+    step's stage states, coeffs its recorded coefficients (3 blocks)."""
+    ptrs, dev, keep = _marshal_in(ctx, lam)
+    p1, d1, k1 = _marshal_in(ctx, U1)
+    p2, d2, k2 = _marshal_in(ctx, U2)
+    if U3 is not None:
+        p3, d3, k3 = _marshal_in(ctx, U3)
+    else:
+        p3, d3, k3 = None, dev, None
+    out, optrs, odev = _outputs(ctx, out, device)
+    if len({dev, odev, d1, d2, d3}) != 1:
+        raise ValueError("lam, out and the stage states must all be on the device or all on the host")
+    dtp, dtd, dtk = _dt_arg(dt)
+    flags = AF_ADJ_DT if dt_sensitivity else 0
+    _check(ctx, _lib().af_adjoint_step_frozen(ctx, dtp, dtd, p1, p2, p3, _coeff_ptr(ctx, coeffs, 3), ptrs, optrs,
+                                              dev, flags))
+    del keep, k1, k2, k3, dtk
+    return out
+
+
 def af_rhs(ctx, out=None, device: bool = True):
     out, ptrs, dev = _outputs(ctx, out, device)
     _check(ctx, _lib().af_rhs(ctx, ptrs, dev))
@@ -449,7 +530,8 @@ def af_status(ctx, reset: bool = False):
     return rc, dict(zip(STAT_NAMES, [int(v) for v in cnt]))
 
 
-KERNEL_NAMES = ["k_pointdata", "k_dt", "k_points", "k_faces", "k_cells", "k_final", "k_repair"]
+KERNEL_NAMES = ["k_pointdata", "k_dt", "k_points", "k_faces", "k_cells", "k_final", "k_repair", "k_points_slow",
+                "k_cells_slow"]
 
 
 def af_timing(ctx, enable: bool):

@@ -27,6 +27,20 @@
 // A 5-point FVS line of an output with index s holds points with indices
 // s-1, s, s+1 along its direction (after the periodic wrap or the outflow
 // mirror), so a DoF is gathered from the outputs at offsets -1, 0, +1.
+//
+// Frozen branch (limiter coefficients recorded by a forward stage, co != NULL):
+// with theta^s, theta_ij, the face theta (Sec. 3.2, 3.4) and the scaling-limiter
+// theta*, theta** (Sec. 3.3, Remark 3.2) held at their recorded values, a
+// limited forward-Euler stage is FE(U) = U + dt L_w(U) with
+//   cell averages: the face flux w_f F^ + (1 - w_f) F^LLF, w_f = theta_f theta^s_f,
+//                  the source w_c S + (1 - w_c) S^LLF, w_c = theta_ij theta^s_ij;
+//   point values:  m o L_pt(U) + (1 - m) o L^LLF_pt(U), m = (theta* theta**, theta**, ...);
+//   cell centres:  m_c o U_c + (1 - m_c) o Ubar (Remark 3.2 toward the average).
+// The kernels above then run on the weighted cotangents (A0 scales the point
+// rows by m; A1, A2 weight the cell rows by w_f, w_c; A3 applies m_c), and AL
+// adds the transposes of the first-order LLF terms (eq. 2d_llf_flux, S^LLF and
+// the three point LLF schemes of Sec. 3.3), with alpha^LLF differentiated along
+// the branch its maxima take.
 #include "../../include/af.h"
 #include "af_internal.h"
 #include "af_math.cuh"
@@ -116,6 +130,30 @@ __device__ __forceinline__ double psi(const AfDev &d, const AfGrid &g, const PI 
   return pval(d, g, q, QP_V1 + (k - 4));
 }
 
+// ---- frozen limiter coefficients (co: one stage's AF_NCOEF arrays, or NULL) ----
+__device__ __forceinline__ double cof(const double *co, const AfGrid &g, int slot, int i, int j) {
+  return __ldg(co + (size_t)slot * g.nxa * g.nya + (size_t)j * g.nxa + i);
+}
+// weight of the high-order flux at x-face (fi, fj) (dir 0) or y-face (dir 1), stored indices
+__device__ __forceinline__ double wface(const double *co, const AfGrid &g, int dir, int fi, int fj) {
+  if (!co) return 1.0;
+  return cof(co, g, dir ? AFC_THY : AFC_THX, fi, fj) * cof(co, g, dir ? AFC_TSY : AFC_TSX, fi, fj);
+}
+// weight of the high-order source of cell (i, j): theta_ij times the least theta^s of its faces
+__device__ __forceinline__ double wcell(const double *co, const AfGrid &g, int i, int j) {
+  if (!co) return 1.0;
+  const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
+  const double ts = fmin(fmin(cof(co, g, AFC_TSX, i, j), cof(co, g, AFC_TSX, ip, j)),
+                         fmin(cof(co, g, AFC_TSY, i, j), cof(co, g, AFC_TSY, i, jp)));
+  return cof(co, g, AFC_TSRC, i, j) * ts;
+}
+// scaling-limiter weight of component k: theta* theta** for the density, theta** otherwise
+// (slot s1: theta* of the class or of the cell centre)
+__device__ __forceinline__ double mweight(const double *co, const AfGrid &g, int s1, int i, int j, int k) {
+  const double t2 = cof(co, g, s1 + 1, i, j);
+  return k == 0 ? cof(co, g, s1, i, j) * t2 : t2;
+}
+
 // ---------------------------------------------------------------------------
 // A1
 // ---------------------------------------------------------------------------
@@ -180,14 +218,15 @@ __device__ __forceinline__ void point_div(const AfDev &d, const AfGrid &g, const
 }
 
 __device__ __forceinline__ void cell_terms(const AfDev &d, const AfGrid &g, const Vec4 &v, int i, int j, double rdx,
-                                           double rdy, double *a) {
+                                           double rdy, double *a, const double *co) {
   PI N[9];
   cell_nodes(g, i, j, N);
   constexpr double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
   const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
+  const double wc = wcell(co, g, i, j);
   double vc[8];
 #pragma unroll
-  for (int k = 1; k < 8; ++k) vc[k] = vval(v, g, 0, i, j, k);
+  for (int k = 1; k < 8; ++k) vc[k] = vval(v, g, 0, i, j, k) * wc;
 #pragma unroll
   for (int m = 0; m < 3; ++m)
 #pragma unroll
@@ -211,7 +250,7 @@ __device__ __forceinline__ void cell_terms(const AfDev &d, const AfGrid &g, cons
 
 // blockIdx.z: 0 corners, 1 x-faces, 2 y-faces, 3 cells
 __global__ void __launch_bounds__(128) k_adj1(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
-                                              const __grid_constant__ Vec4 v, double *a) {
+                                              const __grid_constant__ Vec4 v, double *a, const double *co) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
   switch (blockIdx.z) {
@@ -235,7 +274,7 @@ __global__ void __launch_bounds__(128) k_adj1(const __grid_constant__ AfDev d, c
       }
       break;
     default:
-      if (i < g.nx && j < g.ny) cell_terms(d, g, v, i, j, rdx, rdy, a);
+      if (i < g.nx && j < g.ny) cell_terms(d, g, v, i, j, rdx, rdy, a, co);
   }
 }
 
@@ -248,7 +287,16 @@ struct Acc {
   double ps[8];     // of Psi
   double B[2];      // of B1, B2 through the divergence stencils
   double U[8];      // direct cotangent of U (the alpha (U0 + U4 - ...) terms)
+  double av[2];     // of |v_1|, |v_2| (alpha^LLF)
+  double cf[2];     // of c_f1, c_f2 (alpha^LLF)
+  double srho;      // of sqrt(rho) (alpha^LLF)
 };
+__device__ __forceinline__ void acc_zero(Acc &a) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a.F[0][k] = a.F[1][k] = a.ps[k] = a.U[k] = 0.0;
+  a.sr[0] = a.sr[1] = a.B[0] = a.B[1] = a.av[0] = a.av[1] = a.cf[0] = a.cf[1] = a.srho = 0.0;
+}
+
 
 // output of class oc at offset o (-1..1) from q along dir, mapped into range;
 // false when it does not exist
@@ -329,7 +377,8 @@ __device__ __forceinline__ void gather_central(const AfGrid &g, const Vec4 &v, c
 // left/lower (+) or right/upper (-) face
 template <int DIR>
 __device__ __forceinline__ void face_cot(const AfGrid &g, const Vec4 &v, int fi, int fj, double wgt, double rh,
-                                         Acc &acc) {
+                                         Acc &acc, const double *co) {
+  wgt *= wface(co, g, DIR, fi, fj);
 #pragma unroll
   for (int o = -1; o <= 0; ++o) {
     int ci = fi, cj = fj;
@@ -354,9 +403,9 @@ __device__ __forceinline__ void face_cot(const AfGrid &g, const Vec4 &v, int fi,
 
 template <int C>
 __device__ __forceinline__ void gather_simpson(const AfGrid &g, const Vec4 &v, const PI &q, double rdx, double rdy,
-                                               Acc &acc) {
-  if constexpr (C == CX) face_cot<0>(g, v, q.i, q.j, 4.0 / 6.0, rdx, acc);   // middle node of its own face
-  if constexpr (C == CY) face_cot<1>(g, v, q.i, q.j, 4.0 / 6.0, rdy, acc);
+                                               Acc &acc, const double *co) {
+  if constexpr (C == CX) face_cot<0>(g, v, q.i, q.j, 4.0 / 6.0, rdx, acc, co);   // middle node of its own face
+  if constexpr (C == CY) face_cot<1>(g, v, q.i, q.j, 4.0 / 6.0, rdy, acc, co);
   if constexpr (C == CC) {
     // corner: end node (weight 1/6) of the x-faces below/above and the y-faces left/right
 #pragma unroll
@@ -365,12 +414,12 @@ __device__ __forceinline__ void gather_simpson(const AfGrid &g, const Vec4 &v, c
       if (candidate(g, CX, 1, q, o, s)) {
         const int hj = mface(s.j + 1, g.ny, g.bc);
         const double wgt = (s.j == q.j ? 1.0 : 0.0) + (hj == q.j ? 1.0 : 0.0);
-        if (wgt != 0.0) face_cot<0>(g, v, s.i, s.j, wgt / 6.0, rdx, acc);
+        if (wgt != 0.0) face_cot<0>(g, v, s.i, s.j, wgt / 6.0, rdx, acc, co);
       }
       if (candidate(g, CY, 0, q, o, s)) {
         const int hi = mface(s.i + 1, g.nx, g.bc);
         const double wgt = (s.i == q.i ? 1.0 : 0.0) + (hi == q.i ? 1.0 : 0.0);
-        if (wgt != 0.0) face_cot<1>(g, v, s.i, s.j, wgt / 6.0, rdy, acc);
+        if (wgt != 0.0) face_cot<1>(g, v, s.i, s.j, wgt / 6.0, rdy, acc, co);
       }
     }
   }
@@ -379,7 +428,7 @@ __device__ __forceinline__ void gather_simpson(const AfGrid &g, const Vec4 &v, c
 // the 3x3 source nodes of the cells that have q as a node (node n = l + 3 m)
 template <int C>
 __device__ __forceinline__ void gather_source(const AfGrid &g, const Vec4 &v, const double *a, const PI &q, double rdx,
-                                              double rdy, Acc &acc) {
+                                              double rdy, Acc &acc, const double *co) {
   constexpr int na = C == CC ? 4 : (C == CZ ? 1 : 2);
   constexpr int nodes[4] = {C == CC ? 0 : (C == CX ? 3 : (C == CY ? 1 : 4)), C == CC ? 2 : (C == CX ? 5 : 7),
                             6, 8};
@@ -400,7 +449,7 @@ __device__ __forceinline__ void gather_source(const AfGrid &g, const Vec4 &v, co
         const int n = nodes[t];
         if (!same(N[n], q)) continue;
         const int l = n % 3, m = n / 3;
-        const double wd = aval(a, g, ci, cj, A_WD + n);
+        const double wd = aval(a, g, ci, cj, A_WD + n) * wcell(co, g, ci, cj);
 #pragma unroll
         for (int k = 1; k < 8; ++k) acc.ps[k] = fma(-wd, vval(v, g, 0, ci, cj, k), acc.ps[k]);
         double s1 = 0.0, s2 = 0.0;
@@ -457,10 +506,10 @@ __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGri
   double ab = 0, c2b = 0, k4b = 0;
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
-    const double srb = acc.sr[l];
-    if (srb == 0.0) continue;
+    const double avb = acc.sr[l] + acc.av[l], srb = acc.sr[l] + acc.cf[l];   // of |v_l| and of c_f,l
     const double vl = l == 0 ? v1 : v2, Bl = l == 0 ? B1 : B2;
-    if (l == 0) vb1 += vl >= 0.0 ? srb : -srb; else vb2 += vl >= 0.0 ? srb : -srb;
+    if (l == 0) vb1 += vl >= 0.0 ? avb : -avb; else vb2 += vl >= 0.0 ? avb : -avb;
+    if (srb == 0.0) continue;
     double dd = a * a - k4 * Bl * Bl;
     if (dd < 0.0) dd = 0.0;
     const double sd = dsqrt(dd);
@@ -496,6 +545,7 @@ __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGri
   mb1 += vb1 * r; mb2 += vb2 * r; mb3 += vb3 * r;
   rbar += vb1 * m1 + vb2 * m2 + vb3 * m3;
   out[0] = -r * r * rbar + acc.U[0];
+  if (acc.srho != 0.0) out[0] += 0.5 * acc.srho * rcp(dsqrt(rho));   // d sqrt(rho) / d rho
   out[1] = mb1 + acc.U[1];
   out[2] = mb2 + acc.U[2];
   out[3] = mb3 + acc.U[3];
@@ -507,13 +557,12 @@ __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGri
 
 template <int C>
 __device__ __forceinline__ void adj_point(const AfDev &d, const AfGrid &g, const Vec4 &v, const double *a, int i,
-                                          int j, double rdx, double rdy, double *const *tp, double *zc) {
+                                          int j, double rdx, double rdy, double *const *tp, double *zc,
+                                          const double *co) {
   const PI q = {C, i, j};
   if (!valid_point(g, q)) return;
   Acc acc;
-#pragma unroll
-  for (int k = 0; k < 8; ++k) acc.F[0][k] = acc.F[1][k] = acc.ps[k] = acc.U[k] = 0.0;
-  acc.sr[0] = acc.sr[1] = acc.B[0] = acc.B[1] = 0.0;
+  acc_zero(acc);
   if (C == CC || C == CY) gather_lines<CC, 0>(d, g, v, a, q, rdx, acc);
   if (C == CC || C == CX) gather_lines<CC, 1>(d, g, v, a, q, rdy, acc);
   if (C == CX || C == CZ) gather_lines<CX, 0>(d, g, v, a, q, rdx, acc);
@@ -522,8 +571,8 @@ __device__ __forceinline__ void adj_point(const AfDev &d, const AfGrid &g, const
     gather_central<0>(g, v, a, q, rdx, acc);
     gather_central<1>(g, v, a, q, rdy, acc);
   }
-  gather_simpson<C>(g, v, q, rdx, rdy, acc);
-  gather_source<C>(g, v, a, q, rdx, rdy, acc);
+  gather_simpson<C>(g, v, q, rdx, rdy, acc, co);
+  gather_source<C>(g, v, a, q, rdx, rdy, acc, co);
   if (C != CZ && g.src_point_on) {   // own Powell term -(div B) Psi
     constexpr int sdb = C == CC ? A_C_DB : (C == CX ? A_X_DB : A_Y_DB);
     const double divB = aval(a, g, i, j, sdb);
@@ -548,14 +597,14 @@ __device__ __forceinline__ void adj_point(const AfDev &d, const AfGrid &g, const
 // blockIdx.z: 0 x-faces, 1 y-faces, 2 corners, 3 cell centres
 __global__ void __launch_bounds__(128) k_adj2(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                               const __grid_constant__ Vec4 v, const double *a,
-                                              const __grid_constant__ OVec4 tp, double *zc) {
+                                              const __grid_constant__ OVec4 tp, double *zc, const double *co) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy;
   switch (blockIdx.z) {
-    case 0: adj_point<CX>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
-    case 1: adj_point<CY>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
-    case 2: adj_point<CC>(d, g, v, a, i, j, rdx, rdy, tp.p, zc); break;
-    default: adj_point<CZ>(d, g, v, a, i, j, rdx, rdy, tp.p, zc);
+    case 0: adj_point<CX>(d, g, v, a, i, j, rdx, rdy, tp.p, zc, co); break;
+    case 1: adj_point<CY>(d, g, v, a, i, j, rdx, rdy, tp.p, zc, co); break;
+    case 2: adj_point<CC>(d, g, v, a, i, j, rdx, rdy, tp.p, zc, co); break;
+    default: adj_point<CZ>(d, g, v, a, i, j, rdx, rdy, tp.p, zc, co);
   }
 }
 
@@ -564,14 +613,22 @@ __global__ void __launch_bounds__(128) k_adj2(const __grid_constant__ AfDev d, c
 // ---------------------------------------------------------------------------
 template <int C>
 __device__ __forceinline__ void adj_final(const AfGrid &g, const double *zc, const double *const *tp,
-                                          const AfAdjEpi &e, int i, int j) {
+                                          const AfAdjEpi &e, int i, int j, const double *co) {
   if (i >= g.ex[C] || j >= g.ey[C]) return;
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t cs = (size_t)g.ex[C] * g.ey[C], oo = (size_t)j * g.ex[C] + i;
   double T[8];
   if (C == 0) {
+    if (co) {   // frozen branch: Remark 3.2 blend m_c o U_c + (1 - m_c) o Ubar, plus the LLF part (AL)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) T[k] = 2.25 * __ldg(zc + k * PS + (size_t)j * g.nxa + i);
+      for (int k = 0; k < 8; ++k) {
+        const double z = __ldg(zc + k * PS + (size_t)j * g.nxa + i), m = mweight(co, g, AFC_C1, i, j, k);
+        T[k] = fma(2.25 * m, z, fma(1.0 - m, z, __ldg(tp[0] + k * cs + oo)));
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) T[k] = 2.25 * __ldg(zc + k * PS + (size_t)j * g.nxa + i);
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < 8; ++k) T[k] = __ldg(tp[C] + k * cs + oo);
@@ -593,7 +650,10 @@ __device__ __forceinline__ void adj_final(const AfGrid &g, const double *zc, con
           if (n != 4 && same(N[n], q)) wgt += (n == 1 || n == 3 || n == 5 || n == 7) ? -0.25 : -0.0625;
         if (wgt == 0.0) continue;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) T[k] = fma(wgt, __ldg(zc + k * PS + (size_t)cj * g.nxa + ci), T[k]);
+        for (int k = 0; k < 8; ++k) {
+          const double m = co ? mweight(co, g, AFC_C1, ci, cj, k) : 1.0;
+          T[k] = fma(wgt * m, __ldg(zc + k * PS + (size_t)cj * g.nxa + ci), T[k]);
+        }
       }
   }
   const double bs = e.dt ? e.b * __ldg(e.dt) : e.b;
@@ -610,13 +670,310 @@ __device__ __forceinline__ void adj_final(const AfGrid &g, const double *zc, con
 
 // blockIdx.z: DoF class 0..3
 __global__ void __launch_bounds__(128) k_adj3(const __grid_constant__ AfGrid g, const double *zc,
-                                              const __grid_constant__ OVec4 tp, const __grid_constant__ AfAdjEpi e) {
+                                              const __grid_constant__ OVec4 tp, const __grid_constant__ AfAdjEpi e,
+                                              const double *co) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
   switch (blockIdx.z) {
-    case 0: adj_final<0>(g, zc, tp.p, e, i, j); break;
-    case 1: adj_final<1>(g, zc, tp.p, e, i, j); break;
-    case 2: adj_final<2>(g, zc, tp.p, e, i, j); break;
-    default: adj_final<3>(g, zc, tp.p, e, i, j);
+    case 0: adj_final<0>(g, zc, tp.p, e, i, j, co); break;
+    case 1: adj_final<1>(g, zc, tp.p, e, i, j, co); break;
+    case 2: adj_final<2>(g, zc, tp.p, e, i, j, co); break;
+    default: adj_final<3>(g, zc, tp.p, e, i, j, co);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Frozen branch: A0 (point rows scaled by the scaling-limiter weights m) and AL
+// (transposes of the first-order LLF terms)
+// ---------------------------------------------------------------------------
+// blockIdx.z: point class 1..3 (z = 0 idle); vp = m o v for that class
+__global__ void __launch_bounds__(128) k_adj0(const __grid_constant__ AfGrid g, const __grid_constant__ Vec4 v,
+                                              const __grid_constant__ OVec4 vp, const double *co) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y, c = blockIdx.z;
+  if (c == 0 || i >= g.ex[c] || j >= g.ey[c]) return;
+  const size_t cs = (size_t)g.ex[c] * g.ey[c], oo = (size_t)j * g.ex[c] + i;
+  const int s1 = AFC_P1 + 2 * (c - 1);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) vp.p[c][k * cs + oo] = mweight(co, g, s1, i, j, k) * __ldg(v.p[c] + k * cs + oo);
+}
+
+// What alpha^LLF along direction l and Psi need of one state
+struct LS {
+  double U[8], v[3], B[3], vB, cf, srho;
+};
+__device__ __forceinline__ void lstate(const AfDev &d, const AfGrid &g, int c, int i, int j, int l, LS &s) {
+  const size_t cs = (size_t)g.ex[c] * g.ey[c], oo = (size_t)j * g.ex[c] + i;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s.U[k] = __ldg(d.us[c] + k * cs + oo);
+  const double rho = s.U[0], r = rcp(rho);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.v[k] = s.U[1 + k] * r;
+    s.B[k] = s.U[4 + k];
+  }
+  s.vB = fma(s.v[0], s.B[0], fma(s.v[1], s.B[1], s.v[2] * s.B[2]));
+  const double BB = fma(s.B[0], s.B[0], fma(s.B[1], s.B[1], s.B[2] * s.B[2]));
+  const double mv = fma(s.U[1], s.v[0], fma(s.U[2], s.v[1], s.U[3] * s.v[2]));
+  const double p = g.gm1 * fma(-0.5, mv + BB, s.U[7]);
+  const double c2 = g.gamma * p * r, a = fma(BB, r, c2);
+  double dd = fma(-4.0 * (c2 * r), s.B[l] * s.B[l], a * a);
+  dd = dd > 0.0 ? dd : 0.0;
+  s.cf = dsqrt(fma(0.5, dsqrt(dd), 0.5 * a));
+  s.srho = dsqrt(rho);
+}
+
+// Cotangent c of F^LLF_l(Ua, Ub) = (F_l(Ua) + F_l(Ub) - alpha (Ub - Ua)) / 2 (eq. 2d_llf_flux)
+// taken back to state a (which = 0) or b (which = 1) of that flux.  alpha^LLF =
+// max(|v_a|, |v_b|) + max(c_f,a, c_f,b) + |B_a - B_b| / (sqrt(rho_a) + sqrt(rho_b))
+// (Lemma 3.1 with equality), differentiated through the terms its maxima take
+// (ties: state a).
+__device__ __forceinline__ void llf_vjp(int l, int which, const LS &a, const LS &b, const double *c, Acc &acc) {
+  const double va = absd(a.v[l]), vb = absd(b.v[l]);
+  const double d0 = a.B[0] - b.B[0], d1 = a.B[1] - b.B[1], d2 = a.B[2] - b.B[2];
+  const double n = dsqrt(fma(d0, d0, fma(d1, d1, d2 * d2))), den = a.srho + b.srho;
+  const double al = fmax(va, vb) + fmax(a.cf, b.cf) + n / den;
+  double T = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) T = fma(c[k], b.U[k] - a.U[k], T);
+  const double h = -0.5 * T, sal = which == 0 ? 0.5 * al : -0.5 * al;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    acc.F[l][k] = fma(0.5, c[k], acc.F[l][k]);
+    acc.U[k] = fma(sal, c[k], acc.U[k]);
+  }
+  if (which == 0 ? va >= vb : vb > va) acc.av[l] += h;
+  if (which == 0 ? a.cf >= b.cf : b.cf > a.cf) acc.cf[l] += h;
+  if (n > 0.0) {
+    const double sb = (which == 0 ? h : -h) / (n * den);
+    acc.U[4] = fma(sb, d0, acc.U[4]);
+    acc.U[5] = fma(sb, d1, acc.U[5]);
+    acc.U[6] = fma(sb, d2, acc.U[6]);
+    acc.srho -= h * n / (den * den);
+  }
+}
+
+// Psi(U) . w over the components 1..7 (Psi = (0, B, v, v.B))
+__device__ __forceinline__ double psi_dot(const LS &s, const double *w) {
+  return fma(w[1], s.B[0], fma(w[2], s.B[1], fma(w[3], s.B[2],
+             fma(w[4], s.v[0], fma(w[5], s.v[1], fma(w[6], s.v[2], w[7] * s.vB))))));
+}
+
+// The four LLF neighbours (left/right along x, low/high along y) of point value
+// (c, i, j), mapped as the forward point limiter maps them (Sec. 3.3).
+__device__ __forceinline__ void llf_nbrs(const AfGrid &g, int c, int i, int j, PI *nb) {
+  if (c == CC) {
+    nb[0] = {CC, mface(i - 1, g.nx, g.bc), j}; nb[1] = {CC, mface(i + 1, g.nx, g.bc), j};
+    nb[2] = {CC, i, mface(j - 1, g.ny, g.bc)}; nb[3] = {CC, i, mface(j + 1, g.ny, g.bc)};
+  } else if (c == CX) {
+    nb[0] = {CX, mface(i - 1, g.nx, g.bc), j}; nb[1] = {CX, mface(i + 1, g.nx, g.bc), j};
+    nb[2] = {CC, i, j}; nb[3] = {CC, i, mface(j + 1, g.ny, g.bc)};
+  } else {
+    nb[0] = {CC, i, j}; nb[1] = {CC, mface(i + 1, g.nx, g.bc), j};
+    nb[2] = {CY, i, mface(j - 1, g.ny, g.bc)}; nb[3] = {CY, i, mface(j + 1, g.ny, g.bc)};
+  }
+}
+
+// (1 - m) o v of point p, false when m = 1 (the point limiter took theta* = theta** = 1)
+__device__ __forceinline__ bool llf_cot(const AfGrid &g, const Vec4 &v, const double *co, const PI &p, double *gp) {
+  const int s1 = AFC_P1 + 2 * (p.c - 1);
+  const double t1 = cof(co, g, s1, p.i, p.j), t2 = cof(co, g, s1 + 1, p.i, p.j);
+  if (t1 == 1.0 && t2 == 1.0) return false;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) gp[k] = (1.0 - (k == 0 ? t1 * t2 : t2)) * vval(v, g, p.c, p.i, p.j, k);
+  return true;
+}
+
+// candidate point values whose LLF stencil may hold point q
+__device__ __forceinline__ int llf_candidates(const AfGrid &g, const PI &q, PI *cand) {
+  int n = 0;
+  auto add = [&](int c, int i, int j) {
+    if (g.bc == 0) {
+      i = wrapi(i, g.ex[c]);
+      j = wrapi(j, g.ey[c]);
+    }
+    if (i >= 0 && j >= 0 && i < g.ex[c] && j < g.ey[c]) cand[n++] = {c, i, j};
+  };
+  if (q.c == CC) {
+    add(CC, q.i - 1, q.j); add(CC, q.i + 1, q.j); add(CC, q.i, q.j - 1); add(CC, q.i, q.j + 1);
+    add(CX, q.i, q.j); add(CX, q.i, q.j - 1); add(CY, q.i, q.j); add(CY, q.i - 1, q.j);
+  } else if (q.c == CX) {
+    add(CX, q.i - 1, q.j); add(CX, q.i + 1, q.j);
+  } else {
+    add(CY, q.i, q.j - 1); add(CY, q.i, q.j + 1);
+  }
+  return n;
+}
+
+template <int C>
+__device__ __forceinline__ void adj_llf(const AfDev &d, const AfGrid &g, const Vec4 &v, const double *co, int i,
+                                        int j, double *const *tp) {
+  const double rdx = g.rdx, rdy = g.rdy;
+  Acc acc;
+  acc_zero(acc);
+  bool touched = false;
+  LS me, ot;
+  if constexpr (C == 0) {
+    if (i >= g.nx || j >= g.ny) return;
+    // face fluxes F^LLF of the cell's four faces (weight 1 - w_f)
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+      const int n = dir ? g.ny : g.nx, io = dir ? j : i;
+      const double rh = dir ? rdy : rdx;
+      lstate(d, g, 0, i, j, dir, me);
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const int f = io + side, fs = mface(f, n, g.bc);
+        const double w = wface(co, g, dir, dir ? i : fs, dir ? fs : j);
+        if (w == 1.0) continue;
+        double cv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) cv[k] = 0.0;
+        // the real cells on either side: -F/h for the left/lower one, +F/h for the right/upper one
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          int ci = f - 1 + t;
+          if (g.bc == 0) ci = wrapi(ci, n);
+          else if (ci < 0 || ci >= n) continue;
+          const double sg = (t ? 1.0 : -1.0) * (1.0 - w) * rh;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) cv[k] = fma(sg, vval(v, g, 0, dir ? i : ci, dir ? ci : j, k), cv[k]);
+        }
+        const int ma = mcell(f - 1, n, g.bc), mb = mcell(f, n, g.bc);
+        if (ma == io) {
+          lstate(d, g, 0, dir ? i : mb, dir ? mb : j, dir, ot);
+          llf_vjp(dir, 0, me, ot, cv, acc);
+        }
+        if (mb == io) {
+          lstate(d, g, 0, dir ? i : ma, dir ? ma : j, dir, ot);
+          llf_vjp(dir, 1, ot, me, cv, acc);
+        }
+        touched = true;
+      }
+    }
+    // S^LLF = (central div Bbar) Psi(Ubar) of the cell and of its neighbours (weight 1 - w_c)
+    if (g.src_cell_on) {
+      const int cc[5][2] = {{i, j}, {i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+#pragma unroll
+      for (int t = 0; t < 5; ++t) {
+        int ci = cc[t][0], cj = cc[t][1];
+        if (g.bc == 0) {
+          ci = wrapi(ci, g.nx);
+          cj = wrapi(cj, g.ny);
+        } else if (ci < 0 || cj < 0 || ci >= g.nx || cj >= g.ny) {
+          continue;
+        }
+        const double wc = wcell(co, g, ci, cj);
+        if (wc == 1.0) continue;
+        const int e = mcell(ci + 1, g.nx, g.bc), wv = mcell(ci - 1, g.nx, g.bc);
+        const int nn = mcell(cj + 1, g.ny, g.bc), sv = mcell(cj - 1, g.ny, g.bc);
+        double gc[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) gc[k] = -(1.0 - wc) * vval(v, g, 0, ci, cj, k);
+        lstate(d, g, 0, ci, cj, 0, ot);
+        const double sc = psi_dot(ot, gc);
+        const double c1 = ((cj == j && e == i) ? 1.0 : 0.0) - ((cj == j && wv == i) ? 1.0 : 0.0);
+        const double c2 = ((ci == i && nn == j) ? 1.0 : 0.0) - ((ci == i && sv == j) ? 1.0 : 0.0);
+        acc.U[4] = fma(c1 * 0.5 * rdx, sc, acc.U[4]);
+        acc.U[5] = fma(c2 * 0.5 * rdy, sc, acc.U[5]);
+        if (t == 0) {   // its own Psi, times its central div Bbar
+          const SV A = sview(d.us[0], g, 0);
+          const double divB = fma(A(e, cj, 4) - A(wv, cj, 4), 0.5 * rdx, (A(ci, nn, 5) - A(ci, sv, 5)) * (0.5 * rdy));
+#pragma unroll
+          for (int k = 1; k < 8; ++k) acc.ps[k] = fma(divB, gc[k], acc.ps[k]);
+        }
+        touched = true;
+      }
+    }
+    const size_t cs = (size_t)g.nx * g.ny, oo = (size_t)j * g.nx + i;
+    double o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (touched) {
+      lstate(d, g, 0, i, j, 0, me);
+      pointwise_transpose(me.U, g, acc, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tp[0][k * cs + oo] = o[k];
+  } else {
+    const PI q = {C, i, j};
+    if (!valid_point(g, q)) return;
+    double gq[8];
+    PI nb[4];
+    // its own LLF state: -(F1(q, xr) - F1(xl, q))/dx - (F2(q, yr) - F2(yl, q))/dy - div B Psi(q)
+    if (llf_cot(g, v, co, q, gq)) {
+      llf_nbrs(g, C, i, j, nb);
+      double cp[8], cm[8];
+#pragma unroll
+      for (int l = 0; l < 2; ++l) {
+        const double rh = l ? rdy : rdx;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          cp[k] = rh * gq[k];
+          cm[k] = -rh * gq[k];
+        }
+        lstate(d, g, C, i, j, l, me);
+        lstate(d, g, nb[2 * l].c, nb[2 * l].i, nb[2 * l].j, l, ot);
+        llf_vjp(l, 1, ot, me, cp, acc);
+        lstate(d, g, nb[2 * l + 1].c, nb[2 * l + 1].i, nb[2 * l + 1].j, l, ot);
+        llf_vjp(l, 0, me, ot, cm, acc);
+      }
+      if (g.src_point_on) {
+        const double divB = fma(uval(d, g, nb[1], 4) - uval(d, g, nb[0], 4), 0.5 * rdx,
+                                (uval(d, g, nb[3], 5) - uval(d, g, nb[2], 5)) * (0.5 * rdy));
+#pragma unroll
+        for (int k = 1; k < 8; ++k) acc.ps[k] = fma(-divB, gq[k], acc.ps[k]);
+      }
+      touched = true;
+    }
+    // as a neighbour in the LLF states of other points
+    PI cand[8];
+    const int nc = llf_candidates(g, q, cand);
+    for (int t = 0; t < nc; ++t) {
+      const PI p = cand[t];
+      double gp[8];
+      if (!llf_cot(g, v, co, p, gp)) continue;
+      llf_nbrs(g, p.c, p.i, p.j, nb);
+      for (int r = 0; r < 4; ++r) {
+        if (!same(nb[r], q)) continue;
+        const int l = r >> 1;
+        const double rh = l ? rdy : rdx;
+        double cv[8];
+        lstate(d, g, C, i, j, l, me);
+        lstate(d, g, p.c, p.i, p.j, l, ot);
+        if (r & 1) {   // q is the right/high neighbour: flux F(p, q), cotangent -g_p/h
+#pragma unroll
+          for (int k = 0; k < 8; ++k) cv[k] = -rh * gp[k];
+          llf_vjp(l, 1, ot, me, cv, acc);
+        } else {       // left/low neighbour: flux F(q, p), cotangent +g_p/h
+#pragma unroll
+          for (int k = 0; k < 8; ++k) cv[k] = rh * gp[k];
+          llf_vjp(l, 0, me, ot, cv, acc);
+        }
+        if (g.src_point_on) {   // div B of p: +-B_l(q) / (2 h)
+          const double sp = psi_dot(ot, gp) * 0.5 * rh;
+          acc.U[4 + l] += (r & 1) ? -sp : sp;
+        }
+        touched = true;
+      }
+    }
+    if (!touched) return;
+    double U[8], o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) U[k] = uval(d, g, q, k);
+    pointwise_transpose(U, g, acc, o);
+    const size_t cs = (size_t)g.ex[C] * g.ey[C], oo = (size_t)j * g.ex[C] + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) tp[C][k * cs + oo] += o[k];
+  }
+}
+
+// blockIdx.z: DoF class 0..3; after A2 (adds into its point outputs, writes tp[0])
+__global__ void __launch_bounds__(128) k_adjl(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                              const __grid_constant__ Vec4 v, const __grid_constant__ OVec4 tp,
+                                              const double *co) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  switch (blockIdx.z) {
+    case 0: adj_llf<0>(d, g, v, co, i, j, tp.p); break;
+    case 1: adj_llf<CX>(d, g, v, co, i, j, tp.p); break;
+    case 2: adj_llf<CY>(d, g, v, co, i, j, tp.p); break;
+    default: adj_llf<CC>(d, g, v, co, i, j, tp.p);
   }
 }
 
@@ -742,8 +1099,7 @@ __global__ void __launch_bounds__(256) k_dt_apply(const __grid_constant__ AfDev 
     double U[8], grad[8];
     for (int k = 0; k < 8; ++k) U[k] = d.un[c][k * cs + o];
     Acc acc;
-    for (int k = 0; k < 8; ++k) acc.F[0][k] = acc.F[1][k] = acc.ps[k] = acc.U[k] = 0.0;
-    acc.sr[0] = acc.sr[1] = acc.B[0] = acc.B[1] = 0.0;
+    acc_zero(acc);
     acc.sr[l] = 1.0;
     pointwise_transpose(U, g, acc, grad);                       // d varrho_l / dU at that DoF
     const double coef = -mudt * dt / g.cfl * (l == 0 ? g.rdx : g.rdy);   // mu * (-dt^2/cfl) / h_l
@@ -780,14 +1136,21 @@ void af_launch_dt_apply(const AfDev &d, const AfGrid &g, double *const *lam, dou
   k_dt_apply<<<1, 256, 0, s>>>(d, g, dpart, pv, pi, nb, lo, mu_out);
 }
 void af_launch_vjp(const AfDev &d, const AfGrid &g, const AfAdjEpi &e, double *a, double *zc, double *const *tpart,
-                   cudaStream_t s) {
-  Vec4 vv;
-  OVec4 tp;
+                   cudaStream_t s, const double *co, double *const *vscaled) {
+  Vec4 vv, vr;
+  OVec4 tp, vs;
   for (int c = 0; c < 4; ++c) {
     vv.p[c] = e.v[c];
+    vr.p[c] = e.v[c];
     tp.p[c] = tpart[c];
+    vs.p[c] = co ? vscaled[c] : nullptr;
   }
-  k_adj1<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a);
-  k_adj2<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a, tp, zc);
-  k_adj3<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(g, zc, tp, e);
+  if (co) {   // frozen branch: point rows weighted by m (A0), then A1, A2 on those
+    k_adj0<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(g, vr, vs, co);
+    for (int c = 1; c < 4; ++c) vv.p[c] = vscaled[c];
+  }
+  k_adj1<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a, co);
+  k_adj2<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vv, a, tp, zc, co);
+  if (co) k_adjl<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(d, g, vr, tp, co);
+  k_adj3<<<grid3(g.nxa, g.nya), dim3(32, 4), 0, s>>>(g, zc, tp, e, co);
 }

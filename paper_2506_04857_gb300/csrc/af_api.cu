@@ -47,6 +47,11 @@ struct af_ctx {
   const char *recent_out[3][4];   // host output ranges of the last three af_step_host calls
   size_t recent_len[4];
   AfEventTimer tm;        // per-kernel event timing (af_timing)
+  // limiter coefficients: af_record_coeffs / af_freeze_coeffs (caller's device
+  // buffers of three stage blocks), and the frozen adjoint's scratch state
+  double *rec_buf;
+  const double *frz_buf;
+  double *vscale;
   char msg[512];
 };
 
@@ -156,8 +161,10 @@ void run_stage(af_ctx *c, double a, double b, int reduce_dt) {
   TIMED(AF_K_POINTDATA, af_launch_pointdata(c->dev, c->g, reduce_dt, c->stream));
   if (reduce_dt) TIMED(AF_K_DT, af_launch_dt(c->dev, c->g, c->stream));
   TIMED(AF_K_POINTS, af_launch_points(c->dev, c->g, a, b, 0, c->stream));
+  if (c->g.pp_on && !c->dev.frz) TIMED(AF_K_POINTS_SLOW, af_launch_points_slow(c->dev, c->g, a, b, c->stream));
   TIMED(AF_K_FACES, af_launch_faces(c->dev, c->g, 0, c->stream));
   TIMED(AF_K_CELLS, af_launch_cells(c->dev, c->g, a, b, 0, c->stream));
+  if (c->g.pp_on && !c->dev.frz) TIMED(AF_K_CELLS_SLOW, af_launch_cells_slow(c->dev, c->g, c->stream));
   if (c->g.pp_on) {
     TIMED(AF_K_FINAL, af_launch_final(c->dev, c->g, a, b, c->stream));
     TIMED(AF_K_REPAIR, af_launch_repair(c->dev, c->g, a, b, c->stream));
@@ -181,7 +188,18 @@ int stage_impl(af_ctx *c, int s, int reduce_dt) {
   if (s == 0) bind_states(c, n, n, b1);
   else if (s == 1) bind_states(c, n, b1, b2);
   else bind_states(c, n, b2, b1);
+  const size_t PS = (size_t)c->g.nxa * c->g.nya, blk = (size_t)AF_NCOEF * PS;
+  c->dev.rec = c->rec_buf ? c->rec_buf + s * blk : nullptr;
+  c->dev.frz = c->frz_buf ? c->frz_buf + s * blk : nullptr;
   run_stage(c, RK_A[s], RK_B[s], reduce_dt);
+  if (c->dev.rec && c->g.pp_on) {   // face theta after the Remark 4.1 repair
+    CK(cudaMemcpyAsync(c->dev.rec + AFC_THX * PS, c->dev.thx, PS * sizeof(double), cudaMemcpyDeviceToDevice,
+                       c->stream), "record face theta");
+    CK(cudaMemcpyAsync(c->dev.rec + AFC_THY * PS, c->dev.thy, PS * sizeof(double), cudaMemcpyDeviceToDevice,
+                       c->stream), "record face theta");
+  }
+  c->dev.rec = nullptr;
+  c->dev.frz = nullptr;
   CK(cudaGetLastError(), "stage launch");
   c->last_out = s == 1 ? b2 : b1;
   if (s == 2) c->cur = b1;
@@ -223,7 +241,9 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   }
   c->state_len = off;
   const size_t PS = (size_t)c->g.nxa * c->g.nya;
-  const size_t nwork = PS * (AF_NQA + 4 * AF_NQP + 8 + 4 + 2 * AF_NQF + 4 + 8 + 2);
+  // stage work arrays, then the limiter work lists: points (3 PS entries: an int and 8
+  // doubles each), cells (PS entries: an int and 2 doubles each)
+  const size_t nwork = PS * (AF_NQA + 4 * AF_NQP + 8 + 4 + 2 * AF_NQF + 4 + 8 + 2) + PS * (24 + 2) + 2 * PS + 1;
   int rc = AF_OK;
   for (int b = 0; b < 3; ++b) {
     if (cudaMalloc(&c->state[b], off * sizeof(double)) != cudaSuccess) rc = AF_ENOMEM;
@@ -252,6 +272,12 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   c->dev.lim1 = w; w += 8 * PS;
   c->dev.thx = w; w += PS;
   c->dev.thy = w; w += PS;
+  c->dev.pq_cap = (int)(3 * PS);
+  c->dev.cq_cap = (int)PS;
+  c->dev.pqu = w; w += 24 * PS;
+  c->dev.cqe = w; w += 2 * PS;
+  c->dev.pq = reinterpret_cast<int *>(w); w += (3 * PS + 1) / 2;
+  c->dev.cq = reinterpret_cast<int *>(w); w += (PS + 1) / 2;
   c->dev.sc = c->sc;
   c->dev.st = c->st;
   c->cur = 0;
@@ -445,13 +471,15 @@ void buf_cls(const af_ctx *c, const double *base, const double *out[4]) {
 }
 // Transposed operator at the state U (class pointers) whose point data is in
 // set `set`: the last kernel writes e.out1 (and e.out2), see AfAdjEpi.
-void vjp_at(af_ctx *c, const double *const U[4], int set, const AfAdjEpi &e) {
+void vjp_at(af_ctx *c, const double *const U[4], int set, const AfAdjEpi &e, const double *co = nullptr) {
   bind_pd(c, set);
   bind_cls(c, U);
-  double *tp[4];
+  double *tp[4], *vs[4];
   class_ptrs(c, abuf(c, 1), tp);
+  if (co) class_ptrs(c, c->vscale, vs);
   const size_t PS = (size_t)c->g.nxa * c->g.nya;
-  af_launch_vjp(c->dev, c->g, e, c->adj, c->adj + (size_t)af_adj_nslots() * PS, tp, c->stream);
+  af_launch_vjp(c->dev, c->g, e, c->adj, c->adj + (size_t)af_adj_nslots() * PS, tp, c->stream, co,
+                co ? vs : nullptr);
   bind_pd(c, 2);
 }
 AfAdjEpi epi(const double *const v[4], double *const out1[4], double a, double b, const double *dt) {
@@ -526,7 +554,9 @@ namespace {
 // U0, U1, U2, whose point data are in the sets 0, 1 and 2; S[3] is U3 =
 // U^{n+1} (read only with_dt).  dt is on the device (c->sc->dt).
 int adjoint_sweep(af_ctx *c, const double *const S[4][4], const double *const lam_in[4], double *const lam_out[4],
-                  int on_device, bool with_dt) {
+                  int on_device, bool with_dt, const double *coeffs = nullptr) {
+  const size_t blk = (size_t)AF_NCOEF * c->g.nxa * c->g.nya;
+  const double *co[3] = {coeffs, coeffs ? coeffs + blk : nullptr, coeffs ? coeffs + 2 * blk : nullptr};
   const double *dtp = &c->sc->dt;
   int rc = AF_OK;
   // reverse of U1 = FE(U0), U2 = 3/4 U0 + 1/4 FE(U1), U3 = 1/3 U0 + 2/3 FE(U2), FE(U) = U + dt L(U):
@@ -548,7 +578,7 @@ int adjoint_sweep(af_ctx *c, const double *const S[4][4], const double *const la
     L3[cls] = on_device ? lam_in[cls] : L3b[cls];
     L0[cls] = on_device ? lam_out[cls] : L0b[cls];
   }
-  vjp_at(c, S[2], 2, epi(L3, L2, 2.0 / 3.0, 2.0 / 3.0, dtp));
+  vjp_at(c, S[2], 2, epi(L3, L2, 2.0 / 3.0, 2.0 / 3.0, dtp), co[2]);
   AfAdjEpi e1 = epi(L2, L1, 0.25, 0.25, dtp);
   for (int cls = 0; cls < 4; ++cls) {
     e1.out2[cls] = W[cls];
@@ -556,14 +586,14 @@ int adjoint_sweep(af_ctx *c, const double *const S[4][4], const double *const la
   }
   e1.e = 0.75;
   e1.f = 1.0 / 3.0;
-  vjp_at(c, S[1], 1, e1);
+  vjp_at(c, S[1], 1, e1, co[1]);
   if (with_dt) {   // mu dt from L3, L2, L1 and the stage states, before the last VJP may overwrite L3
     af_launch_dt_dot(c->g, L3, L2, L1, S[0], S[1], S[2], S[3], c->dts, c->stream);
   }
   AfAdjEpi e0 = epi(L1, L0, 1.0, 1.0, dtp);
   for (int cls = 0; cls < 4; ++cls) e0.z1[cls] = W[cls];
   e0.c = 1.0;
-  vjp_at(c, S[0], 0, e0);
+  vjp_at(c, S[0], 0, e0, co[0]);
   if (with_dt) {
     bind_pd(c, 0);
     bind_cls(c, S[0]);
@@ -699,6 +729,137 @@ int af_adjoint_step_stages(af_ctx *c, const double *dt, int dt_on_device, const 
   if (c->cnt_pin[16 + ST_CENTER_LIMITED] != c->cnt_pin[ST_CENTER_LIMITED])
     return fail(c, AF_EINVAL, "af_adjoint_step_stages: the cell-centre limiter acted on a stage state; the transpose "
                 "covers the branch on which every limiter is inactive");
+  return AF_OK;
+}
+
+// ---- the frozen branch: recorded limiter coefficients ------------------------
+int af_coeff_len(const af_ctx *c, long long *n) {
+  if (!c || !n) return AF_EINVAL;
+  *n = (long long)AF_NCOEF * c->g.nxa * c->g.nya;
+  return AF_OK;
+}
+
+int af_record_coeffs(af_ctx *c, double *buf) {
+  if (!c) return AF_EINVAL;
+  if (buf && c->frz_buf) return fail(c, AF_EINVAL, "coefficients are frozen; af_freeze_coeffs(ctx, NULL) first");
+  c->rec_buf = buf;
+  return AF_OK;
+}
+
+int af_freeze_coeffs(af_ctx *c, const double *buf) {
+  if (!c) return AF_EINVAL;
+  if (buf && c->rec_buf) return fail(c, AF_EINVAL, "coefficients are being recorded; af_record_coeffs(ctx, NULL) first");
+  if (buf && !c->g.pp_on) return fail(c, AF_EINVAL, "the frozen branch needs the positivity limiters on");
+  c->frz_buf = buf;
+  return AF_OK;
+}
+
+namespace {
+int frozen_args(af_ctx *c, const double *coeffs) {
+  if (!coeffs) return fail(c, AF_EINVAL, "coefficients missing");
+  if (c->g.special) return fail(c, AF_EINVAL, "the transpose covers periodic and outflow boundaries only");
+  if (c->g.upwind) return fail(c, AF_EINVAL, "the transpose covers the central point source only");
+  if (!c->g.pp_on) return fail(c, AF_EINVAL, "the frozen branch needs the positivity limiters on");
+  if (!c->vscale && cudaMalloc(&c->vscale, sizeof(double) * c->state_len) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, AF_ENOMEM, "frozen adjoint workspace");
+  }
+  return AF_OK;
+}
+// point data (and limited centre values, Remark 3.2 frozen at co) of U into set `set`
+void frozen_pointdata(af_ctx *c, const double *const U[4], int set, const double *co) {
+  bind_pd(c, set);
+  bind_cls(c, U);
+  c->dev.frz = co;
+  af_launch_pointdata(c->dev, c->g, 0, c->stream);
+  c->dev.frz = nullptr;
+}
+}  // namespace
+
+int af_stage_vjp(af_ctx *c, const double *dt, int dt_on_device, const double *coeffs, const double *const lam[4],
+                 double *const out[4], int on_device) {
+  AfNvtxRange nvtx_("af_stage_vjp");
+  if (!c || !lam || !out) return AF_EINVAL;
+  for (int cls = 0; cls < 4; ++cls)
+    if (!lam[cls] || !out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+  int rc = frozen_args(c, coeffs);
+  if (rc) return rc;
+  CK(cudaSetDevice(c->device), "set device");
+  rc = ensure_adjoint(c);
+  if (!rc) rc = set_dt(c, dt, dt_on_device);
+  if (rc) return rc;
+  const double *vp[4], *Ucur[4];
+  double *op[4], *in_buf[4], *out_buf[4];
+  class_ptrs(c, abuf(c, 0), in_buf);
+  class_ptrs(c, abuf(c, 2), out_buf);
+  if (!on_device) {
+    rc = copy_in_buf(c, abuf(c, 0), lam, 0);
+    if (rc) return rc;
+  }
+  for (int cls = 0; cls < 4; ++cls) {
+    vp[cls] = on_device ? lam[cls] : in_buf[cls];
+    op[cls] = on_device ? out[cls] : out_buf[cls];
+  }
+  buf_cls(c, c->state[c->cur], Ucur);
+  frozen_pointdata(c, Ucur, 2, coeffs);
+  vjp_at(c, Ucur, 2, epi(vp, op, 1.0, 1.0, &c->sc->dt), coeffs);
+  bind_states(c, c->cur, c->cur, (c->cur + 1) % 3);
+  CK(cudaGetLastError(), "stage vjp launch");
+  c->next_stage = 0;
+  if (on_device) return AF_OK;
+  return copy_out_buf(c, abuf(c, 2), out, 0);
+}
+
+int af_adjoint_step_frozen(af_ctx *c, const double *dt, int dt_on_device, const double *const U1[4],
+                           const double *const U2[4], const double *const U3[4], const double *coeffs,
+                           const double *const lam_in[4], double *const lam_out[4], int on_device, int flags) {
+  AfNvtxRange nvtx_("af_adjoint_step_frozen");
+  if (!c) return AF_EINVAL;
+  if (!dt || !lam_in || !lam_out) return fail(c, AF_EINVAL, "NULL argument");
+  for (int cls = 0; cls < 4; ++cls)
+    if (!lam_in[cls] || !lam_out[cls]) return fail(c, AF_EINVAL, "class %d is NULL", cls);
+  if (flags & ~AF_ADJ_DT) return fail(c, AF_EINVAL, "unknown flags %d", flags);
+  const bool with_dt = (flags & AF_ADJ_DT) != 0;
+  int rc = frozen_args(c, coeffs);
+  if (rc) return rc;
+  if (!U1 || !U2 || (with_dt && !U3)) return fail(c, AF_EINVAL, "stage states missing");
+  for (int cls = 0; cls < 4; ++cls)
+    if (!U1[cls] || !U2[cls] || (with_dt && !U3[cls])) return fail(c, AF_EINVAL, "stage class %d is NULL", cls);
+  CK(cudaSetDevice(c->device), "set device");
+  rc = ensure_adjoint(c);
+  if (!rc) rc = set_dt(c, dt, dt_on_device);
+  if (rc) return rc;
+  const int n = c->cur, b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+  const size_t blk = (size_t)AF_NCOEF * c->g.nxa * c->g.nya;
+  const double *S[4][4];
+  buf_cls(c, c->state[n], S[0]);
+  if (on_device) {
+    for (int cls = 0; cls < 4; ++cls) {
+      S[1][cls] = U1[cls];
+      S[2][cls] = U2[cls];
+      S[3][cls] = with_dt ? U3[cls] : nullptr;
+    }
+  } else {
+    rc = copy_in_buf(c, c->state[b1], U1, 0);
+    if (!rc) rc = copy_in_buf(c, c->state[b2], U2, 0);
+    if (!rc && with_dt) rc = copy_in_buf(c, abuf(c, 5), U3, 0);
+    if (rc) return rc;
+    buf_cls(c, c->state[b1], S[1]);
+    buf_cls(c, c->state[b2], S[2]);
+    buf_cls(c, abuf(c, 5), S[3]);
+  }
+  for (int set = 0; set < 3; ++set) frozen_pointdata(c, S[set], set, coeffs + set * blk);
+  CK(cudaGetLastError(), "point data");
+  rc = adjoint_sweep(c, S, lam_in, lam_out, on_device, with_dt, coeffs);
+  bind_pd(c, 2);
+  bind_states(c, c->cur, c->cur, (c->cur + 1) % 3);
+  if (rc) return rc;
+  c->next_stage = 0;
+  if (!on_device) {
+    rc = copy_out_buf(c, abuf(c, 1), lam_out, 0);
+    if (rc) return rc;
+  }
+  CK(cudaStreamSynchronize(c->stream), "synchronise");
   return AF_OK;
 }
 
@@ -919,6 +1080,7 @@ void af_destroy(af_ctx *c) {
   if (c->inflow_dev) cudaFree(c->inflow_dev);
   if (c->cnt_pin) cudaFreeHost(c->cnt_pin);
   if (c->abuf) cudaFree(c->abuf);
+  if (c->vscale) cudaFree(c->vscale);
   for (int k = 0; k < 2; ++k) {
     if (c->pipe_in[k]) cudaFree(c->pipe_in[k]);
     if (c->pipe_out[k]) cudaFree(c->pipe_out[k]);

@@ -25,6 +25,14 @@ enum { QP_F1 = 0, QP_F2 = 7, QP_SR1 = 14, QP_SR2 = 15, QP_V1 = 16, QP_V2 = 17, Q
 enum { QA_F1 = 0, QA_F2 = 7, QA_CF1 = 14, QA_CF2 = 15, QA_V1 = 16, QA_V2 = 17, QA_V3 = 18, QA_PT = 19, QA_SRHO = 20 };
 enum { QF_FLLF = 0, QF_G = 8, QF_TS = 16, QF_AL = 17 };
 
+// Limiter coefficients of one stage (af_record_coeffs, af_freeze_coeffs): AF_NCOEF
+// arrays [nya][nxa], at the index point of the face, cell or point they belong to.
+// Point classes c = 1..3 use AFC_P1 + 2 (c - 1) (theta*) and the slot after it (theta**).
+enum { AFC_TSX = 0, AFC_TSY, AFC_THX, AFC_THY, AFC_TSRC, AFC_C1, AFC_C2, AFC_P1 };
+#ifndef AF_NCOEF
+#define AF_NCOEF 13   // also in af.h
+#endif
+
 // counters (same meaning and order as the af_status counters in af.h)
 enum {
   ST_SRC_LIMITED = 0, ST_LAMBDA_LT1, ST_FACE_THETA_LT1, ST_SENSOR_LT099, ST_NEWTON_SOLVES, ST_NEWTON_MAXIT,
@@ -32,7 +40,7 @@ enum {
 };
 
 // device error bits
-enum { AFE_NONADMISSIBLE = 1, AFE_REPAIR_OVERFLOW = 2, AFE_NONFINITE_DT = 4 };
+enum { AFE_NONADMISSIBLE = 1, AFE_REPAIR_OVERFLOW = 2, AFE_NONFINITE_DT = 4, AFE_LIST_OVERFLOW = 8 };
 
 struct AfGrid {
   int nx, ny, bc;          // cells; 0 periodic, 1 outflow
@@ -66,6 +74,7 @@ struct AfStatus {
   int err;
   int nrepair;
   int repair[AF_MAX_REPAIR];
+  int npq, ncq;   // entries of the point and cell work lists of the current stage
 };
 
 struct AfDev {
@@ -81,6 +90,15 @@ struct AfDev {
   AfScalars *sc;
   AfStatus *st;
   const double *inflow;   // inflow state [8], its point data as a point [AF_NQP] and as an average [AF_NQA]
+  double *rec;            // when set: the stage writes its limiter coefficients here (AFC_* slots)
+  const double *frz;      // when set: the stage takes its limiter coefficients from here (frozen branch)
+  // work lists of the limiter slow paths (single runs; NULL: slow paths inline, as in batches):
+  // points whose update leaves the 1e-13 floors (packed class << 28 | index, and their
+  // high-order update, component-major), cells whose Sec. 3.2 box is not certified
+  // (index, eps_rho, eps_p)
+  int *pq, *cq;
+  double *pqu, *cqe;
+  int pq_cap, cq_cap;
 };
 
 // one member of a batch (af_batch.cu): its work pointers and grid
@@ -96,6 +114,9 @@ void af_launch_points(const AfDev &d, const AfGrid &g, double a, double b, int m
 void af_launch_faces(const AfDev &d, const AfGrid &g, int mode, cudaStream_t s);
 void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mode, cudaStream_t s);
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
+// the limiter slow paths over the work lists the point and cell passes filled
+void af_launch_points_slow(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
+void af_launch_cells_slow(const AfDev &d, const AfGrid &g, cudaStream_t s);
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s);
 float af_run_fp64_probe(cudaStream_t s, double *flops);
 // point data of the inflow state U (device, 8 doubles) into out (8 + AF_NQP + AF_NQA doubles)
@@ -220,6 +241,8 @@ struct AfAdjEpi {
 // a: af_adj_nslots() work arrays, zc: 8 work arrays (per index point),
 // tpart: a state-sized scratch buffer (four class pointers)
 int af_adj_nslots();
+// co: one stage's frozen limiter coefficients (NULL: the branch on which every limiter
+// is inactive); vscaled: a state-sized scratch (four class pointers) used when co is set
 void af_launch_vjp(const AfDev &d, const AfGrid &g, const AfAdjEpi &e, double *a, double *zc, double *const *tpart,
-                   cudaStream_t s);
+                   cudaStream_t s, const double *co = nullptr, double *const *vscaled = nullptr);
 void af_launch_math_check(int op, const double *x, const double *y, double *out, long long n, cudaStream_t s);

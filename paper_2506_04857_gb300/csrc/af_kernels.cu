@@ -45,6 +45,22 @@ __device__ __forceinline__ void count(AfStatus *st, int slot, bool pred) {
   if (m && (threadIdx.x & 31) == (__ffs(act) - 1)) atomicAdd(&st->cnt[slot], (unsigned long long)__popc(m));
 }
 
+// Slot of this thread in a work list (warp-aggregated; every active thread enqueues
+// one entry), or -1 with the overflow bit set when the list is full.
+__device__ __forceinline__ int enqueue(AfStatus *st, int *counter, int cap) {
+  const unsigned act = __activemask();
+  const int lane = threadIdx.x & 31, leader = __ffs(act) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(act));
+  base = __shfl_sync(act, base, leader);
+  const int slot = base + __popc(act & ((1u << lane) - 1u));
+  if (slot >= cap) {
+    atomicOr(&st->err, AFE_LIST_OVERFLOW);
+    return -1;
+  }
+  return slot;
+}
+
 // ---------------------------------------------------------------------------
 // L0 physics (Sec. 1)
 // ---------------------------------------------------------------------------
@@ -215,6 +231,14 @@ __device__ void scaling_limiter(const double *UH, const double *UL, double gm1, 
   for (int k = 0; k < 8; ++k) out[k] = fma(t2, Us[k], (1.0 - t2) * UL[k]);
 }
 
+// The scaling limiter's result for given theta*, theta** (frozen branch).
+__device__ void scaling_blend(const double *UH, const double *UL, double t1, double t2, double *out) {
+  double Us[8];
+  for (int k = 0; k < 8; ++k) Us[k] = UH[k];
+  Us[0] = fma(t1, UH[0], (1.0 - t1) * UL[0]);
+  for (int k = 0; k < 8; ++k) out[k] = fma(t2, Us[k], (1.0 - t2) * UL[k]);
+}
+
 // ---------------------------------------------------------------------------
 // P1: point data, cell-centre values, dt reduction
 // ---------------------------------------------------------------------------
@@ -235,10 +259,25 @@ __device__ __forceinline__ bool centre_value(const AfDev &d, const AfGrid &g, in
     const double corners = (C(i, j, k) + C(ip, j, k)) + (C(i, jp, k) + C(ip, jp, k));
     uc[k] = fma(2.25, A[k], fma(-0.25, faces, -0.0625 * corners));
   }
-  if (clear_of_floor(uc, g)) return false;
-  double out[8], t1, t2;
-  scaling_limiter(uc, A, g.gm1, out, t1, t2);
-  for (int k = 0; k < 8; ++k) uc[k] = out[k];
+  const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
+  double t1 = 1.0, t2 = 1.0;
+  if (d.frz) {   // frozen branch: the recorded theta*, theta**
+    t1 = d.frz[AFC_C1 * PS + o];
+    t2 = d.frz[AFC_C2 * PS + o];
+    if (!(t1 == 1.0 && t2 == 1.0)) {
+      double out[8];
+      scaling_blend(uc, A, t1, t2, out);
+      for (int k = 0; k < 8; ++k) uc[k] = out[k];
+    }
+  } else if (!clear_of_floor(uc, g)) {
+    double out[8];
+    scaling_limiter(uc, A, g.gm1, out, t1, t2);
+    for (int k = 0; k < 8; ++k) uc[k] = out[k];
+  }
+  if (d.rec) {
+    d.rec[AFC_C1 * PS + o] = t1;
+    d.rec[AFC_C2 * PS + o] = t2;
+  }
   return t1 < 1.0 || t2 < 1.0;
 }
 
@@ -511,11 +550,10 @@ __device__ __forceinline__ void central_line(const PP &lo, const PP &hi, size_t 
   }
 }
 
-// Slow path of Sec. 3.3 for one point value (cls 1, 2, 3 at (i,j)): its
-// first-order LLF state, the scaling limiter and the round-off shrink.
+// First-order LLF state of Sec. 3.3 for one point value (cls 1, 2, 3 at (i,j)).
 template <bool GB>
-__device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, int i, int j, const double *UH,
-                                      double dt, double *out, int &limited, int &shrunk, int &bad) {
+__device__ __noinline__ void point_llf_state(const AfDev &d, const AfGrid &g, int cls, int i, int j, double dt,
+                                             double *UL) {
   // neighbours (class, unmapped index) for the x and y fluxes (left/low, right/high)
   int cx[2], ix[2], jx[2], cy[2], iy[2], jy[2];
   if (cls == 3) {
@@ -553,15 +591,27 @@ __device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, 
   // half a cell apart are still divided by dx or dy; divergence over 2 dx, 2 dy).
   const double divB = (b1r - b1l) * (0.5 * g.rdx) + (b2r - b2l) * (0.5 * g.rdy);
   const double Ps[8] = {0.0, me.B[0], me.B[1], me.B[2], me.v[0], me.v[1], me.v[2], me.vB};
-  double UL[8];
   const double cxf = dt * g.rdx, cyf = dt * g.rdy;
   for (int k = 0; k < 8; ++k) {
     double u = me.U[k] - cxf * (Fxr[k] - Fxl[k]) - cyf * (Fyr[k] - Fyl[k]);
     if (g.src_point_on) u -= dt * divB * Ps[k];
     UL[k] = u;
   }
+}
+
+// Slow path of Sec. 3.3 for one point value: its first-order LLF state, the
+// scaling limiter and the round-off shrink.  t1o, t2o: the theta*, theta** taken
+// (theta** after the shrink; 0 for the fall-back to the LLF state).
+template <bool GB>
+__device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, int i, int j, const double *UH,
+                                      double dt, double *out, int &limited, int &shrunk, int &bad, double &t1o,
+                                      double &t2o) {
+  double UL[8];
+  point_llf_state<GB>(d, g, cls, i, j, dt, UL);
   double t1, t2;
   scaling_limiter(UH, UL, g.gm1, out, t1, t2);
+  t1o = t1;
+  t2o = t2;
   limited = (t1 < 1.0 || t2 < 1.0);
   shrunk = 0;
   bad = 0;
@@ -576,9 +626,12 @@ __device__ __noinline__ void point_pp(const AfDev &d, const AfGrid &g, int cls, 
       const double th = fmax(0.0, t2 - ldexp(1e-8, m));
       for (int k = 0; k < 8; ++k) out[k] = fma(th, Us[k], (1.0 - th) * UL[k]);
       ok = in_G(out, g.gm1);
+      t2o = th;
     }
-    if (!ok)
+    if (!ok) {
       for (int k = 0; k < 8; ++k) out[k] = UL[k];
+      t2o = 0.0;
+    }
     bad = !in_G(out, g.gm1);
   }
 }
@@ -702,14 +755,41 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
         for (int k = 0; k < 8; ++k) uo[k * cs + oo] = acc[k];
         continue;
       }
-      if (g.pp_on && !clear_of_floor(acc, g)) {
-        double out[8];
-        int lim, shr, bad;
-        point_pp<GB>(d, g, cls, i, j, acc, dt, out, lim, shr, bad);
-        nlim += lim;
-        nshr += shr;
-        nbad += bad;
-        for (int k = 0; k < 8; ++k) acc[k] = out[k];
+      if (g.pp_on) {
+        const size_t op = (size_t)j * g.nxa + i, s1 = (size_t)(AFC_P1 + 2 * (cls - 1)) * PS + op;
+        double t1 = 1.0, t2 = 1.0;
+        if (d.frz) {   // frozen branch: the recorded theta*, theta**
+          t1 = d.frz[s1];
+          t2 = d.frz[s1 + PS];
+          if (!(t1 == 1.0 && t2 == 1.0)) {
+            double UL[8], out[8];
+            point_llf_state<GB>(d, g, cls, i, j, dt, UL);
+            scaling_blend(acc, UL, t1, t2, out);
+            nlim += 1;
+            for (int k = 0; k < 8; ++k) acc[k] = out[k];
+          }
+        } else if (!clear_of_floor(acc, g)) {
+          if (d.pq) {   // slow path in k_points_slow, over a dense list (the warp does not wait here)
+            const int slot = enqueue(d.st, &d.st->npq, d.pq_cap);
+            if (slot >= 0) {
+              d.pq[slot] = (cls << 28) | (int)op;
+#pragma unroll
+              for (int k = 0; k < 8; ++k) d.pqu[(size_t)k * d.pq_cap + slot] = acc[k];
+            }
+            continue;
+          }
+          double out[8];
+          int lim, shr, bad;
+          point_pp<GB>(d, g, cls, i, j, acc, dt, out, lim, shr, bad, t1, t2);
+          nlim += lim;
+          nshr += shr;
+          nbad += bad;
+          for (int k = 0; k < 8; ++k) acc[k] = out[k];
+        }
+        if (d.rec) {
+          d.rec[s1] = t1;
+          d.rec[s1 + PS] = t2;
+        }
       }
       if (a == 0.0) {
 #pragma unroll
@@ -827,7 +907,10 @@ __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const i
     // x-face (f = i, row j): cells i-1 | i; Simpson nodes: corners (i,j), (i,j+1), x-face (i,j)
     if (i < g.ex[1] && j < g.ey[1]) {
       const int jp = mface(j + 1, g.ny, g.bc);
-      const double ts = sens ? theta_s<GB>(d, g, 0, i - 1, j, i, j) : 1.0;
+      double ts;
+      if (d.frz && mode == 0) ts = d.frz[AFC_TSX * PS + o];   // frozen branch
+      else ts = sens ? theta_s<GB>(d, g, 0, i - 1, j, i, j) : 1.0;
+      if (d.rec && mode == 0) d.rec[AFC_TSX * PS + o] = ts;
       if constexpr (GB)
         face<0, true>(d, g, d.fx + o, PS, pref(d, g, 3, i, j), pref(d, g, 1, i, j), pref(d, g, 3, i, jp), i - 1, j, i, j,
                       ts, llf, nsens);
@@ -838,7 +921,10 @@ __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const i
     // y-face (i, g = j): cells j-1 | j; Simpson nodes: corners (i,j), (i+1,j), y-face (i,j)
     if (i < g.ex[2] && j < g.ey[2]) {
       const int ip = mface(i + 1, g.nx, g.bc);
-      const double ts = sens ? theta_s<GB>(d, g, 1, i, j - 1, i, j) : 1.0;
+      double ts;
+      if (d.frz && mode == 0) ts = d.frz[AFC_TSY * PS + o];
+      else ts = sens ? theta_s<GB>(d, g, 1, i, j - 1, i, j) : 1.0;
+      if (d.rec && mode == 0) d.rec[AFC_TSY * PS + o] = ts;
       if constexpr (GB)
         face<1, true>(d, g, d.fy + o, PS, pref(d, g, 3, i, j), pref(d, g, 2, i, j), pref(d, g, 3, ip, j), i, j - 1, i, j,
                       ts, llf, nsens);
@@ -952,14 +1038,15 @@ __device__ __forceinline__ bool box_certified(const double *L1, const double *D,
   return (q0 - T >= 1e-12 * scale) && (rho - 1e-13 >= (1e-12 + D[0]) * (1.0 + 1e-10));
 }
 
-// Full Sec. 3.2 steps (1)-(2) for one cell (slow path).
-__device__ __noinline__ void cell_limiter_full(const double *Ullf, const double *dS, double dtts, const double (*H)[8],
-                                               const AfGrid &g, double *L1, double *Lam, int &srclim, NewtonLog &nl) {
+// Sec. 3.2 step (1) for one cell: theta_ij and Lim1, with the floors eps_rho, eps_p.
+__device__ __forceinline__ void cell_source_limit(const double *Ullf, const double *dS, double dtts, const AfGrid &g,
+                                                  double *L1, int &srclim, double &th_out, double &eps_rho,
+                                                  double &eps_p) {
   double Usrc[8];
   for (int k = 0; k < 8; ++k) Usrc[k] = fma(-dtts, dS[k], Ullf[k]);
-  const double eps_rho = fmin(1e-13, Ullf[0]);
+  eps_rho = fmin(1e-13, Ullf[0]);
   const double pllf = pressure(Ullf, g.gm1);
-  const double eps_p = fmin(1e-13, pllf);
+  eps_p = fmin(1e-13, pllf);
   double th = 1.0;
   const double psrc = pressure(Usrc, g.gm1);
   srclim = 0;
@@ -968,7 +1055,31 @@ __device__ __noinline__ void cell_limiter_full(const double *Ullf, const double 
     srclim = 1;
   }
   for (int k = 0; k < 8; ++k) L1[k] = fma(th, Usrc[k] - Ullf[k], Ullf[k]);
+  th_out = th;
+}
+
+// Full Sec. 3.2 steps (1)-(2) for one cell (slow path).
+__device__ __noinline__ void cell_limiter_full(const double *Ullf, const double *dS, double dtts, const double (*H)[8],
+                                               const AfGrid &g, double *L1, double *Lam, int &srclim, NewtonLog &nl,
+                                               double &th_out) {
+  double eps_rho, eps_p;
+  cell_source_limit(Ullf, dS, dtts, g, L1, srclim, th_out, eps_rho, eps_p);
   flux_limiter_box(L1, H, eps_rho, eps_p, g.gm1, Lam, nl);
+}
+
+// The anti-diffusive fluxes H_L, H_R, H_D, H_U of cell (i, j) (Sec. 3.2 step 2)
+// from the stored G = theta^s (F - F^LLF) of its faces.
+__device__ __forceinline__ void cell_H(const AfDev &d, const AfGrid &g, int i, int j, double cxf, double cyf,
+                                       double (*H)[8]) {
+  const WV FX = wview(d.fx, g), FY = wview(d.fy, g);
+  const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    H[0][k] = cxf * FX(i, j, QF_G + k);
+    H[1][k] = -(cxf * FX(ip, j, QF_G + k));
+    H[2][k] = cyf * FY(i, j, QF_G + k);
+    H[3][k] = -(cyf * FY(i, jp, QF_G + k));
+  }
 }
 
 template <bool GB>
@@ -1132,7 +1243,15 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         }
         const double dtts = dt * tsc;
         double L1[8], Lam[4];
-        bool fast = Ullf[0] >= 1e-13 && qform(Ullf, g.c13) >= 0.0;
+        double th_src = 1.0;
+        if (d.frz) {   // frozen branch: Lim1 with the recorded theta_ij; face theta are recorded too
+          th_src = d.frz[AFC_TSRC * PS + o];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) L1[k] = fma(th_src, fma(-dtts, dS[k], Ullf[k]) - Ullf[k], Ullf[k]);
+          Lam[0] = Lam[1] = Lam[2] = Lam[3] = 1.0;
+          nsrc += th_src < 1.0;
+        }
+        bool fast = !d.frz && Ullf[0] >= 1e-13 && qform(Ullf, g.c13) >= 0.0;
         if (fast) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) L1[k] = fma(-dtts, dS[k], Ullf[k]);
@@ -1144,8 +1263,22 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           for (int k = 0; k < 8; ++k) D[k] = fma(cxf, absd(Gf[0][k]) + absd(Gf[1][k]), cyf * (absd(Gf[2][k]) + absd(Gf[3][k])));
           fast = box_certified(L1, D, g);
         }
-        if (fast) {
+        bool listed = false;
+        if (d.frz) {
+        } else if (fast) {
           Lam[0] = Lam[1] = Lam[2] = Lam[3] = 1.0;
+        } else if (d.cq) {   // step (1) here, the box of step (2) in k_cells_slow over a dense list
+          int sl = 0;
+          double eps_rho, eps_p;
+          cell_source_limit(Ullf, dS, dtts, g, L1, sl, th_src, eps_rho, eps_p);
+          nsrc += sl;
+          const int slot = enqueue(d.st, &d.st->ncq, d.cq_cap);
+          if (slot >= 0) {
+            d.cq[slot] = (int)o;
+            d.cqe[2 * slot] = eps_rho;
+            d.cqe[2 * slot + 1] = eps_p;
+          }
+          listed = true;
         } else {
           double H[4][8];
 #pragma unroll
@@ -1156,14 +1289,16 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
             H[3][k] = -(cyf * Gf[3][k]);
           }
           int sl = 0;
-          cell_limiter_full(Ullf, dS, dtts, H, g, L1, Lam, sl, nl);
+          cell_limiter_full(Ullf, dS, dtts, H, g, L1, Lam, sl, nl, th_src);
           nsrc += sl;
           nlam += (Lam[0] < 1.0 || Lam[1] < 1.0 || Lam[2] < 1.0 || Lam[3] < 1.0);
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) d.lim1[k * PS + o] = L1[k];
+        if (!listed)
 #pragma unroll
-        for (int I = 0; I < 4; ++I) d.lam[I * PS + o] = Lam[I];
+          for (int I = 0; I < 4; ++I) d.lam[I * PS + o] = Lam[I];
+        if (d.rec) d.rec[AFC_TSRC * PS + o] = th_src;
       }
     }
   }
@@ -1223,12 +1358,21 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
   if (i < g.nx && j < g.ny) {
     const double dt = d.sc->dt;
     const WV L = wview(d.lam, g);
-    double th[4];
-    th[0] = theta_x(g, L, i, j);
-    th[1] = theta_x(g, L, i + 1, j);
-    th[2] = theta_y(g, L, i, j);
-    th[3] = theta_y(g, L, i, j + 1);
     const size_t o = (size_t)j * g.nxa + i;
+    double th[4];
+    if (d.frz) {   // frozen branch: the recorded face coefficients (after Remark 4.1)
+      const size_t PS = (size_t)g.nxa * g.nya;
+      const int ip = (g.bc == 0) ? wrapi(i + 1, g.nx) : i + 1, jp = (g.bc == 0) ? wrapi(j + 1, g.ny) : j + 1;
+      th[0] = d.frz[AFC_THX * PS + o];
+      th[1] = d.frz[AFC_THX * PS + (size_t)j * g.nxa + ip];
+      th[2] = d.frz[AFC_THY * PS + o];
+      th[3] = d.frz[AFC_THY * PS + (size_t)jp * g.nxa + i];
+    } else {
+      th[0] = theta_x(g, L, i, j);
+      th[1] = theta_x(g, L, i + 1, j);
+      th[2] = theta_y(g, L, i, j);
+      th[3] = theta_y(g, L, i, j + 1);
+    }
     d.thx[o] = th[0];
     d.thy[o] = th[2];
     nface += lt_one(th[0]) + lt_one(th[2]);
@@ -1248,7 +1392,7 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     bool ok = __double_as_longlong(fe[0]) > 0 && __double_as_longlong(q) > 0 && finite_bits(q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) ok = ok && finite_bits(fe[k]);
-    if (!ok) {
+    if (!ok && !d.frz) {
       const int slot = atomicAdd(&d.st->nrepair, 1);
       if (slot < AF_MAX_REPAIR) d.st->repair[slot] = j * g.nx + i;
       else atomicOr(&d.st->err, AFE_REPAIR_OVERFLOW);
@@ -1364,6 +1508,78 @@ __device__ __forceinline__ bool interior_block(int nx, int ny) {
   const int i0 = blockIdx.x * blockDim.x, j0 = blockIdx.y * blockDim.y;
   return i0 >= kFrame && j0 >= kFrame && i0 + (int)blockDim.x + kFrame <= nx && j0 + (int)blockDim.y + kFrame <= ny;
 }
+// ---- limiter slow paths over the work lists (single runs) -------------------
+// Points whose high-order update left the floors: Sec. 3.3 LLF state, scaling
+// limiter and Remark 4.1 shrink, then the RK combination.
+template <bool GB>
+__device__ __forceinline__ void b_points_slow(const AfDev &d, const AfGrid &g, double a, double b) {
+  const int n = min(*(volatile int *)&d.st->npq, d.pq_cap);
+  const double dt = d.sc->dt;
+  const size_t PS = (size_t)g.nxa * g.nya;
+  int nlim = 0, nshr = 0, nbad = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int packed = d.pq[t], cls = packed >> 28, op = packed & ((1 << 28) - 1);
+    const int i = op % g.nxa, j = op / g.nxa;
+    double UH[8], out[8], t1, t2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) UH[k] = d.pqu[(size_t)k * d.pq_cap + t];
+    int lim, shr, bad;
+    point_pp<GB>(d, g, cls, i, j, UH, dt, out, lim, shr, bad, t1, t2);
+    nlim += lim;
+    nshr += shr;
+    nbad += bad;
+    if (d.rec) {
+      const size_t s1 = (size_t)(AFC_P1 + 2 * (cls - 1)) * PS + op;
+      d.rec[s1] = t1;
+      d.rec[s1 + PS] = t2;
+    }
+    double *uo = d.uo[cls];
+    const size_t cs = (size_t)g.ex[cls] * g.ey[cls], oo = (size_t)j * g.ex[cls] + i;
+    if (a == 0.0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) uo[k * cs + oo] = out[k];
+    } else {
+      const double *un = d.un[cls];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) uo[k * cs + oo] = fma(a, __ldg(un + k * cs + oo), b * out[k]);
+    }
+  }
+  if (nlim) atomicAdd(&d.st->cnt[ST_POINT_LIMITED], (unsigned long long)nlim);
+  if (nshr) atomicAdd(&d.st->cnt[ST_SHRINK], (unsigned long long)nshr);
+  if (nbad) {
+    atomicAdd(&d.st->cnt[ST_NONADMISSIBLE], (unsigned long long)nbad);
+    atomicOr(&d.st->err, AFE_NONADMISSIBLE);
+  }
+}
+
+// Cells whose box was not certified: Sec. 3.2 step (2), the rectangle R_rho and
+// its 16 vertices with the Newton solves, on Lim1 and H of the cell: one thread
+// per listed cell.  (A half-warp per cell, one lane per vertex, measured slower:
+// every lane repeats the loads and the rectangle, and the pass is throughput-bound.)
+__device__ __forceinline__ void b_cells_slow(const AfDev &d, const AfGrid &g) {
+  const int n = min(*(volatile int *)&d.st->ncq, d.cq_cap);
+  const double dt = d.sc->dt, cxf = dt * g.rdx, cyf = dt * g.rdy;
+  const size_t PS = (size_t)g.nxa * g.nya;
+  int nlam = 0;
+  NewtonLog nl = {0, 0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int o = d.cq[t], i = o % g.nxa, j = o / g.nxa;
+    double L1[8], H[4][8], Lam[4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) L1[k] = d.lim1[k * PS + o];
+    cell_H(d, g, i, j, cxf, cyf, H);
+    flux_limiter_box(L1, H, d.cqe[2 * t], d.cqe[2 * t + 1], g.gm1, Lam, nl);
+    nlam += (Lam[0] < 1.0 || Lam[1] < 1.0 || Lam[2] < 1.0 || Lam[3] < 1.0);
+#pragma unroll
+    for (int I = 0; I < 4; ++I) d.lam[I * PS + o] = Lam[I];
+  }
+  if (nlam) atomicAdd(&d.st->cnt[ST_LAMBDA_LT1], (unsigned long long)nlam);
+  if (nl.solves) {
+    atomicAdd(&d.st->cnt[ST_NEWTON_SOLVES], (unsigned long long)nl.solves);
+    atomicMax(&d.st->cnt[ST_NEWTON_MAXIT], (unsigned long long)nl.maxit);
+  }
+}
+
 #define AF_BATCH_LOOP(call)                                       \
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {       \
     const int4 w = items[it];                                     \
@@ -1374,6 +1590,11 @@ __device__ __forceinline__ bool interior_block(int nx, int ny) {
 
 __global__ void __launch_bounds__(128) k_pointdata(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                    int reduce_dt) {
+  // a stage's first pass: the work lists of its point and cell passes start empty
+  if (d.pq && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+    d.st->npq = 0;
+    d.st->ncq = 0;
+  }
   b_pointdata(d, g, AF_IJ, reduce_dt);
 }
 __global__ void __launch_bounds__(256) kb_pointdata(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
@@ -1429,6 +1650,14 @@ __global__ void __launch_bounds__(128) k_final(const __grid_constant__ AfDev d, 
 __global__ void __launch_bounds__(256) kb_final(const AfRun *__restrict__ runs, const int4 *__restrict__ items,
                                                 int nitems, double a, double b) {
   AF_BATCH_LOOP(if (r->g.pp_on) b_final(r->d, r->g, i, j, a, b));
+}
+template <bool GB>
+__global__ void __launch_bounds__(128) k_points_slow(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+                                                     double a, double b) {
+  b_points_slow<GB>(d, g, a, b);
+}
+__global__ void __launch_bounds__(128) k_cells_slow(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
+  b_cells_slow(d, g);
 }
 __global__ void k_repair(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g, double a, double b) {
   if (threadIdx.x == 0 && blockIdx.x == 0) b_repair(d, g, a, b);
@@ -1661,6 +1890,16 @@ void af_launch_cells(const AfDev &d, const AfGrid &g, double a, double b, int mo
 }
 void af_launch_final(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
   k_final<<<grid2(g.nx, g.ny), dim3(32, 4), 0, s>>>(d, g, a, b);
+}
+// a fixed grid of 4 blocks per SM walks the list
+void af_launch_points_slow(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
+  if (!d.pq) return;
+  if (g.special) k_points_slow<true><<<152 * 4, 128, 0, s>>>(d, g, a, b);
+  else k_points_slow<false><<<152 * 4, 128, 0, s>>>(d, g, a, b);
+}
+void af_launch_cells_slow(const AfDev &d, const AfGrid &g, cudaStream_t s) {
+  if (!d.cq) return;
+  k_cells_slow<<<152 * 4, 128, 0, s>>>(d, g);
 }
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
   k_repair<<<1, 32, 0, s>>>(d, g, a, b);
