@@ -595,8 +595,17 @@ def limiter_cost(s, pb, stream, cnt, steps, reps=6):
     stage_on = sum(v for k, v in on.items() if k not in ("k_dt",))
     stage_off = sum(v for k, v in off.items() if k not in ("k_dt",))
     out["limiter_share_of_stage"] = (stage_on - stage_off) / stage_on
+    # the cell limiter: k_cells and its list passes (box, Newton, count), over the cells
+    # with some Lambda_I < 1; the point limiter: k_points and its list pass, over the
+    # points the scaling limiter changed
+    cell_extra = on.get("k_cells", 0.0) + on.get("k_cells_slow", 0.0) - off.get("k_cells", 0.0)
+    point_extra = on.get("k_points", 0.0) + on.get("k_points_slow", 0.0) - off.get("k_points", 0.0)
+    out["cell_limiter_ms_per_stage"] = cell_extra
+    out["point_limiter_ms_per_stage"] = point_extra
     if lam_cells > 0:
-        out["k_cells_extra_ns_per_limited_cell"] = (on["k_cells"] - off["k_cells"]) * 1e6 / lam_cells
+        out["cell_limiter_ns_per_cell_lambda_lt1"] = cell_extra * 1e6 / lam_cells
+    if out["points_limited_per_stage"] > 0:
+        out["point_limiter_ns_per_limited_point"] = point_extra * 1e6 / out["points_limited_per_stage"]
     return out
 
 

@@ -243,7 +243,9 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   const size_t PS = (size_t)c->g.nxa * c->g.nya;
   // stage work arrays, then the limiter work lists: points (3 PS entries: an int and 8
   // doubles each), cells (PS entries: an int and 2 doubles each)
-  const size_t nwork = PS * (AF_NQA + 4 * AF_NQP + 8 + 4 + 2 * AF_NQF + 4 + 8 + 2) + PS * (24 + 2) + 2 * PS + 1;
+  // and the vertex list (16 PS entries, an unsigned each) with Lambda^rho of the listed cells (4 PS)
+  const size_t nwork = PS * (AF_NQA + 4 * AF_NQP + 8 + 4 + 2 * AF_NQF + 4 + 8 + 2) + PS * (24 + 2) + 2 * PS + 1 +
+                       PS * (8 + 4);
   int rc = AF_OK;
   for (int b = 0; b < 3; ++b) {
     if (cudaMalloc(&c->state[b], off * sizeof(double)) != cudaSuccess) rc = AF_ENOMEM;
@@ -278,6 +280,9 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   c->dev.cqe = w; w += 2 * PS;
   c->dev.pq = reinterpret_cast<int *>(w); w += (3 * PS + 1) / 2;
   c->dev.cq = reinterpret_cast<int *>(w); w += (PS + 1) / 2;
+  c->dev.cql = w; w += 4 * PS;
+  c->dev.vq_cap = (int)(16 * PS);
+  c->dev.vq = reinterpret_cast<unsigned *>(w); w += 8 * PS;
   c->dev.sc = c->sc;
   c->dev.st = c->st;
   c->cur = 0;

@@ -75,6 +75,7 @@ struct AfStatus {
   int nrepair;
   int repair[AF_MAX_REPAIR];
   int npq, ncq;   // entries of the point and cell work lists of the current stage
+  int nvq;        // entries of the vertex list (vertices of listed cells that need the Newton solve)
 };
 
 struct AfDev {
@@ -99,6 +100,11 @@ struct AfDev {
   int *pq, *cq;
   double *pqu, *cqe;
   int pq_cap, cq_cap;
+  // vertices of R_rho (listed cell << 4 | vertex) whose pressure falls below eps_p, and
+  // Lambda^rho of each listed cell
+  unsigned *vq;
+  double *cql;
+  int vq_cap;
 };
 
 // one member of a batch (af_batch.cu): its work pointers and grid

@@ -1552,32 +1552,98 @@ __device__ __forceinline__ void b_points_slow(const AfDev &d, const AfGrid &g, d
   }
 }
 
-// Cells whose box was not certified: Sec. 3.2 step (2), the rectangle R_rho and
-// its 16 vertices with the Newton solves, on Lim1 and H of the cell: one thread
-// per listed cell.  (A half-warp per cell, one lane per vertex, measured slower:
-// every lane repeats the loads and the rectangle, and the pass is throughput-bound.)
-__device__ __forceinline__ void b_cells_slow(const AfDev &d, const AfGrid &g) {
+// Cells whose box was not certified: Sec. 3.2 step (2) in three dense passes.
+// A (one thread per listed cell): the rectangle R_rho; Lambda starts at Lambda^rho;
+// the vertices A^k that leave S_p go to the vertex list.  B (one thread per listed
+// vertex): the Newton solve for r, then Lambda_I = min(Lambda_I, r A_I) for the I
+// with k_I = 1, by an atomic minimum on the bit patterns (Lambda >= 0, for which the
+// integer order is the numeric order): exact and order-free, so Lambda equals the
+// one-thread box of Sec. 3.2 bit for bit.  C: the count of cells with Lambda < 1.
+// (A half-warp per cell, one lane per vertex, was measured slower than one thread
+// per cell: every lane repeats the loads and the rectangle.)
+__device__ __forceinline__ void rect_rho(const double *L1, const double (*H)[8], double eps_rho, double *LamRho) {
+  double negsum = 0.0;
+  for (int J = 0; J < 4; ++J)
+    if (H[J][0] < 0.0) negsum = negsum + H[J][0];
+  for (int I = 0; I < 4; ++I) {
+    LamRho[I] = 1.0;
+    if (H[I][0] < 0.0) LamRho[I] = fmin(1.0, (L1[0] - eps_rho) / (1e-12 - negsum));
+  }
+}
+// vertex k of R_rho: A (components Lambda^rho_I for k_I = 1, else 0) and D = sum_I A_I H_I
+__device__ __forceinline__ void box_vertex(int kk, const double *LamRho, const double (*H)[8], double *A, double *D) {
+  for (int I = 0; I < 4; ++I) A[I] = ((kk >> I) & 1) ? LamRho[I] : 0.0;
+  for (int k = 0; k < 8; ++k) {
+    double sum = 0.0;
+    for (int I = 0; I < 4; ++I) sum = fma(A[I], H[I][k], sum);
+    D[k] = sum;
+  }
+}
+
+__device__ __forceinline__ void b_cells_box(const AfDev &d, const AfGrid &g) {
   const int n = min(*(volatile int *)&d.st->ncq, d.cq_cap);
   const double dt = d.sc->dt, cxf = dt * g.rdx, cyf = dt * g.rdy;
   const size_t PS = (size_t)g.nxa * g.nya;
-  int nlam = 0;
-  NewtonLog nl = {0, 0};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const int o = d.cq[t], i = o % g.nxa, j = o / g.nxa;
-    double L1[8], H[4][8], Lam[4];
+    double L1[8], H[4][8], LamRho[4];
 #pragma unroll
     for (int k = 0; k < 8; ++k) L1[k] = d.lim1[k * PS + o];
     cell_H(d, g, i, j, cxf, cyf, H);
-    flux_limiter_box(L1, H, d.cqe[2 * t], d.cqe[2 * t + 1], g.gm1, Lam, nl);
-    nlam += (Lam[0] < 1.0 || Lam[1] < 1.0 || Lam[2] < 1.0 || Lam[3] < 1.0);
-#pragma unroll
-    for (int I = 0; I < 4; ++I) d.lam[I * PS + o] = Lam[I];
+    rect_rho(L1, H, d.cqe[2 * t], LamRho);
+    const double eps_p = d.cqe[2 * t + 1];
+    for (int I = 0; I < 4; ++I) {
+      d.cql[4 * (size_t)t + I] = LamRho[I];
+      d.lam[I * PS + o] = LamRho[I];
+    }
+    for (int kk = 0; kk < 16; ++kk) {
+      double A[4], D[8], V[8];
+      box_vertex(kk, LamRho, H, A, D);
+      for (int k = 0; k < 8; ++k) V[k] = L1[k] + D[k];
+      if (pressure(V, g.gm1) < eps_p) {
+        const int slot = enqueue(d.st, &d.st->nvq, d.vq_cap);
+        if (slot >= 0) d.vq[slot] = ((unsigned)t << 4) | (unsigned)kk;
+      }
+    }
   }
-  if (nlam) atomicAdd(&d.st->cnt[ST_LAMBDA_LT1], (unsigned long long)nlam);
+}
+
+__device__ __forceinline__ void b_cells_newton(const AfDev &d, const AfGrid &g) {
+  const int n = min(*(volatile int *)&d.st->nvq, d.vq_cap);
+  const double dt = d.sc->dt, cxf = dt * g.rdx, cyf = dt * g.rdy;
+  const size_t PS = (size_t)g.nxa * g.nya;
+  NewtonLog nl = {0, 0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const unsigned packed = d.vq[e];
+    const int t = (int)(packed >> 4), kk = (int)(packed & 15u);
+    const int o = d.cq[t], i = o % g.nxa, j = o / g.nxa;
+    double L1[8], H[4][8], LamRho[4], A[4], D[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) L1[k] = d.lim1[k * PS + o];
+    cell_H(d, g, i, j, cxf, cyf, H);
+    for (int I = 0; I < 4; ++I) LamRho[I] = d.cql[4 * (size_t)t + I];
+    box_vertex(kk, LamRho, H, A, D);
+    const double r = newton_root(L1, D, d.cqe[2 * t + 1], g.gm1, nl);
+    for (int I = 0; I < 4; ++I)
+      if ((kk >> I) & 1)
+        atomicMin(reinterpret_cast<unsigned long long *>(d.lam + I * PS + o),
+                  (unsigned long long)__double_as_longlong(r * A[I]));
+  }
   if (nl.solves) {
     atomicAdd(&d.st->cnt[ST_NEWTON_SOLVES], (unsigned long long)nl.solves);
     atomicMax(&d.st->cnt[ST_NEWTON_MAXIT], (unsigned long long)nl.maxit);
   }
+}
+
+__device__ __forceinline__ void b_cells_count(const AfDev &d, const AfGrid &g) {
+  const int n = min(*(volatile int *)&d.st->ncq, d.cq_cap);
+  const size_t PS = (size_t)g.nxa * g.nya;
+  int nlam = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int o = d.cq[t];
+    nlam += (d.lam[o] < 1.0 || d.lam[PS + o] < 1.0 || d.lam[2 * PS + o] < 1.0 || d.lam[3 * PS + o] < 1.0);
+  }
+  if (nlam) atomicAdd(&d.st->cnt[ST_LAMBDA_LT1], (unsigned long long)nlam);
 }
 
 #define AF_BATCH_LOOP(call)                                       \
@@ -1594,6 +1660,7 @@ __global__ void __launch_bounds__(128) k_pointdata(const __grid_constant__ AfDev
   if (d.pq && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
     d.st->npq = 0;
     d.st->ncq = 0;
+    d.st->nvq = 0;
   }
   b_pointdata(d, g, AF_IJ, reduce_dt);
 }
@@ -1656,8 +1723,14 @@ __global__ void __launch_bounds__(128) k_points_slow(const __grid_constant__ AfD
                                                      double a, double b) {
   b_points_slow<GB>(d, g, a, b);
 }
-__global__ void __launch_bounds__(128) k_cells_slow(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
-  b_cells_slow(d, g);
+__global__ void __launch_bounds__(128) k_cells_box(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
+  b_cells_box(d, g);
+}
+__global__ void __launch_bounds__(128) k_cells_newton(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
+  b_cells_newton(d, g);
+}
+__global__ void __launch_bounds__(128) k_cells_count(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
+  b_cells_count(d, g);
 }
 __global__ void k_repair(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g, double a, double b) {
   if (threadIdx.x == 0 && blockIdx.x == 0) b_repair(d, g, a, b);
@@ -1899,7 +1972,9 @@ void af_launch_points_slow(const AfDev &d, const AfGrid &g, double a, double b, 
 }
 void af_launch_cells_slow(const AfDev &d, const AfGrid &g, cudaStream_t s) {
   if (!d.cq) return;
-  k_cells_slow<<<152 * 4, 128, 0, s>>>(d, g);
+  k_cells_box<<<152 * 4, 128, 0, s>>>(d, g);
+  k_cells_newton<<<152 * 4, 128, 0, s>>>(d, g);
+  k_cells_count<<<152 * 2, 128, 0, s>>>(d, g);
 }
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
   k_repair<<<1, 32, 0, s>>>(d, g, a, b);
