@@ -86,43 +86,51 @@ ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
 # capture it comes from and a digest of the kernel sources it was taken on: once the
 # kernels change, the line says so ("counts_stale") until the capture is retaken.
 EXEC_FP64 = {
-    "blast_low_beta": {"source": "profiles/fp64ops_blast1024.md", "kernels": {
-        "k_pointdata": {"dadd": 88.03, "dmul": 142.11, "dfma": 237.18, "pipe": 479.33, "dram_bytes": 1167.5},
-        "k_points": {"dadd": 155.35, "dmul": 51.32, "dfma": 249.92, "pipe": 467.64, "dram_bytes": 1375.8},
-        "k_faces": {"dadd": 60.10, "dmul": 50.03, "dfma": 68.42, "pipe": 191.55, "dram_bytes": 744.6},
-        "k_cells": {"dadd": 67.04, "dmul": 58.04, "dfma": 165.20, "pipe": 297.28, "dram_bytes": 716.7},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 329.3},
+    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "kernels": {
+        "k_pointdata": {"dadd": 88.03, "dmul": 142.11, "dfma": 237.18, "pipe": 481.33, "dram_bytes": 1147.6},
+        "k_points": {"dadd": 155.20, "dmul": 51.08, "dfma": 249.44, "pipe": 466.75, "dram_bytes": 1352.8},
+        "k_points_slow": {"dadd": 0.15, "dmul": 0.24, "dfma": 0.48, "pipe": 0.90, "dram_bytes": 1.9},
+        "k_faces": {"dadd": 60.10, "dmul": 50.03, "dfma": 68.42, "pipe": 191.55, "dram_bytes": 744.7},
+        "k_cells": {"dadd": 67.00, "dmul": 58.00, "dfma": 165.01, "pipe": 297.01, "dram_bytes": 714.7},
+        "k_cells_slow": {"dadd": 0.04, "dmul": 0.03, "dfma": 0.18, "pipe": 0.25, "dram_bytes": 0.8},
+        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 329.4},
     }},
-    "orszag_tang": {"source": "profiles/fp64ops_ot512_jets512_lattice512_blast1d.md", "kernels": {
-        "k_pointdata": {"dadd": 88.00, "dmul": 142.00, "dfma": 237.00, "pipe": 479.00, "dram_bytes": 988.7},
-        "k_points": {"dadd": 155.00, "dmul": 53.00, "dfma": 259.00, "pipe": 479.00, "dram_bytes": 1280.2},
-        "k_faces": {"dadd": 60.00, "dmul": 46.00, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 635.1},
-        "k_cells": {"dadd": 67.00, "dmul": 58.00, "dfma": 165.00, "pipe": 297.00, "dram_bytes": 679.8},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 277.7},
+    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "kernels": {
+        "k_pointdata": {"dadd": 88.00, "dmul": 142.00, "dfma": 237.00, "pipe": 481.00, "dram_bytes": 970.3},
+        "k_points": {"dadd": 155.00, "dmul": 53.00, "dfma": 259.00, "pipe": 479.00, "dram_bytes": 1296.4},
+        "k_points_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2},
+        "k_faces": {"dadd": 60.00, "dmul": 46.00, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 635.0},
+        "k_cells": {"dadd": 67.00, "dmul": 58.00, "dfma": 165.00, "pipe": 297.00, "dram_bytes": 681.5},
+        "k_cells_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2},
+        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 277.6},
     }},
-    "jets": {"source": "profiles/fp64ops_ot512_jets512_lattice512_blast1d.md", "kernels": {
-        "k_pointdata": {"dadd": 88.04, "dmul": 142.14, "dfma": 237.22, "pipe": 479.40, "dram_bytes": 1144.9},
-        "k_points": {"dadd": 189.46, "dmul": 51.11, "dfma": 249.50, "pipe": 501.09, "dram_bytes": 1408.5},
-        "k_faces": {"dadd": 69.11, "dmul": 50.10, "dfma": 68.17, "pipe": 200.48, "dram_bytes": 722.0},
-        "k_cells": {"dadd": 67.54, "dmul": 58.02, "dfma": 165.10, "pipe": 297.66, "dram_bytes": 711.5},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 321.8},
+    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "kernels": {
+        "k_pointdata": {"dadd": 88.04, "dmul": 142.14, "dfma": 237.22, "pipe": 481.40, "dram_bytes": 1125.0},
+        "k_points": {"dadd": 189.44, "dmul": 51.08, "dfma": 249.44, "pipe": 500.98, "dram_bytes": 1431.4},
+        "k_points_slow": {"dadd": 0.02, "dmul": 0.03, "dfma": 0.06, "pipe": 0.11, "dram_bytes": 0.2},
+        "k_faces": {"dadd": 69.11, "dmul": 50.10, "dfma": 68.17, "pipe": 200.48, "dram_bytes": 722.1},
+        "k_cells": {"dadd": 67.52, "dmul": 58.00, "dfma": 165.01, "pipe": 297.53, "dram_bytes": 714.0},
+        "k_cells_slow": {"dadd": 0.02, "dmul": 0.01, "dfma": 0.09, "pipe": 0.13, "dram_bytes": 0.1},
+        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 322.1},
     }},
-    "rarefaction_lattice": {"source": "profiles/fp64ops_ot512_jets512_lattice512_blast1d.md", "kernels": {
-        "k_pointdata": {"dadd": 88.50, "dmul": 144.24, "dfma": 241.10, "pipe": 486.55, "dram_bytes": 982.1},
-        "k_points": {"dadd": 208.51, "dmul": 138.61, "dfma": 429.80, "pipe": 800.01, "dram_bytes": 4283.7},
-        "k_faces": {"dadd": 60.00, "dmul": 46.01, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 635.1},
-        "k_cells": {"dadd": 110.68, "dmul": 105.91, "dfma": 395.87, "pipe": 643.77, "dram_bytes": 792.8},
-        "k_final": {"dadd": 13.14, "dmul": 13.19, "dfma": 31.19, "pipe": 58.51, "dram_bytes": 277.8},
+    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "kernels": {
+        "k_pointdata": {"dadd": 88.50, "dmul": 144.24, "dfma": 241.10, "pipe": 488.30, "dram_bytes": 963.3},
+        "k_points": {"dadd": 155.00, "dmul": 50.81, "dfma": 256.81, "pipe": 474.15, "dram_bytes": 1352.0},
+        "k_points_slow": {"dadd": 53.51, "dmul": 87.80, "dfma": 172.99, "pipe": 325.86, "dram_bytes": 516.6},
+        "k_faces": {"dadd": 60.00, "dmul": 46.01, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 635.0},
+        "k_cells": {"dadd": 68.36, "dmul": 59.59, "dfma": 173.16, "pipe": 308.52, "dram_bytes": 685.3},
+        "k_cells_slow": {"dadd": 44.31, "dmul": 58.33, "dfma": 240.91, "pipe": 359.01, "dram_bytes": 352.8},
+        "k_final": {"dadd": 13.14, "dmul": 13.19, "dfma": 31.19, "pipe": 58.51, "dram_bytes": 277.1},
     }},
-    "blast1d": {"source": "profiles/fp64ops_ot512_jets512_lattice512_blast1d.md", "kernels": {
-        "k1_pointdata": {"dadd": 29.00, "dmul": 90.00, "dfma": 147.00, "pipe": 274.00, "dram_bytes": 688.2},
-        "k1_points": {"dadd": 41.00, "dmul": 18.33, "dfma": 68.33, "pipe": 132.67, "dram_bytes": 430.8},
+    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "kernels": {
+        "k1_pointdata": {"dadd": 29.00, "dmul": 90.00, "dfma": 147.00, "pipe": 274.00, "dram_bytes": 688.4},
+        "k1_points": {"dadd": 41.00, "dmul": 18.33, "dfma": 68.33, "pipe": 132.67, "dram_bytes": 430.9},
         "k1_faces": {"dadd": 29.00, "dmul": 24.00, "dfma": 21.00, "pipe": 80.00, "dram_bytes": 359.2},
-        "k1_cells": {"dadd": 22.00, "dmul": 31.00, "dfma": 34.00, "pipe": 92.00, "dram_bytes": 290.4},
+        "k1_cells": {"dadd": 22.00, "dmul": 31.00, "dfma": 34.00, "pipe": 92.00, "dram_bytes": 290.5},
         "k1_final": {"dadd": 0.00, "dmul": 17.33, "dfma": 28.33, "pipe": 48.67, "dram_bytes": 252.6},
     }},
 }
-EXEC_FP64_DIGEST = "b361fdf6777a1315868cd974e277b8db9fa1b03d"
+EXEC_FP64_DIGEST = "21d09576e9d47c842ec7de77889eef45ca97bd19"
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
@@ -650,6 +658,47 @@ def adjoint_cost(stream, nsteps=200, every=20):
                                "includes": "as above + U3 kept + the mu dt reduction and the argmax gradient"}}
 
 
+def adjoint_limited_cost(stream, nsteps=40, every=20):
+    """The same ratio on a limited run: the low-beta blast 256x256 (kappa = 1; the point,
+    centre and flux limiters act at the front), 40 steps, checkpoints every 20.  The
+    backward pass records every step's limiter coefficients while it recomputes a segment
+    and applies af_adjoint_step_frozen (the gradient along the branch the forward pass took)."""
+    import torch
+    import paper_2506_04857_gb300 as af
+    from paper_2506_04857_gb300.adjoint import af_steps, magnetic_energy
+    pb = ai.blast(256)
+    s = af.Solver(pb.nx, pb.ny, pb.gamma, pb.bc, domain=(pb.x0, pb.x1, pb.y0, pb.y1), cfl=pb.cfl, kappa=pb.kappa,
+                  stream=stream)
+    U0 = [torch.from_numpy(u).cuda() for u in ai.dofs(pb)]
+
+    def once(n):
+        X0 = [t.clone().requires_grad_(True) for t in U0]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        out = af_steps(s, X0, n, checkpoint_every=every)
+        ev[1].record(stream)
+        J = magnetic_energy(out, pb.dx, pb.dy, pb.bc)
+        ev[2].record(stream)
+        J.backward()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])
+
+    once(every)   # warm-up
+    s.status(reset=True)
+    fwd, bwd = once(nsteps)
+    rc, cnt = s.status(reset=True)
+    s.close()
+    return {"workload": "256x256 low-beta blast, kappa=1, %d steps, checkpoints every %d steps, objective total "
+                        "magnetic energy, limiters active" % (nsteps, every),
+            "forward_ms": fwd, "backward_ms": bwd, "forward_ms_per_step": fwd / nsteps,
+            "adjoint_ms_per_step": bwd / nsteps, "ratio": bwd / fwd,
+            "includes": "segment recompute recording the limiter coefficients + point data of 3 stage states + "
+                        "3 frozen-branch VJPs",
+            "limiter_counters_forward_and_recompute": cnt}
+
+
 def adjoint_bench(args, desc):
     """The adjoint workload alone: its backward / forward wall-time ratio."""
     import torch
@@ -982,6 +1031,7 @@ def main():
             line["limiter_cost"] = limiter
         if not args.no_adjoint and world == 1:
             line["adjoint"] = adjoint_cost(stream)
+            line["adjoint_limited"] = adjoint_limited_cost(stream)
         if not args.no_ensemble and world == 1 and key == "blast2048":
             s.close()
             line["ensemble"] = ensemble_cost(torch.cuda.Stream())   # graph capture needs a non-default stream

@@ -9,9 +9,13 @@ af_adjoint_step_stages in reverse, so gradients are those of
 the discrete scheme with dt held fixed, or, with dt_sensitivity=True, with
 every step's dt differentiated as the function of its state that af_step
 forms (dt = cfl / (max varrho_1/dx + max varrho_2/dy), a subgradient at the
-maximising DoFs).  The transpose is that of the smooth
-branch: shock sensor off (kappa = 0) and every positivity limiter inactive;
-backward raises when the forward pass left that branch.
+maximising DoFs).  When every positivity limiter stayed inactive and the
+shock sensor is off (kappa = 0), the transpose is that of the smooth branch.
+Otherwise the backward pass records, while it recomputes a segment (bitwise
+the forward steps), every stage's limiter coefficients (af_record_coeffs) and
+applies af_adjoint_step_frozen: the gradient along the branch the forward pass
+took, with theta^s, theta_ij, the face theta and the scaling-limiter theta*,
+theta** held at their recorded values.
 
 magnetic_energy is the objective of the adjoint workload: the total magnetic
 energy dx dy sum_cells sum_{l,m} w_l w_m |B(U^{l,m})|^2 / 2 on the 3x3 Simpson
@@ -23,8 +27,9 @@ from typing import List
 
 import torch
 
-from . import (AF_BC_PERIODIC, AF_OK, AFError, Solver, af_adjoint_step_stages, af_get_stage, af_get_state,
-               af_last_error, af_set_state, af_stage, af_status, af_step)
+from . import (AF_BC_PERIODIC, AF_OK, AFError, Solver, af_adjoint_step_frozen, af_adjoint_step_stages,
+               af_coeff_len, af_get_params, af_get_stage, af_get_state, af_last_error, af_record_coeffs,
+               af_set_state, af_stage, af_status, af_step)
 
 # counters of the positivity limiters (and of non-admissible states)
 LIMITER_COUNTERS = ("src_limited", "lambda_lt1", "face_theta_lt1", "shrink", "point_limited", "center_limited",
@@ -88,16 +93,15 @@ class AFSteps(torch.autograd.Function):
         out = af_get_state(solver.ctx)
         after = _counters(solver)
         ctx.inactive = all(after[k] == before[k] for k in LIMITER_COUNTERS)
+        ctx.smooth = ctx.inactive and af_get_params(solver.ctx)["kappa"] == 0.0
         ctx.dts = dts
         ctx.checkpoints = checkpoints
         return tuple(out)
 
     @staticmethod
     def backward(ctx, *grads):
-        if not ctx.inactive:
-            raise RuntimeError("a positivity limiter acted in the forward pass: the discrete adjoint covers the "
-                               "branch on which every limiter is inactive")
         s = ctx.solver
+        L = af_coeff_len(s.ctx)
         lam = [g.contiguous() if g is not None else torch.zeros_like(t)
                for g, t in zip(grads, ctx.checkpoints[0] if ctx.checkpoints else grads)]
         for seg in reversed(range(len(ctx.checkpoints))):
@@ -108,18 +112,28 @@ class AFSteps(torch.autograd.Function):
             for n in range(n0, n1):
                 Un = af_get_state(s.ctx)
                 dt = ctx.dts[n:n + 1]
+                co = None
+                if not ctx.smooth:   # the limited branch: this step's limiter coefficients
+                    co = torch.empty(3 * L, dtype=torch.float64, device=Un[0].device)
+                    af_record_coeffs(s.ctx, co)
                 af_stage(s.ctx, 0, dt)
                 U1 = af_get_stage(s.ctx)
                 af_stage(s.ctx, 1, dt)
                 U2 = af_get_stage(s.ctx)
                 af_stage(s.ctx, 2, dt)
                 U3 = af_get_stage(s.ctx) if ctx.dt_sensitivity else None
-                states.append((Un, U1, U2, U3))
+                if co is not None:
+                    af_record_coeffs(s.ctx, None)
+                states.append((Un, U1, U2, U3, co))
             for n in reversed(range(n0, n1)):
-                Un, U1, U2, U3 = states[n - n0]
+                Un, U1, U2, U3, co = states[n - n0]
                 af_set_state(s.ctx, Un)
-                lam = af_adjoint_step_stages(s.ctx, ctx.dts[n:n + 1], U1, U2, lam, U3=U3,
-                                             dt_sensitivity=ctx.dt_sensitivity)
+                if co is None:
+                    lam = af_adjoint_step_stages(s.ctx, ctx.dts[n:n + 1], U1, U2, lam, U3=U3,
+                                                 dt_sensitivity=ctx.dt_sensitivity)
+                else:
+                    lam = af_adjoint_step_frozen(s.ctx, ctx.dts[n:n + 1], U1, U2, co, lam, U3=U3,
+                                                 dt_sensitivity=ctx.dt_sensitivity)
         return (None, None, None, None) + tuple(lam)
 
 

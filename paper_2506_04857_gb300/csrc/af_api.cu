@@ -52,6 +52,9 @@ struct af_ctx {
   double *rec_buf;
   const double *frz_buf;
   double *vscale;
+  // the point work list runs on a second stream beside the face and cell passes
+  cudaStream_t lstream;
+  cudaEvent_t ev_fork, ev_join;
   char msg[512];
 };
 
@@ -149,26 +152,37 @@ void bind_ptrs(af_ctx *c, const double *n, const double *st, double *o) {
   }
 }
 
-#define TIMED(kernel, call)                      \
-  do {                                           \
-    bool on_ = c->tm.begin((kernel), c->stream); \
-    call;                                        \
-    c->tm.end(on_, c->stream);                   \
+#define TIMED_ON(strm, kernel, call)       \
+  do {                                     \
+    bool on_ = c->tm.begin((kernel), strm); \
+    call;                                  \
+    c->tm.end(on_, strm);                  \
   } while (0)
+#define TIMED(kernel, call) TIMED_ON(c->stream, kernel, call)
 
 // One stage: P1..P5 on the bound buffers.
 void run_stage(af_ctx *c, double a, double b, int reduce_dt) {
   TIMED(AF_K_POINTDATA, af_launch_pointdata(c->dev, c->g, reduce_dt, c->stream));
   if (reduce_dt) TIMED(AF_K_DT, af_launch_dt(c->dev, c->g, c->stream));
   TIMED(AF_K_POINTS, af_launch_points(c->dev, c->g, a, b, 0, c->stream));
-  if (c->g.pp_on && !c->dev.frz) TIMED(AF_K_POINTS_SLOW, af_launch_points_slow(c->dev, c->g, a, b, c->stream));
+  const bool lists = c->g.pp_on && !c->dev.frz;
+  if (lists) {
+    // the point list: only the next stage reads what it writes, so it runs on the
+    // second stream beside the face and cell passes and joins at the end of the stage
+    // (a short list would otherwise cost the latency of one thread's slow path)
+    cudaEventRecord(c->ev_fork, c->stream);
+    cudaStreamWaitEvent(c->lstream, c->ev_fork, 0);
+    TIMED_ON(c->lstream, AF_K_POINTS_SLOW, af_launch_points_slow(c->dev, c->g, a, b, c->lstream));
+    cudaEventRecord(c->ev_join, c->lstream);
+  }
   TIMED(AF_K_FACES, af_launch_faces(c->dev, c->g, 0, c->stream));
   TIMED(AF_K_CELLS, af_launch_cells(c->dev, c->g, a, b, 0, c->stream));
-  if (c->g.pp_on && !c->dev.frz) TIMED(AF_K_CELLS_SLOW, af_launch_cells_slow(c->dev, c->g, c->stream));
+  if (lists) TIMED(AF_K_CELLS_SLOW, af_launch_cells_slow(c->dev, c->g, c->stream));
   if (c->g.pp_on) {
     TIMED(AF_K_FINAL, af_launch_final(c->dev, c->g, a, b, c->stream));
     TIMED(AF_K_REPAIR, af_launch_repair(c->dev, c->g, a, b, c->stream));
   }
+  if (lists) cudaStreamWaitEvent(c->stream, c->ev_join, 0);
 }
 
 const double RK_A[3] = {0.0, 3.0 / 4.0, 1.0 / 3.0};
@@ -257,6 +271,9 @@ int af_create(int nx, int ny, double gamma, int bc, af_ctx **out) {
   if (!rc && cudaMalloc(&c->st, sizeof(AfStatus)) != cudaSuccess) rc = AF_ENOMEM;
   if (!rc && cudaMemset(c->sc, 0, sizeof(AfScalars)) != cudaSuccess) rc = AF_ECUDA;
   if (!rc && cudaMemset(c->st, 0, sizeof(AfStatus)) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaStreamCreateWithFlags(&c->lstream, cudaStreamNonBlocking) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess) rc = AF_ECUDA;
+  if (!rc && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) rc = AF_ECUDA;
   if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = AF_ECUDA;
   if (rc) {
     cudaGetLastError();
@@ -1095,6 +1112,12 @@ void af_destroy(af_ctx *c) {
   }
   if (c->h2d) cudaStreamDestroy(c->h2d);
   if (c->d2h) cudaStreamDestroy(c->d2h);
+  if (c->lstream) {
+    cudaStreamSynchronize(c->lstream);
+    cudaStreamDestroy(c->lstream);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   c->tm.destroy();
   delete c;
 }

@@ -1354,11 +1354,15 @@ __device__ __forceinline__ void limited_value(const AfDev &d, const AfGrid &g, i
 }
 
 __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const int i, const int j, double a, double b) {
-  int nface = 0;
+  int nface = 0, nlam = 0;
   if (i < g.nx && j < g.ny) {
     const double dt = d.sc->dt;
     const WV L = wview(d.lam, g);
     const size_t o = (size_t)j * g.nxa + i;
+    // with the work lists the box of Sec. 3.2 ran in its own passes: count its cells
+    // with some Lambda_I < 1 here (Lambda >= 0: bit-pattern compares on the integer pipe)
+    if (d.cq && !d.frz)
+      nlam = lt_one(L(i, j, 0)) || lt_one(L(i, j, 1)) || lt_one(L(i, j, 2)) || lt_one(L(i, j, 3));
     double th[4];
     if (d.frz) {   // frozen branch: the recorded face coefficients (after Remark 4.1)
       const size_t PS = (size_t)g.nxa * g.nya;
@@ -1407,6 +1411,7 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     }
   }
   if (nface) atomicAdd(&d.st->cnt[ST_FACE_THETA_LT1], (unsigned long long)nface);
+  if (nlam) atomicAdd(&d.st->cnt[ST_LAMBDA_LT1], (unsigned long long)nlam);
 }
 
 // Remark 4.1 round-off shrink for the flagged cells, one thread, in cell order.
@@ -1485,10 +1490,15 @@ __device__ void b_repair(const AfDev &d, const AfGrid &g, double a, double b) {
       }
     }
   }
-  d.st->cnt[ST_SHRINK] += nshr;
-  d.st->cnt[ST_CELL_SHRINK] += nshr;
-  d.st->cnt[ST_NONADMISSIBLE] += nbad;
-  if (nbad) d.st->err |= AFE_NONADMISSIBLE;
+  // atomics: the point list pass may update the same counters concurrently
+  if (nshr) {
+    atomicAdd(&d.st->cnt[ST_SHRINK], nshr);
+    atomicAdd(&d.st->cnt[ST_CELL_SHRINK], nshr);
+  }
+  if (nbad) {
+    atomicAdd(&d.st->cnt[ST_NONADMISSIBLE], nbad);
+    atomicOr(&d.st->err, AFE_NONADMISSIBLE);
+  }
   d.st->nrepair = 0;
 }
 
@@ -1552,15 +1562,16 @@ __device__ __forceinline__ void b_points_slow(const AfDev &d, const AfGrid &g, d
   }
 }
 
-// Cells whose box was not certified: Sec. 3.2 step (2) in three dense passes.
+// Cells whose box was not certified: Sec. 3.2 step (2) in two dense passes.
 // A (one thread per listed cell): the rectangle R_rho; Lambda starts at Lambda^rho;
 // the vertices A^k that leave S_p go to the vertex list.  B (one thread per listed
 // vertex): the Newton solve for r, then Lambda_I = min(Lambda_I, r A_I) for the I
 // with k_I = 1, by an atomic minimum on the bit patterns (Lambda >= 0, for which the
 // integer order is the numeric order): exact and order-free, so Lambda equals the
-// one-thread box of Sec. 3.2 bit for bit.  C: the count of cells with Lambda < 1.
-// (A half-warp per cell, one lane per vertex, was measured slower than one thread
-// per cell: every lane repeats the loads and the rectangle.)
+// one-thread box of Sec. 3.2 bit for bit.  The count of cells with Lambda < 1 is
+// taken by the final pass.  (For long lists a half-warp per cell, one lane per vertex,
+// was measured slower than one thread per cell: every lane repeats the loads and the
+// rectangle; short lists take it, for its latency.)
 __device__ __forceinline__ void rect_rho(const double *L1, const double (*H)[8], double eps_rho, double *LamRho) {
   double negsum = 0.0;
   for (int J = 0; J < 4; ++J)
@@ -1580,8 +1591,48 @@ __device__ __forceinline__ void box_vertex(int kk, const double *LamRho, const d
   }
 }
 
+// A short list (at most one cell per half-warp of the grid, as on quiet data): a half-warp
+// per cell, lane v the vertex A^v with its own Newton solve, the minima by shuffles;
+// the whole box is done here (latency: one vertex instead of sixteen in a row).
+__device__ __forceinline__ void cells_box_short(const AfDev &d, const AfGrid &g, int n) {
+  const double dt = d.sc->dt, cxf = dt * g.rdx, cyf = dt * g.rdy;
+  const size_t PS = (size_t)g.nxa * g.nya;
+  const int lane = threadIdx.x & 31, v = lane & 15;
+  const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;   // one cell per half-warp
+  const int tw = (blockIdx.x * blockDim.x + (threadIdx.x & ~31)) >> 4;
+  if (tw >= n) return;   // the whole warp is past the list
+  const bool live = t < n;
+  const int tt = live ? t : tw;
+  const int o = d.cq[tt], i = o % g.nxa, j = o / g.nxa;
+  double L1[8], H[4][8], LamRho[4], A[4], D[8], V[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) L1[k] = d.lim1[k * PS + o];
+  cell_H(d, g, i, j, cxf, cyf, H);
+  rect_rho(L1, H, d.cqe[2 * tt], LamRho);
+  box_vertex(v, LamRho, H, A, D);
+  for (int k = 0; k < 8; ++k) V[k] = L1[k] + D[k];
+  NewtonLog nl = {0, 0};
+  double r = 1.0;
+  if (live && pressure(V, g.gm1) < d.cqe[2 * tt + 1]) r = newton_root(L1, D, d.cqe[2 * tt + 1], g.gm1, nl);
+#pragma unroll
+  for (int I = 0; I < 4; ++I) {
+    double m = ((v >> I) & 1) ? r * A[I] : INFINITY;
+#pragma unroll
+    for (int off = 1; off < 16; off <<= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (live && v == 0) d.lam[I * PS + o] = fmin(LamRho[I], m);
+  }
+  if (nl.solves) {
+    atomicAdd(&d.st->cnt[ST_NEWTON_SOLVES], (unsigned long long)nl.solves);
+    atomicMax(&d.st->cnt[ST_NEWTON_MAXIT], (unsigned long long)nl.maxit);
+  }
+}
+
 __device__ __forceinline__ void b_cells_box(const AfDev &d, const AfGrid &g) {
   const int n = min(*(volatile int *)&d.st->ncq, d.cq_cap);
+  if (n <= (int)((gridDim.x * blockDim.x) >> 4)) {
+    cells_box_short(d, g, n);
+    return;
+  }
   const double dt = d.sc->dt, cxf = dt * g.rdx, cyf = dt * g.rdy;
   const size_t PS = (size_t)g.nxa * g.nya;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -1633,17 +1684,6 @@ __device__ __forceinline__ void b_cells_newton(const AfDev &d, const AfGrid &g) 
     atomicAdd(&d.st->cnt[ST_NEWTON_SOLVES], (unsigned long long)nl.solves);
     atomicMax(&d.st->cnt[ST_NEWTON_MAXIT], (unsigned long long)nl.maxit);
   }
-}
-
-__device__ __forceinline__ void b_cells_count(const AfDev &d, const AfGrid &g) {
-  const int n = min(*(volatile int *)&d.st->ncq, d.cq_cap);
-  const size_t PS = (size_t)g.nxa * g.nya;
-  int nlam = 0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int o = d.cq[t];
-    nlam += (d.lam[o] < 1.0 || d.lam[PS + o] < 1.0 || d.lam[2 * PS + o] < 1.0 || d.lam[3 * PS + o] < 1.0);
-  }
-  if (nlam) atomicAdd(&d.st->cnt[ST_LAMBDA_LT1], (unsigned long long)nlam);
 }
 
 #define AF_BATCH_LOOP(call)                                       \
@@ -1729,9 +1769,7 @@ __global__ void __launch_bounds__(128) k_cells_box(const __grid_constant__ AfDev
 __global__ void __launch_bounds__(128) k_cells_newton(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
   b_cells_newton(d, g);
 }
-__global__ void __launch_bounds__(128) k_cells_count(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g) {
-  b_cells_count(d, g);
-}
+
 __global__ void k_repair(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g, double a, double b) {
   if (threadIdx.x == 0 && blockIdx.x == 0) b_repair(d, g, a, b);
 }
@@ -1974,7 +2012,6 @@ void af_launch_cells_slow(const AfDev &d, const AfGrid &g, cudaStream_t s) {
   if (!d.cq) return;
   k_cells_box<<<152 * 4, 128, 0, s>>>(d, g);
   k_cells_newton<<<152 * 4, 128, 0, s>>>(d, g);
-  k_cells_count<<<152 * 2, 128, 0, s>>>(d, g);
 }
 void af_launch_repair(const AfDev &d, const AfGrid &g, double a, double b, cudaStream_t s) {
   k_repair<<<1, 32, 0, s>>>(d, g, a, b);

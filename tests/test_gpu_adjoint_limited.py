@@ -43,6 +43,7 @@ if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
 import paper_2506_04857_gb300 as af  # noqa: E402
+from paper_2506_04857_gb300.adjoint import af_steps, magnetic_energy  # noqa: E402
 
 GROUPS = [(0,), (1, 2, 3), (1, 2, 3), (1, 2, 3), (4, 5, 6), (4, 5, 6), (4, 5, 6), (7,)]
 
@@ -462,6 +463,53 @@ def test_limited_step_adjoint_against_central_differences(dt_sensitivity):
         mu = af.af_adjoint_step_frozen(s.ctx, dt, stages[0], stages[1], co, lam, U3=stages[2],
                                        dt_sensitivity=dt_sensitivity)
         ad = sum(float((m * x).sum()) for m, x in zip(mu, d))
+        worst = max(worst, abs(fd - ad) / max(abs(fd), abs(ad)))
+    s.close()
+    assert worst <= 1e-6, worst
+
+
+def test_checkpointed_solve_gradient_on_a_limited_run():
+    """af_steps on a limited run (the double rarefaction near vacuum, kappa = 1, every
+    limiter active; 6 steps, checkpoints every 4): the gradient of the magnetic energy
+    against central differences of the same six steps, each frozen at the coefficients its
+    forward step recorded and with its recorded dt, along 4 smooth directions (<= 1e-6)."""
+    pb = generic_field(ai.double_rarefaction(32, speed=6.0))
+    U = cuda_state(noisy(pb, run_oracle(pb, ai.dofs(pb), 10), 1e-2, 51))
+    s = solver_for(pb)
+    L = af.af_coeff_len(s.ctx)
+    nsteps = 6
+    X0 = [t.clone().requires_grad_(True) for t in U]
+    out = af_steps(s, X0, nsteps, checkpoint_every=4)
+    J = magnetic_energy(out, pb.dx, pb.dy, pb.bc)
+    J.backward()
+    grad = [x.grad for x in X0]
+    # the forward steps again, recording each step's coefficients and dt
+    s.set_state(U)
+    cos, dts = [], []
+    for _ in range(nsteps):
+        co = torch.empty(3 * L, dtype=torch.float64, device="cuda")
+        af.af_record_coeffs(s.ctx, co)
+        dts.append(s.step())
+        af.af_record_coeffs(s.ctx, None)
+        cos.append(co)
+    rc, cnt = s.status(reset=True)
+    assert rc == af.AF_OK and cnt["point_limited"] > 0 and cnt["newton_solves"] > 0
+
+    def frozen_run(V):
+        s.set_state(V)
+        for co, dt in zip(cos, dts):
+            af.af_freeze_coeffs(s.ctx, co)
+            for k in range(3):
+                s.stage(k, dt)
+            af.af_freeze_coeffs(s.ctx, None)
+        return float(magnetic_energy(s.get_state(), pb.dx, pb.dy, pb.bc))
+
+    worst = 0.0
+    for trial in range(4):
+        d = cuda_state(smooth_dir(pb, U, 300 + trial))
+        eps = 1e-7
+        fd = (frozen_run([u + eps * x for u, x in zip(U, d)]) - frozen_run([u - eps * x for u, x in zip(U, d)])) / (2 * eps)
+        ad = sum(float((g_ * x).sum()) for g_, x in zip(grad, d))
         worst = max(worst, abs(fd - ad) / max(abs(fd), abs(ad)))
     s.close()
     assert worst <= 1e-6, worst
