@@ -71,10 +71,10 @@ __device__ __forceinline__ double pressure(const double *U, double gm1) {
 }
 // q = rho E - |m|^2/2 - rho |B|^2/2 - rho c; q >= 0 <=> p >= (gamma-1) c for rho > 0
 __device__ __forceinline__ double qform(const double *U, double c) {
-  double m2 = fma(U[1], U[1], fma(U[2], U[2], U[3] * U[3]));
-  double b2 = fma(U[4], U[4], fma(U[5], U[5], U[6] * U[6]));
+  double m2 = fma(U[1], U[1], fma(U[2], U[2], mul_i(U[3], U[3])));
+  double b2 = fma(U[4], U[4], fma(U[5], U[5], mul_i(U[6], U[6])));
   double t = fma(0.5, b2, c);
-  return fma(-U[0], t, fma(U[0], U[7], -0.5 * m2));
+  return fma(-U[0], t, fma(U[0], U[7], ldexp_i<-1>(-m2)));
 }
 // rho >= 1e-13 and p >= 1e-13 (so every limiter of Sec. 3 leaves the state alone)
 __device__ __forceinline__ bool clear_of_floor(const double *U, const AfGrid &g) {
@@ -91,43 +91,45 @@ __device__ __forceinline__ bool in_G(const double *U, double gm1) {
 // avg = true stores the cell-average layout.
 __device__ __forceinline__ void point_data(const double *U, const AfGrid &g, double *out, size_t PS, bool avg,
                                            double &sr1, double &sr2) {
+  // The standalone products run on the integer pipes (mul_i, bitwise those of
+  // DMUL), beside the FMAs and sums on the FP64 pipe.
   const double rho = U[0], r = rcp(rho);
-  const double v1 = U[1] * r, v2 = U[2] * r, v3 = U[3] * r;
+  const double v1 = mul_i(U[1], r), v2 = mul_i(U[2], r), v3 = mul_i(U[3], r);
   const double B1 = U[4], B2 = U[5], B3 = U[6], E = U[7];
-  const double b1s = B1 * B1, b2s = B2 * B2;
+  const double b1s = mul_i(B1, B1), b2s = mul_i(B2, B2);
   const double BB = fma(B3, B3, b1s + b2s);
-  const double mv = fma(U[1], v1, fma(U[2], v2, U[3] * v3));
-  const double p = g.gm1 * fma(-0.5, mv + BB, E);
+  const double mv = fma(U[1], v1, fma(U[2], v2, mul_i(U[3], v3)));
+  const double p = mul_i(g.gm1, fma(-0.5, mv + BB, E));
   const double pt = fma(0.5, BB, p);
-  const double vB = fma(v1, B1, fma(v2, B2, v3 * B3));
+  const double vB = fma(v1, B1, fma(v2, B2, mul_i(v3, B3)));
   const double Ept = E + pt;
-  const double f12 = fma(U[1], v2, -B1 * B2);   // rho v1 v2 - B1 B2 (F1[2] = F2[1])
-  const double f15 = fma(v1, B2, -B1 * v2);     // v1 B2 - B1 v2    (F1[5] = -F2[4])
+  const double f12 = fma(U[1], v2, -mul_i(B1, B2));   // rho v1 v2 - B1 B2 (F1[2] = F2[1])
+  const double f15 = fma(v1, B2, -mul_i(B1, v2));     // v1 B2 - B1 v2    (F1[5] = -F2[4])
   double F1[7], F2[7];
   F1[0] = U[1];
   F1[1] = fma(U[1], v1, pt) - b1s;
   F1[2] = f12;
-  F1[3] = fma(U[1], v3, -B1 * B3);
+  F1[3] = fma(U[1], v3, -mul_i(B1, B3));
   F1[4] = f15;
-  F1[5] = fma(v1, B3, -B1 * v3);
-  F1[6] = fma(Ept, v1, -B1 * vB);
+  F1[5] = fma(v1, B3, -mul_i(B1, v3));
+  F1[6] = fma(Ept, v1, -mul_i(B1, vB));
   F2[0] = U[2];
   F2[1] = f12;
   F2[2] = fma(U[2], v2, pt) - b2s;
-  F2[3] = fma(U[2], v3, -B2 * B3);
+  F2[3] = fma(U[2], v3, -mul_i(B2, B3));
   F2[4] = -f15;
-  F2[5] = fma(v2, B3, -B2 * v3);
-  F2[6] = fma(Ept, v2, -B2 * vB);
+  F2[5] = fma(v2, B3, -mul_i(B2, v3));
+  F2[6] = fma(Ept, v2, -mul_i(B2, vB));
   // eq. (cf)
-  const double c2 = g.gamma * p * r;
+  const double c2 = mul_i(mul_i(g.gamma, p), r);
   const double a = fma(BB, r, c2);
-  const double k4 = 4.0 * (c2 * r);
-  const double aa = a * a, ha = 0.5 * a;
+  const double k4 = 4.0 * mul_i(c2, r);
+  const double aa = mul_i(a, a), ha = 0.5 * a;
   double d1 = fma(-k4, b1s, aa), d2 = fma(-k4, b2s, aa);
-  d1 = d1 > 0.0 ? d1 : 0.0;
-  d2 = d2 > 0.0 ? d2 : 0.0;
-  const double cf1 = dsqrt(fma(0.5, dsqrt(d1), ha));
-  const double cf2 = dsqrt(fma(0.5, dsqrt(d2), ha));
+  d1 = gt_zero(d1) ? d1 : 0.0;
+  d2 = gt_zero(d2) ? d2 : 0.0;
+  const double cf1 = dsqrt_i(fma(0.5, dsqrt_i(d1), ha));
+  const double cf2 = dsqrt_i(fma(0.5, dsqrt_i(d2), ha));
   sr1 = absd(v1) + cf1;
   sr2 = absd(v2) + cf2;
 #pragma unroll
@@ -142,7 +144,7 @@ __device__ __forceinline__ void point_data(const double *U, const AfGrid &g, dou
     out[QA_CF1 * PS] = cf1;
     out[QA_CF2 * PS] = cf2;
     out[QA_PT * PS] = pt;
-    out[QA_SRHO * PS] = dsqrt(rho);
+    out[QA_SRHO * PS] = dsqrt_i(rho);
   } else {
     out[QP_SR1 * PS] = sr1;
     out[QP_SR2 * PS] = sr2;
@@ -204,9 +206,9 @@ __device__ __noinline__ void full_data(const double *U, const AfGrid &g, Full &d
 __device__ __forceinline__ double alpha_llf(double va, double vb, double cfa, double cfb, double sra, double srb,
                                             const double *Ba, const double *Bb) {
   const double rden = rcp(sra + srb);
-  const double roe = absd(fma(sra, va, srb * vb)) * rden;
+  const double roe = mul_i(absd(fma(sra, va, mul_i(srb, vb))), rden);
   const double d0 = Ba[0] - Bb[0], d1 = Ba[1] - Bb[1], d2 = Ba[2] - Bb[2];
-  const double nb = dsqrt(fma(d0, d0, fma(d1, d1, d2 * d2)));
+  const double nb = dsqrt_i(fma(d0, d0, fma(d1, d1, mul_i(d2, d2))));
   const double mv = maxnn(maxnn(absd(va), absd(vb)), roe);
   return mv + maxnn(cfa, cfb) + nb * rden;
 }
@@ -500,7 +502,7 @@ __device__ __forceinline__ void fvs_line(const PP *P, size_t PS, int nxa, double
     const double up = fma(6.0, u2, fma(-4.0, u1 + u3, u0 + u4));
     double dk;
     if (k == 4 + L) {
-      dk = al * up;
+      dk = mul_i(al, up);
       dBl = b_line(u0, u1, u2, u3, u4, upw);
     } else {
       const int s = (L == 0 ? QP_F1 : QP_F2) + fslot(L, k);
@@ -660,20 +662,20 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   const double ptc = A(ci, cj, QA_PT), pte = A(e, cj, QA_PT), ptw = A(w, cj, QA_PT);
   const double ptn = A(ci, n, QA_PT), pts = A(ci, s, QA_PT);
   const double sx = pte + ptw, sy = ptn + pts;
-  phi[0] = ddiv(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
-  phi[1] = ddiv(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
+  phi[0] = ddiv_i(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
+  phi[1] = ddiv_i(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
-  const double divv = fma(A(e, cj, QA_V1) - A(w, cj, QA_V1), hx, (A(ci, n, QA_V2) - A(ci, s, QA_V2)) * hy);
-  const double curl = fma(A(e, cj, QA_V2) - A(w, cj, QA_V2), hx, -(A(ci, n, QA_V1) - A(ci, s, QA_V1)) * hy);
+  const double divv = fma(A(e, cj, QA_V1) - A(w, cj, QA_V1), hx, mul_i(A(ci, n, QA_V2) - A(ci, s, QA_V2), hy));
+  const double curl = fma(A(e, cj, QA_V2) - A(w, cj, QA_V2), hx, -mul_i(A(ci, n, QA_V1) - A(ci, s, QA_V1), hy));
   if (is_zero(divv)) {   // -0 / den gives 0: no square root or quotient needed
     phi[2] = 0.0;
   } else {
-    const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
-    const double ph2 = ddiv(-divv, den);
-    phi[2] = ph2 > 0.0 ? ph2 : 0.0;
+    const double den = dsqrt_i(fma(divv, divv, fma(curl, curl, 1e-40)));
+    const double ph2 = ddiv_i(-divv, den);
+    phi[2] = gt_zero(ph2) ? ph2 : 0.0;
   }
   const double num = (Ub(e, cj, 4) - Ub(w, cj, 4)) + (Ub(ci, n, 5) - Ub(ci, s, 5));
-  phi[3] = ddiv(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
+  phi[3] = ddiv_i(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
 }
 
 template <bool GB, bool UP>
@@ -725,21 +727,21 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
         const PP Py[5] = {pref(d, g, 3, i, jm), pref(d, g, 1, i, cj0), me, pref(d, g, 1, i, cj1), pref(d, g, 3, i, jp)};
         fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
         fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-        divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
+        divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, 0.5 * g.rdy));
       } else if (cls == 1) {
         const PP Px[5] = {pref(d, g, 1, im, j), pref(d, g, 4, ci0, j), me, pref(d, g, 4, ci1, j), pref(d, g, 1, ip, j)};
         fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
         central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
-        divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
+        divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, g.rdy));
       } else {
         central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
         const PP Py[5] = {pref(d, g, 2, i, jm), pref(d, g, 4, i, cj0), me, pref(d, g, 4, i, cj1), pref(d, g, 2, i, jp)};
         fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-        divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
+        divB = fma(dBx, g.rdx, mul_i(dBy, 0.5 * g.rdy));
       }
       if (g.src_point_on) {
         // -(div B) Psi(U), Psi = (0, B, v, v.B)
-        const double sdt = dt * divB;
+        const double sdt = mul_i(dt, divB);
         acc[1] = fma(-sdt, pu(me, 4), acc[1]);
         acc[2] = fma(-sdt, pu(me, 5), acc[2]);
         acc[3] = fma(-sdt, pu(me, 6), acc[3]);
@@ -797,7 +799,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
       } else {
         const double *un = d.un[cls];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) uo[k * cs + oo] = fma(a, __ldg(un + k * cs + oo), b * acc[k]);
+        for (int k = 0; k < 8; ++k) uo[k * cs + oo] = fma(a, __ldg(un + k * cs + oo), mul_i(b, acc[k]));
       }
     }
     if (mode != 1 && i < g.nx && j < g.ny && g.kappa != 0.0) {
@@ -844,7 +846,7 @@ __device__ __forceinline__ double theta_s(const AfDev &d, const AfGrid &g, int d
   get_phi<GB>(d, g, ia, ja, pa);
   get_phi<GB>(d, g, ib, jb, pb);
   const double p1 = maxnn(pa[dir], pb[dir]), p2 = maxnn(pa[2], pb[2]), p3 = maxnn(pa[3], pb[3]);
-  const double arg = -g.kappa * fma(p1, p2, p3);
+  const double arg = mul_i(-g.kappa, fma(p1, p2, p3));
   return is_zero(arg) ? 1.0 : exp(arg);   // quiet data: exp(-0) = 1 without the call
 }
 
@@ -883,17 +885,17 @@ __device__ __forceinline__ void face(const AfDev &d, const AfGrid &g, double *ou
     double Fh = 0.0, Fl = 0.0;
     if (k != 4 + L) {
       const int s = f0 + fslot(L, k);
-      Fh = (pw(lo, PS, g.nxa, s) + pw(hi, PS, g.nxa, s) + 4.0 * pw(mid, PS, g.nxa, s)) * (1.0 / 6.0);
-      if (llf) Fl = 0.5 * fma(-al, Ub(cbi, cbj, k) - Ub(cai, caj, k), A(cai, caj, s) + A(cbi, cbj, s));
+      Fh = mul_i(fma(4.0, pw(mid, PS, g.nxa, s), pw(lo, PS, g.nxa, s) + pw(hi, PS, g.nxa, s)), 1.0 / 6.0);
+      if (llf) Fl = ldexp_i<-1>(fma(-al, Ub(cbi, cbj, k) - Ub(cai, caj, k), A(cai, caj, s) + A(cbi, cbj, s)));
     } else if (llf) {
-      Fl = -0.5 * al * (Ub(cbi, cbj, k) - Ub(cai, caj, k));
+      Fl = mul_i(ldexp_i<-1>(-al), Ub(cbi, cbj, k) - Ub(cai, caj, k));
     }
     out[(QF_FLLF + k) * PS] = Fl;
-    out[(QF_G + k) * PS] = ts == 1.0 ? Fh - Fl : ts * (Fh - Fl);
+    out[(QF_G + k) * PS] = is_one(ts) ? Fh - Fl : mul_i(ts, Fh - Fl);
   }
   out[QF_TS * PS] = ts;
   out[QF_AL * PS] = al;
-  nsens += ts < 0.99;
+  nsens += (long long)bits(ts) < (long long)bits(0.99);   // ts in [0, 1]
 }
 
 template <bool GB>
@@ -1022,18 +1024,19 @@ __device__ __noinline__ void flux_limiter_box(const double *L1, const double (*H
 // |H_I,k|, q(V) >= q(L1) - T, T bounding the linear, quadratic and cubic terms.
 __device__ __forceinline__ bool box_certified(const double *L1, const double *D, const AfGrid &g) {
   const double rho = L1[0], E = L1[7];
-  const double bb = fma(L1[4], L1[4], fma(L1[5], L1[5], L1[6] * L1[6]));
-  const double mm = fma(L1[1], L1[1], fma(L1[2], L1[2], L1[3] * L1[3]));
-  const double q0 = fma(rho, E, -0.5 * mm) - rho * fma(0.5, bb, g.c13);
-  const double bD = fma(absd(L1[4]), D[4], fma(absd(L1[5]), D[5], absd(L1[6]) * D[6]));
-  const double mD = fma(absd(L1[1]), D[1], fma(absd(L1[2]), D[2], absd(L1[3]) * D[3]));
-  const double DB2 = fma(D[4], D[4], fma(D[5], D[5], D[6] * D[6]));
-  const double DM2 = fma(D[1], D[1], fma(D[2], D[2], D[3] * D[3]));
+  const double bb = fma(L1[4], L1[4], fma(L1[5], L1[5], mul_i(L1[6], L1[6])));
+  const double mm = fma(L1[1], L1[1], fma(L1[2], L1[2], mul_i(L1[3], L1[3])));
+  const double q0 = fma(rho, E, ldexp_i<-1>(-mm)) - rho * fma(0.5, bb, g.c13);
+  const double bD = fma(absd(L1[4]), D[4], fma(absd(L1[5]), D[5], mul_i(absd(L1[6]), D[6])));
+  const double mD = fma(absd(L1[1]), D[1], fma(absd(L1[2]), D[2], mul_i(absd(L1[3]), D[3])));
+  const double DB2 = fma(D[4], D[4], fma(D[5], D[5], mul_i(D[6], D[6])));
+  const double DM2 = fma(D[1], D[1], fma(D[2], D[2], mul_i(D[3], D[3])));
+  const double hrho = ldexp_i<-1>(rho);
   const double T1 = fma(absd(E - fma(0.5, bb, g.c13)), D[0], fma(rho, D[7], fma(rho, bD, mD)));
-  const double T2 = fma(D[0], D[7], fma(0.5, DM2, fma(0.5 * rho, DB2, D[0] * bD)));
-  const double T3 = 0.5 * D[0] * DB2;
+  const double T2 = fma(D[0], D[7], fma(0.5, DM2, fma(hrho, DB2, mul_i(D[0], bD))));
+  const double T3 = mul_i(ldexp_i<-1>(D[0]), DB2);
   const double T = T1 + T2 + T3;
-  const double scale = fma(rho, absd(E), fma(0.5, mm, fma(0.5 * rho, bb, T)));
+  const double scale = fma(rho, absd(E), fma(0.5, mm, fma(hrho, bb, T)));
   // density rectangle: Lambda^rho = 1 when rho(L1) - 1e-13 >= 1e-12 + sum |rho(H)|
   return (q0 - T >= 1e-12 * scale) && (rho - 1e-13 >= (1e-12 + D[0]) * (1.0 + 1e-10));
 }
@@ -1121,7 +1124,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           if (m == 0) dy2 = fma(3.0, b2[l][1] - b2[l][0], -(b2[l][2] - b2[l][1]));
           else if (m == 1) dy2 = b2[l][2] - b2[l][0];
           else dy2 = fma(3.0, b2[l][2] - b2[l][1], -(b2[l][1] - b2[l][0]));
-          wd[l][m] = (w[l] * w[m]) * fma(dx1, rdx, dy2 * rdy);
+          wd[l][m] = mul_i(w[l] * w[m], fma(dx1, rdx, mul_i(dy2, rdy)));
         }
       // Psi at the nodes: B from the DoFs, v and v.B from the point data
       // node (l,m): corners (l,m even), x-faces (l even, m = 1), y-faces (l = 1, m even), centre (1,1)
@@ -1133,7 +1136,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
 #pragma unroll
       for (int l = 0; l < 3; ++l)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) nz |= (unsigned long long)__double_as_longlong(wd[l][m]) << 1;
+        for (int m = 0; m < 3; ++m) nz |= bits(wd[l][m]) << 1;
       if (nz == 0) {
 #pragma unroll
         for (int k = 1; k < 8; ++k) S[k] = 0.0;
@@ -1193,19 +1196,19 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         bn = Ub(i, jn, 5);
         bs = Ub(i, js, 5);
       }
-      const double divBb = fma(be - bw, 0.5 * g.rdx, (bn - bs) * (0.5 * g.rdy));
+      const double divBb = fma(be - bw, 0.5 * g.rdx, mul_i(bn - bs, 0.5 * g.rdy));
       double Ubar[8];
       load8(Ub, i, j, Ubar);
       const double vb1 = A(i, j, QA_V1), vb2 = A(i, j, QA_V2), vb3 = A(i, j, QA_V3);
       double SL[8];
       SL[0] = 0.0;
-      SL[1] = divBb * Ubar[4];
-      SL[2] = divBb * Ubar[5];
-      SL[3] = divBb * Ubar[6];
-      SL[4] = divBb * vb1;
-      SL[5] = divBb * vb2;
-      SL[6] = divBb * vb3;
-      SL[7] = divBb * fma(vb1, Ubar[4], fma(vb2, Ubar[5], vb3 * Ubar[6]));
+      SL[1] = mul_i(divBb, Ubar[4]);
+      SL[2] = mul_i(divBb, Ubar[5]);
+      SL[3] = mul_i(divBb, Ubar[6]);
+      SL[4] = mul_i(divBb, vb1);
+      SL[5] = mul_i(divBb, vb2);
+      SL[6] = mul_i(divBb, vb3);
+      SL[7] = mul_i(divBb, fma(vb1, Ubar[4], fma(vb2, Ubar[5], mul_i(vb3, Ubar[6]))));
       if (!g.src_cell_on)
         for (int k = 0; k < 8; ++k) SL[k] = 0.0;
       // theta^s_ij = min over the four faces
@@ -1237,11 +1240,11 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         }
         // Lemma 3.1 CFL condition (diagnostic count only)
         {
-          const double lhs = dt * ((FX(i, j, QF_AL) + FX(ip, j, QF_AL)) * g.rdx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) * g.rdy +
-                                   ddiv(absd(divBb), A(i, j, QA_SRHO)));
+          const double lhs = mul_i(dt, (FX(i, j, QF_AL) + FX(ip, j, QF_AL)) * g.rdx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) * g.rdy +
+                                   ddiv_i(absd(divBb), A(i, j, QA_SRHO)));
           ncfl += lhs > 1.0 + 1e-12;
         }
-        const double dtts = dt * tsc;
+        const double dtts = mul_i(dt, tsc);
         double L1[8], Lam[4];
         double th_src = 1.0;
         if (d.frz) {   // frozen branch: Lim1 with the recorded theta_ij; face theta are recorded too
@@ -1260,7 +1263,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         if (fast) {
           double D[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) D[k] = fma(cxf, absd(Gf[0][k]) + absd(Gf[1][k]), cyf * (absd(Gf[2][k]) + absd(Gf[3][k])));
+          for (int k = 0; k < 8; ++k) D[k] = fma(cxf, absd(Gf[0][k]) + absd(Gf[1][k]), mul_i(cyf, absd(Gf[2][k]) + absd(Gf[3][k])));
           fast = box_certified(L1, D, g);
         }
         bool listed = false;
@@ -1393,7 +1396,7 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     // rho > 0 and p > 0 and all finite, on the integer pipe: for finite doubles
     // x > 0 exactly when the bit pattern, read as a signed integer, is > 0
     const double q = qform(fe, 0.0);
-    bool ok = __double_as_longlong(fe[0]) > 0 && __double_as_longlong(q) > 0 && finite_bits(q);
+    bool ok = (long long)bits(fe[0]) > 0 && (long long)bits(q) > 0 && finite_bits(q);
 #pragma unroll
     for (int k = 0; k < 8; ++k) ok = ok && finite_bits(fe[k]);
     if (!ok && !d.frz) {
@@ -1407,7 +1410,7 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
       for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fe[k];
     } else {
 #pragma unroll
-      for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fma(a, __ldg(d.un[0] + k * cs0 + o0), b * fe[k]);
+      for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fma(a, __ldg(d.un[0] + k * cs0 + o0), mul_i(b, fe[k]));
     }
   }
   if (nface) atomicAdd(&d.st->cnt[ST_FACE_THETA_LT1], (unsigned long long)nface);
@@ -1794,7 +1797,10 @@ __global__ void k_math_check(int op, const double *x, const double *y, double *o
   if (t >= n) return;
   if (op == 0) out[t] = rcp(x[t]);
   else if (op == 1) out[t] = ddiv(x[t], y[t]);
-  else out[t] = dsqrt(x[t]);
+  else if (op == 2) out[t] = dsqrt(x[t]);
+  else if (op == 3) out[t] = add_i(x[t], y[t]);
+  else if (op == 4) out[t] = mul_i(x[t], y[t]);
+  else out[t] = dsqrt_i(x[t]);
 }
 
 // FP64 FMA throughput probe: 8 independent register chains per thread.

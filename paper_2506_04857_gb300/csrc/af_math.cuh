@@ -13,6 +13,11 @@
 //     operators.
 //   * maxnn/minnn/absd: min/max/abs of doubles on the integer pipe (valid for
 //     non-negative, non-NaN operands where stated).
+//   * mul_i/add_i: correctly rounded binary64 product and sum computed with
+//     integer instructions only, for code that is bound by the FP64 pipe while
+//     the integer pipes idle (GB300 has 2 FP64 lanes per SM against 64 integer
+//     ones).  Their results are bitwise those of DMUL/DADD; a kernel that moves
+//     part of its products and sums onto them runs both pipes at once.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -20,8 +25,24 @@ namespace afm {
 
 __device__ __forceinline__ unsigned hi32(double x) { return (unsigned)__double2hiint(x); }
 
+// The bit pattern of a double and back.  The move is opaque to the compiler, so
+// integer tests on the pattern stay integer instructions (a plain bit cast lets
+// the compiler turn e.g. (bits << 1) == 0 back into an FP64 compare).
+__device__ __forceinline__ unsigned long long bits(double x) {
+  unsigned long long r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double from_bits(unsigned long long u) {
+  double r;
+  asm("mov.b64 %0, %1;" : "=d"(r) : "l"(u));
+  return r;
+}
+
 // x == +0 or -0, on the integer pipe
-__device__ __forceinline__ bool is_zero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(double x) { return (bits(x) << 1) == 0; }
+// x > 0 (false for NaN), on the integer pipe: the patterns of +min subnormal .. +inf
+__device__ __forceinline__ bool gt_zero(double x) { return bits(x) - 1ULL < 0x7ff0000000000000ULL; }
 
 // true when the FP32 seed path is valid: 2^-123 <= |x| < 2^124
 __device__ __forceinline__ bool seed_ok(double x) {
@@ -88,28 +109,158 @@ __device__ __forceinline__ double dsqrt(double x) {
   return fma(r, h, s);
 }
 
+// dsqrt with its first product on the integer pipes (bitwise dsqrt)
+__device__ __forceinline__ double mul_i(double a, double b);
+__device__ __forceinline__ double dsqrt_i(double x) {
+  if (!seed_ok(x)) return is_zero(x) ? x : sqrt(x);
+  float yf = rsqrt_approx_f32(seed_f32(x));
+  double y = widen_f32(yf), h = widen_f32(0.5f * yf);
+  double s = mul_i(x, y);
+  double r = fma(-s, s, x);
+  s = fma(r, h, s);
+  r = fma(-s, s, x);
+  return fma(r, h, s);
+}
+
+// ddiv with its quotient product on the integer pipes (bitwise ddiv)
+__device__ __forceinline__ double ddiv_i(double a, double b) {
+  if (!seed_ok(b)) return a / b;
+  double y = widen_f32(rcp_approx_f32(seed_f32(b)));
+  double e = fma(-b, y, 1.0);
+  y = fma(y, e, y);
+  double q = mul_i(a, y);
+  double r = fma(-b, q, a);
+  return fma(r, y, q);
+}
+
 // max/min of non-negative, non-NaN doubles via their bit patterns
 __device__ __forceinline__ double maxnn(double a, double b) {
-  long long x = __double_as_longlong(a), y = __double_as_longlong(b);
-  return __longlong_as_double(x > y ? x : y);
+  const long long x = (long long)bits(a), y = (long long)bits(b);
+  return from_bits((unsigned long long)(x > y ? x : y));
 }
 __device__ __forceinline__ double minnn(double a, double b) {
-  long long x = __double_as_longlong(a), y = __double_as_longlong(b);
-  return __longlong_as_double(x < y ? x : y);
+  const long long x = (long long)bits(a), y = (long long)bits(b);
+  return from_bits((unsigned long long)(x < y ? x : y));
 }
-__device__ __forceinline__ double absd(double a) {
-  return __hiloint2double(__double2hiint(a) & 0x7fffffff, __double2loint(a));
-}
+__device__ __forceinline__ double absd(double a) { return from_bits(bits(a) & 0x7fffffffffffffffULL); }
 // finite (neither infinite nor NaN), from the exponent bits
 __device__ __forceinline__ bool finite_bits(double a) { return ((hi32(a) >> 20) & 0x7ffu) != 0x7ffu; }
 // a == 1.0 and a < 1.0 for non-negative a, +NaN included (bit-pattern comparisons on the
 // integer pipe)
-__device__ __forceinline__ bool is_one(double a) { return __double_as_longlong(a) == 0x3ff0000000000000LL; }
-__device__ __forceinline__ bool lt_one(double a) { return __double_as_longlong(a) < 0x3ff0000000000000LL; }
+__device__ __forceinline__ bool is_one(double a) { return bits(a) == 0x3ff0000000000000ULL; }
+__device__ __forceinline__ bool lt_one(double a) { return (long long)bits(a) < 0x3ff0000000000000LL; }
 // a < 0 for non-NaN a (negative zero is not negative)
 __device__ __forceinline__ bool isneg(double a) {
-  long long x = __double_as_longlong(a);
+  const long long x = (long long)bits(a);
   return x < 0 && (x & 0x7fffffffffffffffLL) != 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Binary64 product and sum on the integer pipes (IEEE 754-2008 round to nearest,
+// ties to even).  Method: the exact integer product or sum of the significands,
+// normalised, then rounded with a half bit and a sticky bit (the textbook
+// construction, e.g. D. Goldberg, ACM Comput. Surv. 23(1), 1991, Sec. 1.4 and
+// Theorem 2; J.-M. Muller et al., Handbook of Floating-Point Arithmetic, 2018,
+// ch. 7).  A fast path covers every finite case whose result cannot be
+// subnormal; the rest (infinities, NaN, subnormal operands or results) takes
+// the FP64 instruction in a function that is not inlined: a branch around an
+// inlined one is turned into a predicated FP64 instruction that still takes
+// its issue slot on the FP64 pipe.
+// ---------------------------------------------------------------------------
+static __device__ __noinline__ double mul_hw(double a, double b) { return __dmul_rn(a, b); }
+static __device__ __noinline__ double add_hw(double a, double b) { return __dadd_rn(a, b); }
+
+// a * b.  Fast path: both finite with normal exponent fields and a product
+// exponent field in [1, 2045], or a zero factor times a finite one (+-0).
+__device__ __forceinline__ double mul_i(double a, double b) {
+  const unsigned long long ia = bits(a), ib = bits(b);
+  const unsigned s = (unsigned)((ia ^ ib) >> 32) & 0x80000000u;
+  const unsigned ea = (unsigned)(ia >> 52) & 0x7ffu, eb = (unsigned)(ib >> 52) & 0x7ffu;
+  const bool za = (ia << 1) == 0, zb = (ib << 1) == 0;
+  const int esum = (int)(ea + eb) - 1023;   // product exponent field when the significand product is < 2
+  const bool fast = ((ea - 1u < 2046u) && (eb - 1u < 2046u) && esum >= 1 && esum <= 2045) ||
+                    ((za || zb) && ea != 0x7ffu && eb != 0x7ffu);
+  if (!fast) return mul_hw(a, b);
+  // significands with the leading one at bit 63: x, y in [2^63, 2^64)
+  const unsigned long long x = ((ia & 0x000fffffffffffffULL) | 0x0010000000000000ULL) << 11;
+  const unsigned long long y = ((ib & 0x000fffffffffffffULL) | 0x0010000000000000ULL) << 11;
+  const unsigned x0 = (unsigned)x, x1 = (unsigned)(x >> 32), y0 = (unsigned)y, y1 = (unsigned)(y >> 32);
+  unsigned r0, r1, r2, r3;   // the 128-bit product r3:r2:r1:r0, in [2^126, 2^128)
+  asm("mul.lo.u32 %0, %4, %6;\n\t"
+      "mul.hi.u32 %1, %4, %6;\n\t"
+      "mad.lo.cc.u32 %1, %4, %7, %1;\n\t"
+      "madc.hi.u32 %2, %4, %7, 0;\n\t"
+      "mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32 %3, 0, 0;\n\t"
+      "mad.lo.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.u32 %3, %5, %7, %3;"
+      : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+      : "r"(x0), "r"(x1), "r"(y0), "r"(y1));
+  const bool top = (r3 >> 31) != 0;   // significand product in [2, 4)
+  // the 53-bit significand (leading one at bit 52) and the bits below it scaled
+  // to 11 bits (half = 0x400); the low 64 bits of the product are sticky
+  const unsigned sh = top ? 11u : 10u;
+  const unsigned qlo = __funnelshift_r(r2, r3, sh), qhi = r3 >> sh;
+  const unsigned rem = top ? (r2 & 0x7ffu) : ((r2 & 0x3ffu) << 1);
+  const bool st = (r0 | r1) != 0;
+  const unsigned up = (rem > 0x400u || (rem == 0x400u && (st || (qlo & 1u)))) ? 1u : 0u;
+  // exponent field minus one plus sign into the high word; the leading one of the
+  // significand adds the missing one, and a rounding carry out of it the next
+  const unsigned eh = ((unsigned)(esum + (top ? 1 : 0) - 1) << 20) | s;
+  unsigned lo, hi;
+  asm("add.cc.u32 %0, %2, %4;\n\taddc.u32 %1, %3, %5;" : "=r"(lo), "=r"(hi) : "r"(qlo), "r"(qhi), "r"(up), "r"(eh));
+  const unsigned long long r = (za || zb) ? ((unsigned long long)s << 32) : (((unsigned long long)hi << 32) | lo);
+  return from_bits(r);
+}
+
+// x * 2^K for a small constant K (an exact scaling): the exponent field moved by
+// K on the integer pipes when x and the result are normal, +-0 kept, the rest
+// (infinities, NaN, subnormal operand or result) by the FP64 product.
+template <int K>
+__device__ __forceinline__ double ldexp_i(double x) {
+  static_assert(K >= -8 && K <= 8, "small scalings only");
+  const unsigned long long ix = bits(x);
+  const unsigned e = (unsigned)(ix >> 52) & 0x7ffu;
+  if ((ix << 1) == 0) return x;
+  const bool ok = K >= 0 ? (e - 1u < (unsigned)(2046 - K)) : (e - (unsigned)(1 - K) < (unsigned)(2046 + K));
+  if (!ok) return mul_hw(x, K >= 0 ? (double)(1 << (K >= 0 ? K : 0)) : 1.0 / (double)(1 << (K < 0 ? -K : 0)));
+  return from_bits(ix + ((unsigned long long)(long long)K << 52));
+}
+
+// a + b.  Fast path: the operand of larger magnitude finite and normal with an
+// exponent field <= 2045, the other zero or with an exponent field >= 54 (no
+// result is then subnormal), or both zero.
+__device__ __forceinline__ double add_i(double a, double b) {
+  const unsigned long long SGN = 0x8000000000000000ULL;
+  const unsigned long long ia = bits(a), ib = bits(b);
+  const unsigned long long ma = ia & ~SGN, mb = ib & ~SGN;
+  const bool swp = ma < mb;
+  const unsigned long long X = swp ? mb : ma, Y = swp ? ma : mb;   // |x| >= |y|
+  const unsigned long long sx = (swp ? ib : ia) & SGN;
+  const unsigned ex = (unsigned)(X >> 52), ey = (unsigned)(Y >> 52);
+  const bool fast = (ex - 1u < 2045u && (ey >= 54u || Y == 0)) || X == 0;
+  if (!fast) return add_hw(a, b);
+  // significands with the leading one at bit 62 (10 guard bits below)
+  const unsigned long long fx = ((X & 0x000fffffffffffffULL) | 0x0010000000000000ULL) << 10;
+  const unsigned long long fy = Y == 0 ? 0ULL : ((Y & 0x000fffffffffffffULL) | 0x0010000000000000ULL) << 10;
+  unsigned dsh = ex - ey;
+  dsh = dsh < 63u ? dsh : 63u;
+  unsigned long long al = fy >> dsh;
+  al |= (unsigned long long)((al << dsh) != fy);   // sticky: some bit of y was shifted out
+  const bool sub = ((ia ^ ib) & SGN) != 0;
+  unsigned long long m = sub ? fx - al : fx + al;
+  const int lz = __clzll((long long)m);
+  m <<= (lz & 63);
+  const unsigned long long q0 = m >> 11;   // leading one at bit 52
+  const unsigned rem = (unsigned)m & 0x7ffu;   // half = 0x400
+  const unsigned long long q = q0 + (unsigned long long)(rem > 0x400u || (rem == 0x400u && (q0 & 1ULL)));
+  const unsigned long long e = (unsigned long long)(ex - (unsigned)lz);   // exponent field minus one
+  unsigned long long r = sx | ((e << 52) + q);
+  r = (m == 0) ? 0ULL : r;                // exact cancellation: +0
+  r = (X == 0) ? (ia & ib) : r;           // +-0 + +-0: -0 only for -0 + -0
+  return from_bits(r);
 }
 
 }  // namespace afm

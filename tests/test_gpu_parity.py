@@ -104,6 +104,70 @@ def test_fp64_helpers_error_bound(op):
         assert torch.equal(o2, 1.0 / xs if op == 0 else torch.sqrt(xs))
 
 
+def _bit_patterns(n, seed):
+    """Doubles from random bit patterns over every exponent, with families that
+    stress the rounding: close exponents (cancellation), exact halfway cases,
+    operands near the subnormal and overflow ranges, zeros, infinities and NaN."""
+    rng = np.random.default_rng(seed)
+    m = np.uint64(0x000FFFFFFFFFFFFF)
+    a = rng.integers(0, 2 ** 63, n, dtype=np.uint64) | (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
+    b = rng.integers(0, 2 ** 63, n, dtype=np.uint64) | (rng.integers(0, 2, n, dtype=np.uint64) << np.uint64(63))
+    fam = rng.integers(0, 10, n)
+    ea = (a >> np.uint64(52)) & np.uint64(0x7FF)
+    gap = rng.integers(-3, 4, n).astype(np.int64)
+    eb = np.clip(ea.astype(np.int64) + gap, 0, 2046).astype(np.uint64)
+    close = fam < 4   # exponents within 3 of each other
+    b = np.where(close, (b & ~(np.uint64(0x7FF) << np.uint64(52))) | (eb << np.uint64(52)), b)
+    b = np.where(fam == 4, (a & ~m) | ((a & m) ^ rng.integers(0, 256, n, dtype=np.uint64)), b)   # near-equal
+    b = np.where(fam == 5, b & ~np.uint64(0x3FF), b)                                             # halfway sums
+    few = ~np.uint64((1 << 26) - 1)
+    a = np.where(fam == 6, a & few, a)                                                           # halfway products
+    b = np.where(fam == 6, b & few, b)
+    b = np.where(fam == 7, rng.choice(np.array([0, 1 << 63], dtype=np.uint64), n), b)            # +-0
+    special = np.array([0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000000, 1, 0x000FFFFFFFFFFFFF,
+                        0x0010000000000000, 0x7FEFFFFFFFFFFFFF], dtype=np.uint64)
+    b = np.where(fam == 8, rng.choice(special, n), b)
+    a = a.view(np.float64)
+    b = b.view(np.float64)
+    return a, b
+
+
+@pytest.mark.parametrize("op", [3, 4])
+def test_integer_pipe_add_and_mul_are_ieee(op):
+    """add_i and mul_i (binary64 sum and product on the integer pipes) give the
+    IEEE round-to-nearest-even result bit for bit, specials included."""
+    n = 1 << 22
+    a, b = _bit_patterns(n, 100 + op)
+    if op == 4:   # products across the whole exponent range: rescale b so a * b spans it
+        rng = np.random.default_rng(7)
+        eb = (2046 - ((a.view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
+              + rng.integers(-40, 40, n))
+        bb = b.view(np.uint64)
+        keep = (rng.integers(0, 2, n) == 0) | ((bb >> np.uint64(52) & np.uint64(0x7FF)) == 0x7FF)
+        bb = np.where(keep, bb, (bb & ~(np.uint64(0x7FF) << np.uint64(52)))
+                      | (np.clip(eb, 1, 2046).astype(np.uint64) << np.uint64(52)))
+        b = bb.view(np.float64)
+    with np.errstate(all="ignore"):
+        ref = (a + b) if op == 3 else (a * b)
+    x, y = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty_like(x)
+    af.af_math_check(op, x, y, out)
+    got = out.cpu().numpy()
+    same = (got.view(np.uint64) == ref.view(np.uint64)) | (np.isnan(got) & np.isnan(ref))
+    bad = np.flatnonzero(~same)
+    assert bad.size == 0, [(a[k].hex(), b[k].hex(), got[k].hex(), ref[k].hex()) for k in bad[:5]]
+
+
+def test_integer_pipe_sqrt_is_dsqrt():
+    a, _ = _bit_patterns(1 << 20, 9)
+    a = np.abs(a)
+    x = torch.from_numpy(a).cuda()
+    o2, o5 = torch.empty_like(x), torch.empty_like(x)
+    af.af_math_check(2, x, None, o2)
+    af.af_math_check(5, x, None, o5)
+    assert torch.equal(o2.view(torch.int64), o5.view(torch.int64))
+
+
 @pytest.mark.parametrize("bc,nx,ny", [(ai.PERIODIC, 16, 12), (ai.OUTFLOW, 13, 9), (ai.PERIODIC, 37, 29)])
 def test_rhs_parity(bc, nx, ny):
     pb = ai.random_smooth(nx, ny, seed=21, amp=0.2, bc=bc)
