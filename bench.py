@@ -79,57 +79,62 @@ ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
 # Executed FP64 arithmetic per cell-stage of each stage kernel: DADD, DMUL and DFMA
 # thread instructions (ncu sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum)
 # of one captured step, divided by the cell-stages of that step.  Flops = DADD + DMUL +
-# 2 DFMA: the arithmetic the kernels execute, which is what the FP64 pipe is timed on.
-# The literal count of the paper's formulas (ALGO_FLOPS) is larger where a kernel uses
-# a cheaper algebraic form (the LLF-FVS line as one expression, products by 1/h), so it
-# is reported beside the roofline, never divided by the peak.  Each table names the
-# capture it comes from and a digest of the kernel sources it was taken on: once the
-# kernels change, the line says so ("counts_stale") until the capture is retaken.
-# The work-list kernels of the limiter slow paths are summed as k_points_slow and
-# k_cells_slow (the box and the Newton pass), the names af_timing reports them under.
+# 2 DFMA: the arithmetic the FP64 pipe executes, which is what the FP64 peak bounds.
+# The kernels run part of their binary64 products and sums on the integer pipes
+# (mul_i, sub_i: bitwise the IEEE results, no FP64 instruction); int_mul and int_add
+# count them per cell-stage, as the DMUL and DADD counts of the same captures taken on
+# the build that ran every product on the FP64 pipe (kernel digest e1110cc7...) minus
+# today's.  The literal count of the paper's formulas (ALGO_FLOPS) is larger where a
+# kernel uses a cheaper algebraic form (the LLF-FVS line as one expression, products
+# by 1/h), so it is reported beside the roofline, never divided by the peak.  Each
+# table names the capture it comes from and a digest of the kernel sources it was
+# taken on: once the kernels change, the line says so ("counts_stale") until the
+# capture is retaken.  The work-list kernels of the limiter slow paths are summed as
+# k_points_slow and k_cells_slow (the box and the Newton pass), the names af_timing
+# reports them under.
 EXEC_FP64 = {
-    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "e1110cc771517632678c3e5e8eda7fe7bfef77e9", "kernels": {
-        "k_pointdata": {"dadd": 88.03, "dmul": 142.11, "dfma": 237.18, "pipe": 481.33, "dram_bytes": 1147.6},
-        "k_points": {"dadd": 155.20, "dmul": 51.08, "dfma": 249.44, "pipe": 466.75, "dram_bytes": 1352.7},
-        "k_points_slow": {"dadd": 0.15, "dmul": 0.24, "dfma": 0.48, "pipe": 0.90, "dram_bytes": 1.9},
-        "k_faces": {"dadd": 60.10, "dmul": 50.03, "dfma": 68.42, "pipe": 191.55, "dram_bytes": 744.6},
-        "k_cells": {"dadd": 67.00, "dmul": 58.00, "dfma": 165.01, "pipe": 297.01, "dram_bytes": 715.1},
-        "k_cells_slow": {"dadd": 0.06, "dmul": 0.18, "dfma": 0.21, "pipe": 0.55, "dram_bytes": 0.8},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 329.4},
+    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
+        "k_pointdata": {"dadd": 93.04, "dmul": 18.02, "dfma": 242.19, "pipe": 357.23, "dram_bytes": 1115.4, "int_mul": 124.09, "int_add": 0.00},
+        "k_points": {"dadd": 155.22, "dmul": 11.02, "dfma": 249.44, "pipe": 425.68, "dram_bytes": 1498.4, "int_mul": 40.06, "int_add": 0.00},
+        "k_points_slow": {"dadd": 0.15, "dmul": 0.22, "dfma": 0.48, "pipe": 0.88, "dram_bytes": 1.9, "int_mul": 0.02, "int_add": 0.00},
+        "k_faces": {"dadd": 74.11, "dmul": 5.95, "dfma": 56.41, "pipe": 141.48, "dram_bytes": 744.1, "int_mul": 44.08, "int_add": 0.00},
+        "k_cells": {"dadd": 80.00, "dmul": 7.00, "dfma": 171.01, "pipe": 265.01, "dram_bytes": 1172.7, "int_mul": 51.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 0.06, "dmul": 0.18, "dfma": 0.21, "pipe": 0.55, "dram_bytes": 0.8, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 329.2, "int_mul": 8.33, "int_add": 16.00},
     }},
-    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "e1110cc771517632678c3e5e8eda7fe7bfef77e9", "kernels": {
-        "k_pointdata": {"dadd": 88.00, "dmul": 142.00, "dfma": 237.00, "pipe": 481.00, "dram_bytes": 970.4},
-        "k_points": {"dadd": 155.00, "dmul": 53.00, "dfma": 259.00, "pipe": 479.00, "dram_bytes": 1295.6},
-        "k_points_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2},
-        "k_faces": {"dadd": 60.00, "dmul": 46.00, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 634.6},
-        "k_cells": {"dadd": 67.00, "dmul": 58.00, "dfma": 165.00, "pipe": 297.00, "dram_bytes": 681.4},
-        "k_cells_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.3},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 277.7},
+    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
+        "k_pointdata": {"dadd": 93.00, "dmul": 18.00, "dfma": 242.00, "pipe": 357.00, "dram_bytes": 943.8, "int_mul": 124.00, "int_add": 0.00},
+        "k_points": {"dadd": 156.00, "dmul": 11.00, "dfma": 259.00, "pipe": 436.00, "dram_bytes": 1411.1, "int_mul": 42.00, "int_add": 0.00},
+        "k_points_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
+        "k_faces": {"dadd": 74.00, "dmul": 0.00, "dfma": 82.00, "pipe": 159.00, "dram_bytes": 637.1, "int_mul": 46.00, "int_add": 0.00},
+        "k_cells": {"dadd": 80.00, "dmul": 7.00, "dfma": 171.00, "pipe": 265.00, "dram_bytes": 1031.7, "int_mul": 51.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.3, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 277.4, "int_mul": 8.33, "int_add": 16.00},
     }},
-    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "e1110cc771517632678c3e5e8eda7fe7bfef77e9", "kernels": {
-        "k_pointdata": {"dadd": 88.04, "dmul": 142.14, "dfma": 237.22, "pipe": 481.40, "dram_bytes": 1124.8},
-        "k_points": {"dadd": 189.44, "dmul": 51.08, "dfma": 249.44, "pipe": 500.98, "dram_bytes": 1430.8},
-        "k_points_slow": {"dadd": 0.02, "dmul": 0.03, "dfma": 0.06, "pipe": 0.11, "dram_bytes": 0.2},
-        "k_faces": {"dadd": 69.11, "dmul": 50.10, "dfma": 68.17, "pipe": 200.48, "dram_bytes": 722.1},
-        "k_cells": {"dadd": 67.52, "dmul": 58.00, "dfma": 165.01, "pipe": 297.53, "dram_bytes": 713.6},
-        "k_cells_slow": {"dadd": 0.03, "dmul": 0.09, "dfma": 0.11, "pipe": 0.28, "dram_bytes": 0.1},
-        "k_final": {"dadd": 16.00, "dmul": 10.33, "dfma": 28.33, "pipe": 55.67, "dram_bytes": 322.0},
+    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
+        "k_pointdata": {"dadd": 93.05, "dmul": 18.01, "dfma": 242.23, "pipe": 357.27, "dram_bytes": 1094.3, "int_mul": 124.13, "int_add": 0.00},
+        "k_points": {"dadd": 189.44, "dmul": 11.94, "dfma": 249.44, "pipe": 460.84, "dram_bytes": 1625.3, "int_mul": 39.14, "int_add": 0.00},
+        "k_points_slow": {"dadd": 0.02, "dmul": 0.03, "dfma": 0.06, "pipe": 0.11, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
+        "k_faces": {"dadd": 83.13, "dmul": 6.02, "dfma": 56.16, "pipe": 150.39, "dram_bytes": 724.0, "int_mul": 44.08, "int_add": 0.00},
+        "k_cells": {"dadd": 80.52, "dmul": 7.00, "dfma": 171.01, "pipe": 265.53, "dram_bytes": 1135.7, "int_mul": 51.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 0.03, "dmul": 0.09, "dfma": 0.11, "pipe": 0.28, "dram_bytes": 0.1, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 321.9, "int_mul": 8.33, "int_add": 16.00},
     }},
-    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "e1110cc771517632678c3e5e8eda7fe7bfef77e9", "kernels": {
-        "k_pointdata": {"dadd": 88.50, "dmul": 144.24, "dfma": 241.10, "pipe": 488.30, "dram_bytes": 963.7},
-        "k_points": {"dadd": 155.00, "dmul": 50.81, "dfma": 256.81, "pipe": 474.15, "dram_bytes": 1351.4},
-        "k_points_slow": {"dadd": 53.51, "dmul": 87.80, "dfma": 172.99, "pipe": 325.86, "dram_bytes": 515.2},
-        "k_faces": {"dadd": 60.00, "dmul": 46.01, "dfma": 94.00, "pipe": 209.00, "dram_bytes": 635.2},
-        "k_cells": {"dadd": 68.36, "dmul": 59.59, "dfma": 173.16, "pipe": 308.52, "dram_bytes": 684.8},
-        "k_cells_slow": {"dadd": 44.31, "dmul": 58.33, "dfma": 240.91, "pipe": 358.32, "dram_bytes": 321.5},
-        "k_final": {"dadd": 13.14, "dmul": 13.19, "dfma": 31.19, "pipe": 58.51, "dram_bytes": 277.5},
+    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
+        "k_pointdata": {"dadd": 93.50, "dmul": 20.24, "dfma": 246.10, "pipe": 364.30, "dram_bytes": 940.1, "int_mul": 124.00, "int_add": 0.00},
+        "k_points": {"dadd": 156.00, "dmul": 11.00, "dfma": 256.81, "pipe": 433.34, "dram_bytes": 1474.0, "int_mul": 39.81, "int_add": 0.00},
+        "k_points_slow": {"dadd": 53.51, "dmul": 80.96, "dfma": 172.99, "pipe": 319.01, "dram_bytes": 507.1, "int_mul": 6.84, "int_add": 0.00},
+        "k_faces": {"dadd": 74.00, "dmul": 0.01, "dfma": 82.00, "pipe": 159.00, "dram_bytes": 637.2, "int_mul": 46.00, "int_add": 0.00},
+        "k_cells": {"dadd": 81.36, "dmul": 8.59, "dfma": 179.16, "pipe": 276.52, "dram_bytes": 1032.2, "int_mul": 51.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 44.31, "dmul": 58.33, "dfma": 240.91, "pipe": 358.34, "dram_bytes": 321.5, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 4.86, "dfma": 31.19, "pipe": 37.05, "dram_bytes": 277.8, "int_mul": 8.33, "int_add": 13.14},
     }},
-    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "cf38773d849495268e5d2d4031928735da0cca73", "kernels": {
-        "k1_pointdata": {"dadd": 29.00, "dmul": 90.00, "dfma": 147.00, "pipe": 274.00, "dram_bytes": 688.4},
-        "k1_points": {"dadd": 41.00, "dmul": 18.33, "dfma": 68.33, "pipe": 132.67, "dram_bytes": 430.9},
-        "k1_faces": {"dadd": 29.00, "dmul": 24.00, "dfma": 21.00, "pipe": 80.00, "dram_bytes": 359.2},
-        "k1_cells": {"dadd": 22.00, "dmul": 31.00, "dfma": 34.00, "pipe": 92.00, "dram_bytes": 290.5},
-        "k1_final": {"dadd": 0.00, "dmul": 17.33, "dfma": 28.33, "pipe": 48.67, "dram_bytes": 252.6},
+    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "34657efad9e053a3c26205343469505cf2570de2", "kernels": {
+        "k1_pointdata": {"dadd": 31.00, "dmul": 14.00, "dfma": 145.00, "pipe": 192.00, "dram_bytes": 667.6, "int_mul": 76.00, "int_add": 0.00},
+        "k1_points": {"dadd": 41.00, "dmul": 9.33, "dfma": 68.33, "pipe": 122.67, "dram_bytes": 430.6, "int_mul": 9.00, "int_add": 0.00},
+        "k1_faces": {"dadd": 30.00, "dmul": 20.00, "dfma": 21.00, "pipe": 75.00, "dram_bytes": 359.0, "int_mul": 4.00, "int_add": 0.00},
+        "k1_cells": {"dadd": 23.00, "dmul": 21.00, "dfma": 40.00, "pipe": 89.00, "dram_bytes": 290.5, "int_mul": 10.00, "int_add": 0.00},
+        "k1_final": {"dadd": 0.00, "dmul": 14.33, "dfma": 28.33, "pipe": 45.67, "dram_bytes": 252.6, "int_mul": 3.00, "int_add": 0.00},
     }},
 }
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
@@ -169,23 +174,28 @@ def kernel_digest(files=KERNEL_FILES_2D) -> str:
 
 
 def exec_flops(name: str):
-    """{kernel: executed FP64 flops per cell-stage} of a workload, its source and whether
-    the kernels changed since the capture (None when no capture covers the workload)."""
+    """{kernel: FP64-pipe flops per cell-stage}, {kernel: integer-pipe flops per
+    cell-stage}, the capture's source, and whether the kernels changed since the
+    capture (None, None, None when no capture covers the workload)."""
     t = EXEC_FP64.get(name)
     if t is None:
-        return None, None, None
+        return None, None, None, None
     fl = {k: v["dadd"] + v["dmul"] + 2.0 * v["dfma"] for k, v in t["kernels"].items()}
+    fi = {k: v.get("int_mul", 0.0) + v.get("int_add", 0.0) for k, v in t["kernels"].items()}
     files = KERNEL_FILES_1D if name == "blast1d" else KERNEL_FILES_2D
-    return fl, t["source"], kernel_digest(files) != t["digest"]
+    return fl, fi, t["source"], kernel_digest(files) != t["digest"]
 
 
 def fp64_roofline(name, ktimes, cells_per_launch, units_timed, ms_timed, peak, peak_src, probe, world=1):
     """Roofline of the dominant stage kernel and of the whole step on executed FP64 flops
-    (bound: the FP64 ALU pipe).  ktimes: {kernel: (total ms, launches)} of the timed region."""
+    (bound: the FP64 ALU pipe).  ktimes: {kernel: (total ms, launches)} of the timed region.
+    achieved / frac count the flops the FP64 pipe executed; work_* add the binary64
+    products and sums the kernels ran on the integer pipes (the same arithmetic, other
+    hardware), so work_frac may exceed the FP64 pipe's share of the peak."""
     lit = ALGO_FLOPS.get(name, {})
-    fl, src, stale = exec_flops(name)
+    fl, fi, src, stale = exec_flops(name)
     known = fl if fl is not None else lit
-    dom = max((k for k in ktimes if k in known), key=lambda k: ktimes[k][0])
+    dom = max((k for k in ktimes if k in known and k not in SIDE_STREAM_KERNELS), key=lambda k: ktimes[k][0])
     dom_ms, dom_n = ktimes[dom]
     avg_s = dom_ms / max(dom_n, 1) * 1e-3
     # shares of the library stream's serial time; a kernel on the second stream runs beside
@@ -204,15 +214,20 @@ def fp64_roofline(name, ktimes, cells_per_launch, units_timed, ms_timed, peak, p
         r.update({"achieved": None, "frac": None, "executed_counts": None})
         return r
     achieved = fl[dom] * cells_per_launch / avg_s * 1e-12
+    work = (fl[dom] + fi[dom]) * cells_per_launch / avg_s * 1e-12
     step_tf = sum(fl.values()) * units_timed / (ms_timed * 1e-3) * 1e-12 / world
+    step_work = (sum(fl.values()) + sum(fi.values())) * units_timed / (ms_timed * 1e-3) * 1e-12 / world
     pipe = EXEC_FP64[name]["kernels"][dom].get("pipe")
     if pipe is not None:   # FP64-pipe thread instructions per second against 2 per SM per cycle (= peak / 2 flops)
         r["fp64_pipe_busy"] = pipe * cells_per_launch / avg_s / (peak * 1e12 / 2.0)
     r.update({"achieved": achieved, "frac": achieved / peak, "frac_of_probe": achieved / probe if probe else None,
               "executed_flops_per_cell_stage": fl[dom], "executed_flops_per_cell_stage_all_kernels": sum(fl.values()),
+              "int_pipe_flops_per_cell_stage": fi[dom], "int_pipe_flops_per_cell_stage_all_kernels": sum(fi.values()),
+              "work_achieved": work, "work_frac": work / peak,
               "executed_counts": src, "counts_stale": stale,
               "step_achieved_tflops": step_tf, "step_frac": step_tf / peak,
-              "step_frac_of_probe": step_tf / probe if probe else None})
+              "step_frac_of_probe": step_tf / probe if probe else None,
+              "step_work_tflops": step_work, "step_work_frac": step_work / peak})
     return r
 
 
@@ -987,7 +1002,7 @@ def main():
     # ---------------- roofline of the dominant kernel -----------------------
     peak, peak_src = fp64_peak(torch, local, clk)
     roofline = fp64_roofline(pb.name, ktimes, cells, units, ms, peak, peak_src, peak_fp64, world)
-    fl, src, stale = exec_flops(pb.name)
+    _, _, src, stale = exec_flops(pb.name)
     dram = EXEC_FP64.get(pb.name, {}).get("kernels", {}).get(roofline["kernel"], {}).get("dram_bytes")
     roofline["traffic"] = dram * cells if dram is not None and not stale else None
     roofline["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per cell of the capture, "

@@ -74,7 +74,7 @@ __device__ __forceinline__ double qform(const double *U, double c) {
   double m2 = fma(U[1], U[1], fma(U[2], U[2], mul_i(U[3], U[3])));
   double b2 = fma(U[4], U[4], fma(U[5], U[5], mul_i(U[6], U[6])));
   double t = fma(0.5, b2, c);
-  return fma(-U[0], t, fma(U[0], U[7], ldexp_i<-1>(-m2)));
+  return fma(-U[0], t, fma(U[0], U[7], ldexp_i<-1>(neg_i(m2))));
 }
 // rho >= 1e-13 and p >= 1e-13 (so every limiter of Sec. 3 leaves the state alone)
 __device__ __forceinline__ bool clear_of_floor(const double *U, const AfGrid &g) {
@@ -289,27 +289,33 @@ __device__ __forceinline__ void b_pointdata(const AfDev &d, const AfGrid &g, con
   double m1 = 0.0, m2 = 0.0;
   bool clim = false;
   if (i < g.nxa && j < g.nya) {
+    // the five points of index (i, j) -- x-face, y-face, corner, cell average, cell
+    // centre -- through one instance of point_data (one copy of its code)
+    double A[8];
 #pragma unroll 1
-    for (int c = 1; c <= 3; ++c) {
-      if (i < g.ex[c] && j < g.ey[c]) {
-        double U[8], s1, s2;
+    for (int c = 1; c <= 5; ++c) {
+      double U[8];
+      if (c <= 3) {
+        if (!(i < g.ex[c] && j < g.ey[c])) continue;
         load8(sview(d.us[c], g, c), i, j, U);
-        point_data(U, g, d.pd[c] + o, PS, false, s1, s2);
+      } else {
+        if (!(i < g.nx && j < g.ny)) break;
+        if (c == 4) {
+          load8(sview(d.us[0], g, 0), i, j, A);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) U[k] = A[k];
+        } else {
+          clim = centre_value(d, g, i, j, A, U);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) d.uc[k * PS + o] = U[k];
+        }
+      }
+      double s1, s2;
+      point_data(U, g, d.pd[c == 5 ? 4 : (c == 4 ? 0 : c)] + o, PS, c == 4, s1, s2);
+      if (c <= 4) {   // the centre is not a DoF: not in the time-step bound
         m1 = maxnn(m1, s1);
         m2 = maxnn(m2, s2);
       }
-    }
-    if (i < g.nx && j < g.ny) {
-      double A[8], s1, s2;
-      load8(sview(d.us[0], g, 0), i, j, A);
-      point_data(A, g, d.pd[0] + o, PS, true, s1, s2);
-      m1 = maxnn(m1, s1);
-      m2 = maxnn(m2, s2);
-      double uc[8];
-      clim = centre_value(d, g, i, j, A, uc);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) d.uc[k * PS + o] = uc[k];
-      point_data(uc, g, d.pd[4] + o, PS, false, s1, s2);
     }
   }
   count(d.st, ST_CENTER_LIMITED, clim);
@@ -888,7 +894,7 @@ __device__ __forceinline__ void face(const AfDev &d, const AfGrid &g, double *ou
       Fh = mul_i(fma(4.0, pw(mid, PS, g.nxa, s), pw(lo, PS, g.nxa, s) + pw(hi, PS, g.nxa, s)), 1.0 / 6.0);
       if (llf) Fl = ldexp_i<-1>(fma(-al, Ub(cbi, cbj, k) - Ub(cai, caj, k), A(cai, caj, s) + A(cbi, cbj, s)));
     } else if (llf) {
-      Fl = mul_i(ldexp_i<-1>(-al), Ub(cbi, cbj, k) - Ub(cai, caj, k));
+      Fl = mul_i(ldexp_i<-1>(neg_i(al)), Ub(cbi, cbj, k) - Ub(cai, caj, k));
     }
     out[(QF_FLLF + k) * PS] = Fl;
     out[(QF_G + k) * PS] = is_one(ts) ? Fh - Fl : mul_i(ts, Fh - Fl);
@@ -1026,7 +1032,7 @@ __device__ __forceinline__ bool box_certified(const double *L1, const double *D,
   const double rho = L1[0], E = L1[7];
   const double bb = fma(L1[4], L1[4], fma(L1[5], L1[5], mul_i(L1[6], L1[6])));
   const double mm = fma(L1[1], L1[1], fma(L1[2], L1[2], mul_i(L1[3], L1[3])));
-  const double q0 = fma(rho, E, ldexp_i<-1>(-mm)) - rho * fma(0.5, bb, g.c13);
+  const double q0 = fma(rho, E, ldexp_i<-1>(neg_i(mm))) - rho * fma(0.5, bb, g.c13);
   const double bD = fma(absd(L1[4]), D[4], fma(absd(L1[5]), D[5], mul_i(absd(L1[6]), D[6])));
   const double mD = fma(absd(L1[1]), D[1], fma(absd(L1[2]), D[2], mul_i(absd(L1[3]), D[3])));
   const double DB2 = fma(D[4], D[4], fma(D[5], D[5], mul_i(D[6], D[6])));
@@ -1346,8 +1352,8 @@ __device__ __forceinline__ void limited_value(const AfDev &d, const AfGrid &g, i
     const double gl = FX(i, j, QF_G + k), gr = FX(ip, j, QF_G + k), gd = FY(i, j, QF_G + k), gu = FY(i, jp, QF_G + k);
     double tx, ty;
     if (ones) {
-      tx = gl - gr;
-      ty = gd - gu;
+      tx = sub_i(gl, gr);
+      ty = sub_i(gd, gu);
     } else {
       tx = fma(-th[1], gr, th[0] * gl);
       ty = fma(-th[3], gu, th[2] * gd);
@@ -1697,7 +1703,36 @@ __device__ __forceinline__ void b_cells_newton(const AfDev &d, const AfGrid &g) 
     call;                                                         \
   }
 
-__global__ void __launch_bounds__(128) k_pointdata(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+// Launch bounds of the stage kernels (128 threads): a kernel given AF_MINB_x
+// resident blocks per SM is capped at 65536 / (128 x blocks) registers; without
+// it ptxas picks the count.  The kernels keep the FP64 pipe and the integer
+// pipes busy at once; the defaults are the fastest of a sweep on the 2048x2048
+// blast (point data and point pass at 5 blocks = 96 registers, cell pass at
+// 5 = 96; faces and final pass at the compiler's count).
+#define AF_LB(minb) __launch_bounds__(128, minb)
+#ifndef AF_MINB_PD
+#define AF_MINB_PD 5
+#endif
+#define AF_LB_PD AF_LB(AF_MINB_PD)
+#ifndef AF_MINB_PT
+#define AF_MINB_PT 5
+#endif
+#define AF_LB_PT AF_LB(AF_MINB_PT)
+#ifdef AF_MINB_FC
+#define AF_LB_FC AF_LB(AF_MINB_FC)
+#else
+#define AF_LB_FC __launch_bounds__(128)
+#endif
+#ifndef AF_MINB_CL
+#define AF_MINB_CL 5
+#endif
+#define AF_LB_CL AF_LB(AF_MINB_CL)
+#ifdef AF_MINB_FN
+#define AF_LB_FN AF_LB(AF_MINB_FN)
+#else
+#define AF_LB_FN __launch_bounds__(128)
+#endif
+__global__ void AF_LB_PD k_pointdata(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                    int reduce_dt) {
   // a stage's first pass: the work lists of its point and cell passes start empty
   if (d.pq && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
@@ -1723,7 +1758,7 @@ __global__ void kb_dt(const AfRun *__restrict__ runs, int nruns) {
 // UP: the velocity-upwind point source (Example 4.2 variant) is compiled in
 // only where it is asked for; the central scheme pays nothing for it.
 template <bool GB, bool UP>
-__global__ void __launch_bounds__(128, 4) k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+__global__ void AF_LB_PT k_points(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                 double a, double b, int mode) {
   if (GB && interior_block(g.nx, g.ny)) b_points<false, UP>(d, g, AF_IJ, a, b, mode);
   else b_points<GB, UP>(d, g, AF_IJ, a, b, mode);
@@ -1734,7 +1769,7 @@ __global__ void __launch_bounds__(256, 2) kb_points(const AfRun *__restrict__ ru
   AF_BATCH_LOOP((b_points<false, UP>(r->d, r->g, i, j, a, b, 0)));
 }
 template <bool GB>
-__global__ void __launch_bounds__(128) k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+__global__ void AF_LB_FC k_faces(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                int mode) {
   if (GB && interior_block(g.nx, g.ny)) b_faces<false>(d, g, AF_IJ, mode);
   else b_faces<GB>(d, g, AF_IJ, mode);
@@ -1744,7 +1779,7 @@ __global__ void __launch_bounds__(256) kb_faces(const AfRun *__restrict__ runs, 
   AF_BATCH_LOOP(b_faces<false>(r->d, r->g, i, j, 0));
 }
 template <bool GB>
-__global__ void __launch_bounds__(128) k_cells(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+__global__ void AF_LB_CL k_cells(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                double a, double b, int mode) {
   if (GB && interior_block(g.nx, g.ny)) b_cells<false>(d, g, AF_IJ, a, b, mode);
   else b_cells<GB>(d, g, AF_IJ, a, b, mode);
@@ -1753,7 +1788,7 @@ __global__ void __launch_bounds__(256, 2) kb_cells(const AfRun *__restrict__ run
                                                 int nitems, double a, double b) {
   AF_BATCH_LOOP(b_cells<false>(r->d, r->g, i, j, a, b, 0));
 }
-__global__ void __launch_bounds__(128) k_final(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+__global__ void AF_LB_FN k_final(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                                double a, double b) {
   b_final(d, g, AF_IJ, a, b);
 }

@@ -215,6 +215,9 @@ __device__ __forceinline__ double mul_i(double a, double b) {
   return from_bits(r);
 }
 
+// -x on the integer pipe
+__device__ __forceinline__ double neg_i(double x) { return from_bits(bits(x) ^ 0x8000000000000000ULL); }
+
 // x * 2^K for a small constant K (an exact scaling): the exponent field moved by
 // K on the integer pipes when x and the result are normal, +-0 kept, the rest
 // (infinities, NaN, subnormal operand or result) by the FP64 product.
@@ -262,5 +265,8 @@ __device__ __forceinline__ double add_i(double a, double b) {
   r = (X == 0) ? (ia & ib) : r;           // +-0 + +-0: -0 only for -0 + -0
   return from_bits(r);
 }
+
+// a - b on the integer pipes
+__device__ __forceinline__ double sub_i(double a, double b) { return add_i(a, neg_i(b)); }
 
 }  // namespace afm
