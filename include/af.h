@@ -337,10 +337,9 @@ void af_destroy(af_ctx *ctx);
 /* Diagnostic: n results of the FP64 helpers the kernels use, on device
  * arrays, in stream order: op 0 out = 1/x, op 1 out = x/y, op 2 out = sqrt(x),
  * op 3 out = x + y and op 4 out = x * y on the integer pipes (bitwise the IEEE
- * round-to-nearest sum and product), op 5 out = sqrt(x) with its first product
- * on the integer pipes (bitwise op 2).  y is read by ops 1, 3 and 4 only.  Used
+ * round-to-nearest sum and product).  y is read by ops 1, 3 and 4 only.  Used
  * by the tests to bound the helpers' error against the CUDA operators.
- * AF_EINVAL for an op outside 0..5 or a null x or out. */
+ * AF_EINVAL for an op outside 0..4 or a null x or out (or y where it is read). */
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
 
 /* ---- Batched ensembles (not in the paper: many independent runs at once) ----

@@ -123,13 +123,13 @@ __device__ __forceinline__ void point_data(const double *U, const AfGrid &g, dou
   // eq. (cf)
   const double c2 = mul_i(mul_i(g.gamma, p), r);
   const double a = fma(BB, r, c2);
-  const double k4 = 4.0 * mul_i(c2, r);
-  const double aa = mul_i(a, a), ha = 0.5 * a;
+  const double k4 = ldexp_i<2>(mul_i(c2, r));
+  const double aa = mul_i(a, a), ha = ldexp_i<-1>(a);
   double d1 = fma(-k4, b1s, aa), d2 = fma(-k4, b2s, aa);
   d1 = gt_zero(d1) ? d1 : 0.0;
   d2 = gt_zero(d2) ? d2 : 0.0;
-  const double cf1 = dsqrt_i(fma(0.5, dsqrt_i(d1), ha));
-  const double cf2 = dsqrt_i(fma(0.5, dsqrt_i(d2), ha));
+  const double cf1 = dsqrt(fma(0.5, dsqrt(d1), ha));
+  const double cf2 = dsqrt(fma(0.5, dsqrt(d2), ha));
   sr1 = absd(v1) + cf1;
   sr2 = absd(v2) + cf2;
 #pragma unroll
@@ -144,7 +144,7 @@ __device__ __forceinline__ void point_data(const double *U, const AfGrid &g, dou
     out[QA_CF1 * PS] = cf1;
     out[QA_CF2 * PS] = cf2;
     out[QA_PT * PS] = pt;
-    out[QA_SRHO * PS] = dsqrt_i(rho);
+    out[QA_SRHO * PS] = dsqrt(rho);
   } else {
     out[QP_SR1 * PS] = sr1;
     out[QP_SR2 * PS] = sr2;
@@ -208,7 +208,7 @@ __device__ __forceinline__ double alpha_llf(double va, double vb, double cfa, do
   const double rden = rcp(sra + srb);
   const double roe = mul_i(absd(fma(sra, va, mul_i(srb, vb))), rden);
   const double d0 = Ba[0] - Bb[0], d1 = Ba[1] - Bb[1], d2 = Ba[2] - Bb[2];
-  const double nb = dsqrt_i(fma(d0, d0, fma(d1, d1, mul_i(d2, d2))));
+  const double nb = dsqrt(fma(d0, d0, fma(d1, d1, mul_i(d2, d2))));
   const double mv = maxnn(maxnn(absd(va), absd(vb)), roe);
   return mv + maxnn(cfa, cfb) + nb * rden;
 }
@@ -259,7 +259,7 @@ __device__ __forceinline__ bool centre_value(const AfDev &d, const AfGrid &g, in
   for (int k = 0; k < 8; ++k) {
     const double faces = (X(i, j, k) + X(ip, j, k)) + (Y(i, j, k) + Y(i, jp, k));
     const double corners = (C(i, j, k) + C(ip, j, k)) + (C(i, jp, k) + C(ip, jp, k));
-    uc[k] = fma(2.25, A[k], fma(-0.25, faces, -0.0625 * corners));
+    uc[k] = fma(2.25, A[k], fma(-0.25, faces, ldexp_i<-4>(neg_i(corners))));
   }
   const size_t PS = (size_t)g.nxa * g.nya, o = (size_t)j * g.nxa + i;
   double t1 = 1.0, t2 = 1.0;
@@ -668,20 +668,20 @@ __device__ void sensor_phi(const AfDev &d, const AfGrid &g, int ci, int cj, doub
   const double ptc = A(ci, cj, QA_PT), pte = A(e, cj, QA_PT), ptw = A(w, cj, QA_PT);
   const double ptn = A(ci, n, QA_PT), pts = A(ci, s, QA_PT);
   const double sx = pte + ptw, sy = ptn + pts;
-  phi[0] = ddiv_i(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
-  phi[1] = ddiv_i(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
+  phi[0] = ddiv(absd(fma(-2.0, ptc, sx)), absd(fma(2.0, ptc, sx)));
+  phi[1] = ddiv(absd(fma(-2.0, ptc, sy)), absd(fma(2.0, ptc, sy)));
   const double hx = 0.5 * g.rdx, hy = 0.5 * g.rdy;
   const double divv = fma(A(e, cj, QA_V1) - A(w, cj, QA_V1), hx, mul_i(A(ci, n, QA_V2) - A(ci, s, QA_V2), hy));
   const double curl = fma(A(e, cj, QA_V2) - A(w, cj, QA_V2), hx, -mul_i(A(ci, n, QA_V1) - A(ci, s, QA_V1), hy));
   if (is_zero(divv)) {   // -0 / den gives 0: no square root or quotient needed
     phi[2] = 0.0;
   } else {
-    const double den = dsqrt_i(fma(divv, divv, fma(curl, curl, 1e-40)));
-    const double ph2 = ddiv_i(-divv, den);
+    const double den = dsqrt(fma(divv, divv, fma(curl, curl, 1e-40)));
+    const double ph2 = ddiv(-divv, den);
     phi[2] = gt_zero(ph2) ? ph2 : 0.0;
   }
   const double num = (Ub(e, cj, 4) - Ub(w, cj, 4)) + (Ub(ci, n, 5) - Ub(ci, s, 5));
-  phi[3] = ddiv_i(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
+  phi[3] = ddiv(absd(num), absd(Ub(ci, cj, 4) + Ub(ci, cj, 5)) + 1e-40);
 }
 
 template <bool GB, bool UP>
@@ -689,8 +689,8 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
                                          int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const double dt = mode == 1 ? 1.0 : d.sc->dt;
-  const double cx = 0.5 * dt * g.rdx, cy = 0.5 * dt * g.rdy;   // the FVS lines carry a factor 1/2
-  const double cxc = dt * g.rdx, cyc = dt * g.rdy;             // central differences
+  const double cxc = mul_i(dt, g.rdx), cyc = mul_i(dt, g.rdy);   // central differences
+  const double cx = ldexp_i<-1>(cxc), cy = ldexp_i<-1>(cyc);      // the FVS lines carry a factor 1/2
   int nlim = 0, nshr = 0, nbad = 0;
   if (i < g.nxa && j < g.nya) {
     const int im = mface(i - 1, g.nx, g.bc), ip = mface(i + 1, g.nx, g.bc);
@@ -714,19 +714,19 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
                              prefg(d, g, 3, i, j + 1)};
           fvs_line_g<0>(Px, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
           fvs_line_g<1>(Py, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-          divB = fma(dBx, 0.5 * g.rdx, dBy * (0.5 * g.rdy));
+          divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, 0.5 * g.rdy));
         } else if (cls == 1) {
           const PPG Px[5] = {prefg(d, g, 1, i - 1, j), prefg(d, g, 4, i - 1, j), mg, prefg(d, g, 4, i, j),
                              prefg(d, g, 1, i + 1, j)};
           fvs_line_g<0>(Px, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
           central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
-          divB = fma(dBx, 0.5 * g.rdx, dBy * g.rdy);
+          divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, g.rdy));
         } else {
           central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
           const PPG Py[5] = {prefg(d, g, 2, i, j - 1), prefg(d, g, 4, i, j - 1), mg, prefg(d, g, 4, i, j),
                              prefg(d, g, 2, i, j + 1)};
           fvs_line_g<1>(Py, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-          divB = fma(dBx, g.rdx, dBy * (0.5 * g.rdy));
+          divB = fma(dBx, g.rdx, mul_i(dBy, 0.5 * g.rdy));
         }
       } else if (cls == 3) {
         const PP Px[5] = {pref(d, g, 3, im, j), pref(d, g, 2, ci0, j), me, pref(d, g, 2, ci1, j), pref(d, g, 3, ip, j)};
@@ -1175,7 +1175,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
     const SV Ub = sview(d.us[0], g, 0);
     const WV A = wview(d.pd[0], g);
     const WV FX = wview(d.fx, g), FY = wview(d.fy, g);
-    const double cxf = dt * g.rdx, cyf = dt * g.rdy;
+    const double cxf = mul_i(dt, g.rdx), cyf = mul_i(dt, g.rdy);
     double *uo = d.uo[0];
     const size_t cs0 = (size_t)g.nx * g.ny, o0 = (size_t)j * g.nx + i;
     if (mode == 1) {
@@ -1247,7 +1247,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         // Lemma 3.1 CFL condition (diagnostic count only)
         {
           const double lhs = mul_i(dt, (FX(i, j, QF_AL) + FX(ip, j, QF_AL)) * g.rdx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) * g.rdy +
-                                   ddiv_i(absd(divBb), A(i, j, QA_SRHO)));
+                                   ddiv(absd(divBb), A(i, j, QA_SRHO)));
           ncfl += lhs > 1.0 + 1e-12;
         }
         const double dtts = mul_i(dt, tsc);
@@ -1345,7 +1345,7 @@ __device__ __forceinline__ void limited_value(const AfDev &d, const AfGrid &g, i
                                               double *out) {
   const WV FX = wview(d.fx, g), FY = wview(d.fy, g), L1 = wview(d.lim1, g);
   const int ip = mface(i + 1, g.nx, g.bc), jp = mface(j + 1, g.ny, g.bc);
-  const double cxf = dt * g.rdx, cyf = dt * g.rdy;
+  const double cxf = mul_i(dt, g.rdx), cyf = mul_i(dt, g.rdy);
   const bool ones = is_one(th[0]) && is_one(th[1]) && is_one(th[2]) && is_one(th[3]);
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -1834,8 +1834,7 @@ __global__ void k_math_check(int op, const double *x, const double *y, double *o
   else if (op == 1) out[t] = ddiv(x[t], y[t]);
   else if (op == 2) out[t] = dsqrt(x[t]);
   else if (op == 3) out[t] = add_i(x[t], y[t]);
-  else if (op == 4) out[t] = mul_i(x[t], y[t]);
-  else out[t] = dsqrt_i(x[t]);
+  else out[t] = mul_i(x[t], y[t]);
 }
 
 // FP64 FMA throughput probe: 8 independent register chains per thread.

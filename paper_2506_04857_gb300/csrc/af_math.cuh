@@ -76,7 +76,7 @@ __device__ __forceinline__ float rsqrt_approx_f32(float x) {
 }
 
 // 1/x: two Newton steps y <- y + y (1 - x y) from the FP32 seed.
-__device__ __forceinline__ double rcp(double x) {
+__device__ __forceinline__ double rcp_nr2(double x) {
   if (!seed_ok(x)) return 1.0 / x;
   double y = widen_f32(rcp_approx_f32(seed_f32(x)));
   double e = fma(-x, y, 1.0);
@@ -86,7 +86,7 @@ __device__ __forceinline__ double rcp(double x) {
 }
 
 // a/b: one Newton step on the seed, then one residual correction of the quotient.
-__device__ __forceinline__ double ddiv(double a, double b) {
+__device__ __forceinline__ double ddiv_nr(double a, double b) {
   if (!seed_ok(b)) return a / b;
   double y = widen_f32(rcp_approx_f32(seed_f32(b)));
   double e = fma(-b, y, 1.0);
@@ -98,7 +98,7 @@ __device__ __forceinline__ double ddiv(double a, double b) {
 
 // sqrt(x): s = x * rsqrt-seed, then two Heron corrections s <- s + (x - s^2)/(2 s)
 // with 1/(2 s) taken from the seed.
-__device__ __forceinline__ double dsqrt(double x) {
+__device__ __forceinline__ double dsqrt_nr2(double x) {
   if (!seed_ok(x)) return is_zero(x) ? x : sqrt(x);   // sqrt(+-0) = +-0
   float yf = rsqrt_approx_f32(seed_f32(x));
   double y = widen_f32(yf), h = widen_f32(0.5f * yf);
@@ -109,28 +109,88 @@ __device__ __forceinline__ double dsqrt(double x) {
   return fma(r, h, s);
 }
 
-// dsqrt with its first product on the integer pipes (bitwise dsqrt)
-__device__ __forceinline__ double mul_i(double a, double b);
-__device__ __forceinline__ double dsqrt_i(double x) {
-  if (!seed_ok(x)) return is_zero(x) ? x : sqrt(x);
-  float yf = rsqrt_approx_f32(seed_f32(x));
-  double y = widen_f32(yf), h = widen_f32(0.5f * yf);
-  double s = mul_i(x, y);
-  double r = fma(-s, s, x);
-  s = fma(r, h, s);
-  r = fma(-s, s, x);
-  return fma(r, h, s);
+// ---- seeds refined once in FP32 ------------------------------------------
+// A double x is split into two floats, xh (its leading 24 significand bits) and xl
+// (the next 24, truncated): |x - xh - xl| < 2^-47 |x|.  One Newton (or Heron) step
+// taken in FP32 on the pair carries the FP32 seed from about 23 to about 44 bits;
+// one FP64 step then leaves the result within one ulp (its error is the square of
+// 2^-44 plus the final rounding), so a reciprocal, quotient or square root costs
+// two FP64 instructions instead of four.  Valid for 2^-63 <= |x| < 2^78, where
+// every float involved is normal; elsewhere the two-step forms above.
+__device__ __forceinline__ bool split_f32(double x, float &xh, float &xl) {
+  const unsigned long long b = bits(x);
+  const unsigned hi = (unsigned)(b >> 32), e = (hi >> 20) & 0x7ffu;
+  if (e - 960u > 140u) return false;
+  xh = seed_f32(x);
+  // the 29 significand bits below xh, times 2^(e - 1075) (an exact power of two)
+  const float scale = __uint_as_float(((e - 948u) << 23) | (hi & 0x80000000u));
+  xl = __uint2float_rn((unsigned)b & 0x1fffffffu) * scale;
+  return true;
+}
+// y + c as a double for floats with |c| <= 2^-20 |y|, y normal: the significand of
+// c aligned to that of y and added as an integer (bits of c below 2^-52 |y| are
+// dropped, which the FP64 step that follows absorbs).
+__device__ __forceinline__ double join_f32(float y, float c) {
+  const unsigned a = __float_as_uint(y), bc = __float_as_uint(c);
+  const unsigned ea = (a >> 23) & 0xffu, eb = (bc >> 23) & 0xffu;
+  unsigned long long M = (unsigned long long)((a & 0x7fffffu) | 0x800000u) << 29;   // leading one at bit 52
+  const unsigned sh = ea - eb;                                                        // c's at bit 52 - sh
+  const unsigned long long mc0 = (unsigned long long)((bc & 0x7fffffu) | 0x800000u);
+  unsigned long long mc = sh <= 29u ? (mc0 << (29u - sh)) : (sh < 53u ? (mc0 >> (sh - 29u)) : 0ULL);
+  mc = eb == 0u ? 0ULL : mc;
+  M = ((a ^ bc) >> 31) ? M - mc : M + mc;
+  unsigned e = ea;
+  if (M >> 53) {
+    M >>= 1;
+    ++e;
+  } else if (!(M >> 52)) {
+    M <<= 1;
+    --e;
+  }
+  return from_bits(((unsigned long long)(a >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                   (M & 0x000fffffffffffffULL));
+}
+// 1/x to about 44 bits: y0 + y0 (1 - x y0) in FP32 on the split of x
+__device__ __forceinline__ double rcp44(float xh, float xl) {
+  const float y0 = rcp_approx_f32(xh);
+  const float e1 = fmaf(-xl, y0, fmaf(-xh, y0, 1.0f));
+  return join_f32(y0, e1 * y0);
 }
 
-// ddiv with its quotient product on the integer pipes (bitwise ddiv)
-__device__ __forceinline__ double ddiv_i(double a, double b) {
-  if (!seed_ok(b)) return a / b;
-  double y = widen_f32(rcp_approx_f32(seed_f32(b)));
-  double e = fma(-b, y, 1.0);
-  y = fma(y, e, y);
-  double q = mul_i(a, y);
-  double r = fma(-b, q, a);
+__device__ __forceinline__ double mul_i(double a, double b);
+
+// 1/x: the 44-bit reciprocal and one FP64 Newton step
+__device__ __forceinline__ double rcp(double x) {
+  float xh, xl;
+  if (!split_f32(x, xh, xl)) return rcp_nr2(x);
+  const double y = rcp44(xh, xl);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+// a/b: q = a y with the 44-bit reciprocal y of b (product on the integer pipes),
+// then one residual correction
+__device__ __forceinline__ double ddiv(double a, double b) {
+  float bh, bl;
+  if (!split_f32(b, bh, bl)) return ddiv_nr(a, b);
+  const double y = rcp44(bh, bl);
+  const double q = mul_i(a, y);
+  const double r = fma(-b, q, a);
   return fma(r, y, q);
+}
+
+// sqrt(x), x > 0 in range: s0 = xh / sqrt(xh) from the rsqrt seed, one Heron step
+// s0 + (x - s0^2) / (2 s0) in FP32 on the split, one FP64 Heron step (1/(2 s) from
+// the seed)
+__device__ __forceinline__ double dsqrt(double x) {
+  float xh, xl;
+  if ((long long)bits(x) <= 0 || !split_f32(x, xh, xl)) return dsqrt_nr2(x);
+  const float r0 = rsqrt_approx_f32(xh);
+  const float s0 = xh * r0, h0 = 0.5f * r0;
+  const float d = fmaf(-s0, s0, xh) + xl;
+  const double s = join_f32(s0, d * h0);
+  const double r = fma(-s, s, x);
+  return fma(r, widen_f32(h0), s);
 }
 
 // max/min of non-negative, non-NaN doubles via their bit patterns
