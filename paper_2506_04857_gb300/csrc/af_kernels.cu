@@ -78,7 +78,7 @@ __device__ __forceinline__ double qform(const double *U, double c) {
 }
 // rho >= 1e-13 and p >= 1e-13 (so every limiter of Sec. 3 leaves the state alone)
 __device__ __forceinline__ bool clear_of_floor(const double *U, const AfGrid &g) {
-  return U[0] >= 1e-13 && qform(U, g.c13) >= 0.0;
+  return ge_pos(U[0], 1e-13) && ge_zero(qform(U, g.c13));
 }
 __device__ __forceinline__ bool in_G(const double *U, double gm1) {
   for (int k = 0; k < 8; ++k)
@@ -280,7 +280,7 @@ __device__ __forceinline__ bool centre_value(const AfDev &d, const AfGrid &g, in
     d.rec[AFC_C1 * PS + o] = t1;
     d.rec[AFC_C2 * PS + o] = t2;
   }
-  return t1 < 1.0 || t2 < 1.0;
+  return lt_one(t1) || lt_one(t2);   // theta in [0, 1]
 }
 
 __device__ __forceinline__ void b_pointdata(const AfDev &d, const AfGrid &g, const int i, const int j, int reduce_dt) {
@@ -799,7 +799,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
           d.rec[s1 + PS] = t2;
         }
       }
-      if (a == 0.0) {
+      if (is_zero(a)) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) uo[k * cs + oo] = acc[k];
       } else {
@@ -808,7 +808,7 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
         for (int k = 0; k < 8; ++k) uo[k * cs + oo] = fma(a, __ldg(un + k * cs + oo), mul_i(b, acc[k]));
       }
     }
-    if (mode != 1 && i < g.nx && j < g.ny && g.kappa != 0.0) {
+    if (mode != 1 && i < g.nx && j < g.ny && !is_zero(g.kappa)) {
       double phi[4];
       sensor_phi<GB>(d, g, i, j, phi);
       const size_t o = (size_t)j * g.nxa + i;
@@ -847,7 +847,7 @@ __device__ __forceinline__ void get_phi(const AfDev &d, const AfGrid &g, int ci,
 // theta^s = exp(-kappa [phi_1 phi_2 + phi_3]) with each phi maxed over the two cells
 template <bool GB>
 __device__ __forceinline__ double theta_s(const AfDev &d, const AfGrid &g, int dir, int ia, int ja, int ib, int jb) {
-  if (g.kappa == 0.0) return 1.0;
+  if (is_zero(g.kappa)) return 1.0;
   double pa[4], pb[4];
   get_phi<GB>(d, g, ia, ja, pa);
   get_phi<GB>(d, g, ib, jb, pb);
@@ -908,7 +908,7 @@ template <bool GB>
 __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const int i, const int j, int mode) {
   const size_t PS = (size_t)g.nxa * g.nya;
   const size_t o = (size_t)j * g.nxa + i;
-  const bool llf = mode == 0 && (g.pp_on || g.kappa != 0.0);
+  const bool llf = mode == 0 && (g.pp_on || !is_zero(g.kappa));
   const bool sens = mode != 1;   // theta^s for stages (mode 0) and af_sensor (mode 2)
   int nsens = 0;
   if (i < g.nxa && j < g.nya) {
@@ -941,7 +941,7 @@ __device__ __forceinline__ void b_faces(const AfDev &d, const AfGrid &g, const i
                        mcell(j - 1, g.ny, g.bc), i, mcell(j, g.ny, g.bc), ts, llf, nsens);
     }
   }
-  if (sens && g.kappa != 0.0) {
+  if (sens && !is_zero(g.kappa)) {
     const unsigned act = __activemask();
     const int tot = __reduce_add_sync(act, nsens);
     if (tot && (threadIdx.x & 31) == (__ffs(act) - 1)) atomicAdd(&d.st->cnt[ST_SENSOR_LT099], (unsigned long long)tot);
@@ -1044,7 +1044,7 @@ __device__ __forceinline__ bool box_certified(const double *L1, const double *D,
   const double T = T1 + T2 + T3;
   const double scale = fma(rho, absd(E), fma(0.5, mm, fma(hrho, bb, T)));
   // density rectangle: Lambda^rho = 1 when rho(L1) - 1e-13 >= 1e-12 + sum |rho(H)|
-  return (q0 - T >= 1e-12 * scale) && (rho - 1e-13 >= (1e-12 + D[0]) * (1.0 + 1e-10));
+  return ge_i(q0 - T, mul_i(1e-12, scale)) && ge_i(rho - 1e-13, mul_i(1e-12 + D[0], 1.0 + 1e-10));
 }
 
 // Sec. 3.2 step (1) for one cell: theta_ij and Lim1, with the floors eps_rho, eps_p.
@@ -1248,7 +1248,7 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
         {
           const double lhs = mul_i(dt, (FX(i, j, QF_AL) + FX(ip, j, QF_AL)) * g.rdx + (FY(i, j, QF_AL) + FY(i, jp, QF_AL)) * g.rdy +
                                    ddiv(absd(divBb), A(i, j, QA_SRHO)));
-          ncfl += lhs > 1.0 + 1e-12;
+          ncfl += gt_pos(lhs, 1.0 + 1e-12);
         }
         const double dtts = mul_i(dt, tsc);
         double L1[8], Lam[4];
@@ -1260,11 +1260,11 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           Lam[0] = Lam[1] = Lam[2] = Lam[3] = 1.0;
           nsrc += th_src < 1.0;
         }
-        bool fast = !d.frz && Ullf[0] >= 1e-13 && qform(Ullf, g.c13) >= 0.0;
+        bool fast = !d.frz && ge_pos(Ullf[0], 1e-13) && ge_zero(qform(Ullf, g.c13));
         if (fast) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) L1[k] = fma(-dtts, dS[k], Ullf[k]);
-          fast = L1[0] >= 1e-13 && qform(L1, g.c13) >= 0.0;
+          fast = ge_pos(L1[0], 1e-13) && ge_zero(qform(L1, g.c13));
         }
         if (fast) {
           double D[8];
@@ -1411,7 +1411,7 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
       else atomicOr(&d.st->err, AFE_REPAIR_OVERFLOW);
     }
     const size_t cs0 = (size_t)g.nx * g.ny, o0 = (size_t)j * g.nx + i;
-    if (a == 0.0) {
+    if (is_zero(a)) {
 #pragma unroll
       for (int k = 0; k < 8; ++k) d.uo[0][k * cs0 + o0] = fe[k];
     } else {

@@ -275,6 +275,34 @@ __device__ __forceinline__ double mul_i(double a, double b) {
   return from_bits(r);
 }
 
+// IEEE compares on the integer pipe (the same result as the FP64 compare for every
+// input, NaN and +-0 included).
+// x >= c and x > c for a constant c > 0: x in [c, +inf] (resp. (c, +inf]) by pattern
+__device__ __forceinline__ bool ge_pos(double x, double c) {
+  const unsigned long long bc = bits(c);
+  return bits(x) - bc <= 0x7ff0000000000000ULL - bc;
+}
+__device__ __forceinline__ bool gt_pos(double x, double c) {
+  const unsigned long long bc = bits(c);
+  return bits(x) - bc - 1ULL < 0x7ff0000000000000ULL - bc;
+}
+// x >= 0: +-0, the positive finite values and +inf
+__device__ __forceinline__ bool ge_zero(double x) {
+  const unsigned long long b = bits(x);
+  return b <= 0x7ff0000000000000ULL || b == 0x8000000000000000ULL;
+}
+// x >= y: the patterns mapped to an order-preserving unsigned key (negative values
+// complemented, positive ones with the sign bit set); +-0 compare equal, NaN false
+__device__ __forceinline__ bool ge_i(double x, double y) {
+  const unsigned long long bx = bits(x), by = bits(y);
+  const unsigned long long ax = bx & 0x7fffffffffffffffULL, ay = by & 0x7fffffffffffffffULL;
+  if (ax > 0x7ff0000000000000ULL || ay > 0x7ff0000000000000ULL) return false;
+  if ((ax | ay) == 0) return true;
+  const unsigned long long kx = (bx >> 63) ? ~bx : (bx | 0x8000000000000000ULL);
+  const unsigned long long ky = (by >> 63) ? ~by : (by | 0x8000000000000000ULL);
+  return kx >= ky;
+}
+
 // -x on the integer pipe
 __device__ __forceinline__ double neg_i(double x) { return from_bits(bits(x) ^ 0x8000000000000000ULL); }
 
