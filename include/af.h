@@ -337,9 +337,11 @@ void af_destroy(af_ctx *ctx);
 /* Diagnostic: n results of the FP64 helpers the kernels use, on device
  * arrays, in stream order: op 0 out = 1/x, op 1 out = x/y, op 2 out = sqrt(x),
  * op 3 out = x + y and op 4 out = x * y on the integer pipes (bitwise the IEEE
- * round-to-nearest sum and product).  y is read by ops 1, 3 and 4 only.  Used
- * by the tests to bound the helpers' error against the CUDA operators.
- * AF_EINVAL for an op outside 0..4 or a null x or out (or y where it is read). */
+ * round-to-nearest sum and product), and the integer-pipe compares as 1.0 / 0.0:
+ * op 5 x >= y, op 6 x >= y and op 7 x > y for a constant y > 0, op 8 x >= 0.
+ * y is read by ops 1 and 3..7.  Used by the tests to bound the helpers' error
+ * against the CUDA operators.  AF_EINVAL for an op outside 0..8 or a null x or
+ * out (or y where it is read). */
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
 
 /* ---- Batched ensembles (not in the paper: many independent runs at once) ----

@@ -469,13 +469,13 @@ __device__ __forceinline__ void gather_source(const AfGrid &g, const Vec4 &v, co
 __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGrid &g, const Acc &acc, double *out) {
   const double rho = U[0], r = rcp(rho);
   const double m1 = U[1], m2 = U[2], m3 = U[3];
-  const double v1 = m1 * r, v2 = m2 * r, v3 = m3 * r;
+  const double v1 = mul_i(m1, r), v2 = mul_i(m2, r), v3 = mul_i(m3, r);
   const double B1 = U[4], B2 = U[5], B3 = U[6], E = U[7];
-  const double BB = B1 * B1 + B2 * B2 + B3 * B3;
-  const double mv = m1 * v1 + m2 * v2 + m3 * v3;
-  const double p = g.gm1 * (E - 0.5 * (mv + BB));
-  const double pt = p + 0.5 * BB;
-  const double vB = v1 * B1 + v2 * B2 + v3 * B3;
+  const double BB = fma(B3, B3, fma(B2, B2, mul_i(B1, B1)));
+  const double mv = fma(m3, v3, fma(m2, v2, mul_i(m1, v1)));
+  const double p = mul_i(g.gm1, fma(-0.5, mv + BB, E));
+  const double pt = fma(0.5, BB, p);
+  const double vB = fma(v3, B3, fma(v2, B2, mul_i(v1, B1)));
   const double Ept = E + pt;
   double mb1 = 0, mb2 = 0, mb3 = 0, Bb1 = acc.B[0], Bb2 = acc.B[1], Bb3 = 0, Eb = 0;
   double vb1 = 0, vb2 = 0, vb3 = 0, ptb = 0, vBb = 0, Eptb = 0, pb = 0;
@@ -500,9 +500,9 @@ __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGri
   Bb1 += acc.ps[1]; Bb2 += acc.ps[2]; Bb3 += acc.ps[3];
   vb1 += acc.ps[4]; vb2 += acc.ps[5]; vb3 += acc.ps[6]; vBb += acc.ps[7];
   // spectral radii varrho_l = |v_l| + c_{f,l}
-  const double c2 = g.gamma * p * r;
-  const double a = BB * r + c2;
-  const double k4 = 4.0 * c2 * r;
+  const double c2 = mul_i(mul_i(g.gamma, p), r);
+  const double a = fma(BB, r, c2);
+  const double k4 = ldexp_i<2>(mul_i(c2, r));
   double ab = 0, c2b = 0, k4b = 0;
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
@@ -510,42 +510,45 @@ __device__ __forceinline__ void pointwise_transpose(const double *U, const AfGri
     const double vl = l == 0 ? v1 : v2, Bl = l == 0 ? B1 : B2;
     if (l == 0) vb1 += vl >= 0.0 ? avb : -avb; else vb2 += vl >= 0.0 ? avb : -avb;
     if (srb == 0.0) continue;
-    double dd = a * a - k4 * Bl * Bl;
-    if (dd < 0.0) dd = 0.0;
+    const double k4B = mul_i(k4, Bl);
+    double dd = fma(-k4B, Bl, mul_i(a, a));
+    if (!gt_zero(dd)) dd = 0.0;
     const double sd = dsqrt(dd);
-    const double s = 0.5 * sd + 0.5 * a;
+    const double s = fma(0.5, sd, ldexp_i<-1>(a));
     const double cf = dsqrt(s);
-    const double sb = cf > 0.0 ? 0.5 * srb * rcp(cf) : 0.0;
-    ab += 0.5 * sb;
-    const double ddb = sd > 0.0 ? 0.25 * sb * rcp(sd) : 0.0;
-    ab += 2.0 * a * ddb;
-    k4b -= Bl * Bl * ddb;
-    if (l == 0) Bb1 -= 2.0 * k4 * Bl * ddb; else Bb2 -= 2.0 * k4 * Bl * ddb;
+    const double sb = gt_zero(cf) ? mul_i(ldexp_i<-1>(srb), rcp(cf)) : 0.0;
+    ab = fma(0.5, sb, ab);
+    const double ddb = gt_zero(sd) ? mul_i(ldexp_i<-2>(sb), rcp(sd)) : 0.0;
+    ab = fma(ldexp_i<1>(a), ddb, ab);
+    k4b = fma(-mul_i(Bl, Bl), ddb, k4b);
+    if (l == 0) Bb1 = fma(-ldexp_i<1>(k4B), ddb, Bb1); else Bb2 = fma(-ldexp_i<1>(k4B), ddb, Bb2);
   }
   double rbar = 0.0;
-  c2b += 4.0 * r * k4b;
-  rbar += 4.0 * c2 * k4b;
-  Bb1 += 2.0 * B1 * r * ab; Bb2 += 2.0 * B2 * r * ab; Bb3 += 2.0 * B3 * r * ab;
-  rbar += BB * ab;
+  c2b = fma(ldexp_i<2>(r), k4b, c2b);
+  rbar = fma(ldexp_i<2>(c2), k4b, rbar);
+  const double rab2 = ldexp_i<1>(mul_i(r, ab));
+  Bb1 = fma(B1, rab2, Bb1); Bb2 = fma(B2, rab2, Bb2); Bb3 = fma(B3, rab2, Bb3);
+  rbar = fma(BB, ab, rbar);
   c2b += ab;
-  pb += g.gamma * r * c2b;
-  rbar += g.gamma * p * c2b;
+  pb = fma(mul_i(g.gamma, r), c2b, pb);
+  rbar = fma(mul_i(g.gamma, p), c2b, rbar);
   // Ept = E + pt; vB = v.B; pt = p + BB/2; p = (gamma-1)(E - (mv + BB)/2)
   Eb += Eptb; ptb += Eptb;
   vb1 += vBb * B1; vb2 += vBb * B2; vb3 += vBb * B3;
   Bb1 += vBb * v1; Bb2 += vBb * v2; Bb3 += vBb * v3;
   pb += ptb;
   Bb1 += ptb * B1; Bb2 += ptb * B2; Bb3 += ptb * B3;
-  Eb += g.gm1 * pb;
-  const double mvb = -0.5 * g.gm1 * pb;
-  Bb1 -= g.gm1 * pb * B1; Bb2 -= g.gm1 * pb * B2; Bb3 -= g.gm1 * pb * B3;
+  const double gpb = mul_i(g.gm1, pb);
+  Eb += gpb;
+  const double mvb = ldexp_i<-1>(neg_i(gpb));
+  Bb1 = fma(-gpb, B1, Bb1); Bb2 = fma(-gpb, B2, Bb2); Bb3 = fma(-gpb, B3, Bb3);
   mb1 += mvb * v1; mb2 += mvb * v2; mb3 += mvb * v3;
   vb1 += mvb * m1; vb2 += mvb * m2; vb3 += mvb * m3;
   // v_k = m_k r, r = 1/rho
   mb1 += vb1 * r; mb2 += vb2 * r; mb3 += vb3 * r;
   rbar += vb1 * m1 + vb2 * m2 + vb3 * m3;
-  out[0] = -r * r * rbar + acc.U[0];
-  if (acc.srho != 0.0) out[0] += 0.5 * acc.srho * rcp(dsqrt(rho));   // d sqrt(rho) / d rho
+  out[0] = fma(-mul_i(r, r), rbar, acc.U[0]);
+  if (!is_zero(acc.srho)) out[0] = fma(ldexp_i<-1>(acc.srho), rcp(dsqrt(rho)), out[0]);   // d sqrt(rho) / d rho
   out[1] = mb1 + acc.U[1];
   out[2] = mb2 + acc.U[2];
   out[3] = mb3 + acc.U[3];
@@ -595,7 +598,13 @@ __device__ __forceinline__ void adj_point(const AfDev &d, const AfGrid &g, const
 }
 
 // blockIdx.z: 0 x-faces, 1 y-faces, 2 corners, 3 cell centres
-__global__ void __launch_bounds__(128) k_adj2(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
+// A2 compiled for 4 resident blocks of 128 threads (128 registers): 3 % faster than
+// the compiler's 166 registers on the 256x256 adjoint workload
+#ifndef AF_MINB_ADJ2
+#define AF_MINB_ADJ2 4
+#endif
+#define AF_LB_ADJ2 __launch_bounds__(128, AF_MINB_ADJ2)
+__global__ void AF_LB_ADJ2 k_adj2(const __grid_constant__ AfDev d, const __grid_constant__ AfGrid g,
                                               const __grid_constant__ Vec4 v, const double *a,
                                               const __grid_constant__ OVec4 tp, double *zc, const double *co) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;

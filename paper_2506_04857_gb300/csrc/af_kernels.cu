@@ -1834,7 +1834,11 @@ __global__ void k_math_check(int op, const double *x, const double *y, double *o
   else if (op == 1) out[t] = ddiv(x[t], y[t]);
   else if (op == 2) out[t] = dsqrt(x[t]);
   else if (op == 3) out[t] = add_i(x[t], y[t]);
-  else out[t] = mul_i(x[t], y[t]);
+  else if (op == 4) out[t] = mul_i(x[t], y[t]);
+  else if (op == 5) out[t] = ge_i(x[t], y[t]) ? 1.0 : 0.0;
+  else if (op == 6) out[t] = ge_pos(x[t], y[t]) ? 1.0 : 0.0;
+  else if (op == 7) out[t] = gt_pos(x[t], y[t]) ? 1.0 : 0.0;
+  else out[t] = ge_zero(x[t]) ? 1.0 : 0.0;
 }
 
 // FP64 FMA throughput probe: 8 independent register chains per thread.

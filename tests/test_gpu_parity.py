@@ -172,6 +172,37 @@ def test_integer_pipe_add_and_mul_are_ieee(op):
     assert bad.size == 0, [(a[k].hex(), b[k].hex(), got[k].hex(), ref[k].hex()) for k in bad[:5]]
 
 
+@pytest.mark.parametrize("op", [5, 6, 7, 8])
+def test_integer_pipe_compares_are_ieee(op):
+    """ge_i, ge_pos, gt_pos and ge_zero (compares on the bit patterns) agree with the
+    IEEE compares for every input, NaN, +-0 and infinities included."""
+    n = 1 << 21
+    a, b = _bit_patterns(n, 200 + op)
+    rng = np.random.default_rng(op)
+    if op in (6, 7):   # a positive constant, and x near it
+        c = np.array([1e-13, 1.0 + 1e-12, 0.99, 3.0, 2.0 ** -1000, 1e300])[rng.integers(0, 6, n)]
+        near = rng.integers(0, 3, n) == 0
+        a = np.where(near, np.nextafter(c, np.where(rng.integers(0, 2, n) == 0, np.inf, -np.inf)), a)
+        a = np.where(rng.integers(0, 7, n) == 0, c, a)
+        b = c
+    if op == 5:   # equal values, +-0 pairs and neighbours
+        pick = rng.integers(0, 6, n)
+        b = np.where(pick == 0, a, b)
+        b = np.where(pick == 1, -a, b)
+        b = np.where(pick == 2, np.nextafter(a, np.inf), b)
+        zeros = np.array([0.0, -0.0])
+        a = np.where(pick == 3, zeros[rng.integers(0, 2, n)], a)
+        b = np.where(pick == 3, zeros[rng.integers(0, 2, n)], b)
+    with np.errstate(all="ignore"):
+        ref = {5: a >= b, 6: a >= b, 7: a > b, 8: a >= 0.0}[op]
+    x, y = torch.from_numpy(np.ascontiguousarray(a)).cuda(), torch.from_numpy(np.ascontiguousarray(b)).cuda()
+    out = torch.empty_like(x)
+    af.af_math_check(op, x, None if op == 8 else y, out)
+    got = out.cpu().numpy() == 1.0
+    bad = np.flatnonzero(got != ref)
+    assert bad.size == 0, [(a[k].hex(), b[k].hex(), bool(got[k]), bool(ref[k])) for k in bad[:5]]
+
+
 @pytest.mark.parametrize("bc,nx,ny", [(ai.PERIODIC, 16, 12), (ai.OUTFLOW, 13, 9), (ai.PERIODIC, 37, 29)])
 def test_rhs_parity(bc, nx, ny):
     pb = ai.random_smooth(nx, ny, seed=21, amp=0.2, bc=bc)
