@@ -728,22 +728,27 @@ __device__ __forceinline__ void b_points(const AfDev &d, const AfGrid &g, const 
           fvs_line_g<1>(Py, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
           divB = fma(dBx, g.rdx, mul_i(dBy, 0.5 * g.rdy));
         }
-      } else if (cls == 3) {
-        const PP Px[5] = {pref(d, g, 3, im, j), pref(d, g, 2, ci0, j), me, pref(d, g, 2, ci1, j), pref(d, g, 3, ip, j)};
-        const PP Py[5] = {pref(d, g, 3, i, jm), pref(d, g, 1, i, cj0), me, pref(d, g, 1, i, cj1), pref(d, g, 3, i, jp)};
-        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
-        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-        divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, 0.5 * g.rdy));
-      } else if (cls == 1) {
-        const PP Px[5] = {pref(d, g, 1, im, j), pref(d, g, 4, ci0, j), me, pref(d, g, 4, ci1, j), pref(d, g, 1, ip, j)};
-        fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
-        central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
-        divB = fma(dBx, 0.5 * g.rdx, mul_i(dBy, g.rdy));
       } else {
-        central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
-        const PP Py[5] = {pref(d, g, 2, i, jm), pref(d, g, 4, i, cj0), me, pref(d, g, 4, i, cj1), pref(d, g, 2, i, jp)};
-        fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
-        divB = fma(dBx, g.rdx, mul_i(dBy, 0.5 * g.rdy));
+        // the x line, then the y line of the point (one instance of each form): an FVS
+        // line through points half a cell apart, or, for the other direction of a face
+        // point, the central difference between the corners at its ends
+        if (cls == 2) {
+          central_line<0>(pref(d, g, 3, i, j), pref(d, g, 3, ip, j), PS, g.nxa, cxc, acc, dBx);
+        } else {
+          const int cm = cls == 3 ? 2 : 4;   // between the points: y-faces (corner), centres (x-face)
+          const PP Px[5] = {pref(d, g, cls, im, j), pref(d, g, cm, ci0, j), me, pref(d, g, cm, ci1, j),
+                            pref(d, g, cls, ip, j)};
+          fvs_line<0>(Px, PS, g.nxa, cx, acc, dBx, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V1)) : 0));
+        }
+        if (cls == 1) {
+          central_line<1>(pref(d, g, 3, i, j), pref(d, g, 3, i, jp), PS, g.nxa, cyc, acc, dBy);
+        } else {
+          const int cm = cls == 3 ? 1 : 4;   // x-faces (corner), centres (y-face)
+          const PP Py[5] = {pref(d, g, cls, i, jm), pref(d, g, cm, i, cj0), me, pref(d, g, cm, i, cj1),
+                            pref(d, g, cls, i, jp)};
+          fvs_line<1>(Py, PS, g.nxa, cy, acc, dBy, (UP ? upwind_sign(g, pw(me, PS, g.nxa, QP_V2)) : 0));
+        }
+        divB = fma(dBx, cls == 2 ? g.rdx : 0.5 * g.rdx, mul_i(dBy, cls == 1 ? g.rdy : 0.5 * g.rdy));
       }
       if (g.src_point_on) {
         // -(div B) Psi(U), Psi = (0, B, v, v.B)
@@ -1707,15 +1712,15 @@ __device__ __forceinline__ void b_cells_newton(const AfDev &d, const AfGrid &g) 
 // resident blocks per SM is capped at 65536 / (128 x blocks) registers; without
 // it ptxas picks the count.  The kernels keep the FP64 pipe and the integer
 // pipes busy at once; the defaults are the fastest of a sweep on the 2048x2048
-// blast (point data and point pass at 5 blocks = 96 registers, cell pass at
-// 5 = 96; faces and final pass at the compiler's count).
+// blast (point data at 5 blocks = 96 registers, point pass at 8 = 64, cell pass
+// at 5 = 96; faces and final pass at the compiler's count).
 #define AF_LB(minb) __launch_bounds__(128, minb)
 #ifndef AF_MINB_PD
 #define AF_MINB_PD 5
 #endif
 #define AF_LB_PD AF_LB(AF_MINB_PD)
 #ifndef AF_MINB_PT
-#define AF_MINB_PT 5
+#define AF_MINB_PT 8
 #endif
 #define AF_LB_PT AF_LB(AF_MINB_PT)
 #ifdef AF_MINB_FC
