@@ -76,9 +76,55 @@ __device__ __forceinline__ double qform(const double *U, double c) {
   double t = fma(0.5, b2, c);
   return fma(-U[0], t, fma(U[0], U[7], ldexp_i<-1>(neg_i(m2))));
 }
+// A double as a float truncated toward zero (integer operations).  In range:
+// 2^-60 <= |x| < 2^61 (every product of two such floats is a normal float) or x = 0.
+// With small = true a value below 2^-60 is taken as 0 (and stays in range).
+template <bool SMALL>
+__device__ __forceinline__ float trunc_f32(double x, bool &ok) {
+  const unsigned long long b = bits(x);
+  const unsigned hi = (unsigned)(b >> 32), e = (hi >> 20) & 0x7ffu;
+  const bool zero = SMALL ? e < 963u : (b << 1) == 0;
+  ok = ok && (zero || e - 963u <= 120u);
+  const unsigned fb = ((((hi & 0x7fffffffu) - (896u << 20)) << 3) | ((unsigned)b >> 29)) | (hi & 0x80000000u);
+  return zero ? 0.0f : __uint_as_float(fb);
+}
+// True when q(U) = rho E - |m|^2/2 - rho (|B|^2/2 + c), c > 0, is certainly >= 0, from
+// q and the sum S of the magnitudes of its terms evaluated in FP32 on the truncated
+// inputs: each term then carries a relative error below 8 * 2^-23 and the combination
+// two more roundings, so |q32 - q| < 10 * 2^-23 S < 1.3e-6 S.  Components of m and B
+// below 2^-60 are taken as 0: they enter squared, |m|^2/2 then errs by < 2^-119 and
+// rho |B|^2/2 by < rho 2^-119 < 2^-77 rho c, both < 2^-19 S since S >= rho c and
+// S32 > 2^-100 is required (which also keeps negligible the absolute error of a
+// product of three inputs below the normal FP32 range).  So q32 > 2^-16 S32 implies
+// q > 0 (and the FP64 qform > 0, whose error is about 1e-15 S).  An overflow makes
+// S32 infinite.  False means undecided: the FP64 form decides.
+__device__ __forceinline__ bool qform_cert32(const double *U, double c) {
+  bool ok = true;
+  float f[8];
+  f[0] = trunc_f32<false>(U[0], ok);
+  f[7] = trunc_f32<false>(U[7], ok);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) f[k] = trunc_f32<true>(U[k], ok);
+  const float cf = trunc_f32<false>(c, ok);
+  const float m2 = fmaf(f[1], f[1], fmaf(f[2], f[2], f[3] * f[3]));
+  const float b2 = fmaf(f[4], f[4], fmaf(f[5], f[5], f[6] * f[6]));
+  const float t = fmaf(0.5f, b2, cf);
+  const float q = fmaf(-f[0], t, fmaf(f[0], f[7], -0.5f * m2));
+  const float S = fmaf(fabsf(f[0]), fabsf(f[7]), fmaf(0.5f, m2, fabsf(f[0]) * fabsf(t)));
+  return ok && cf > 0.0f && S > 0x1p-100f && q > 0x1p-16f * S;
+}
+// qform(U, c) >= 0 in FP64, in a function that is not inlined (values by value): an
+// inlined one is evaluated whether or not the FP32 certificate decided
+__device__ __noinline__ bool qform_ge0(double u0, double u1, double u2, double u3, double u4, double u5, double u6,
+                                       double u7, double c) {
+  const double U[8] = {u0, u1, u2, u3, u4, u5, u6, u7};
+  return ge_zero(qform(U, c));
+}
 // rho >= 1e-13 and p >= 1e-13 (so every limiter of Sec. 3 leaves the state alone)
 __device__ __forceinline__ bool clear_of_floor(const double *U, const AfGrid &g) {
-  return ge_pos(U[0], 1e-13) && ge_zero(qform(U, g.c13));
+  if (!ge_pos(U[0], 1e-13)) return false;
+  if (qform_cert32(U, g.c13)) return true;
+  return qform_ge0(U[0], U[1], U[2], U[3], U[4], U[5], U[6], U[7], g.c13);
 }
 __device__ __forceinline__ bool in_G(const double *U, double gm1) {
   for (int k = 0; k < 8; ++k)
@@ -1265,11 +1311,11 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           Lam[0] = Lam[1] = Lam[2] = Lam[3] = 1.0;
           nsrc += th_src < 1.0;
         }
-        bool fast = !d.frz && ge_pos(Ullf[0], 1e-13) && ge_zero(qform(Ullf, g.c13));
+        bool fast = !d.frz && clear_of_floor(Ullf, g);
         if (fast) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) L1[k] = fma(-dtts, dS[k], Ullf[k]);
-          fast = ge_pos(L1[0], 1e-13) && ge_zero(qform(L1, g.c13));
+          fast = clear_of_floor(L1, g);
         }
         if (fast) {
           double D[8];
