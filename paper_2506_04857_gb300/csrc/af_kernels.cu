@@ -1098,6 +1098,79 @@ __device__ __forceinline__ bool box_certified(const double *L1, const double *D,
   return ge_i(q0 - T, mul_i(1e-12, scale)) && ge_i(rho - 1e-13, mul_i(1e-12 + D[0], 1.0 + 1e-10));
 }
 
+// |x| as a float, rounded up to 2^-60 when 0 < |x| < 2^-60 (an upper bound; 0 stays 0)
+// and truncated toward zero above; ok false from 2^61 on
+__device__ __forceinline__ float abs_f32_bound(double x, bool &ok) {
+  const unsigned long long b = bits(x) & 0x7fffffffffffffffULL;
+  const unsigned hi = (unsigned)(b >> 32), e = hi >> 20;
+  ok = ok && e < 1084u;
+  const float f = __uint_as_float(((hi - (896u << 20)) << 3) | ((unsigned)b >> 29));
+  return b == 0 ? 0.0f : (e < 963u ? 0x1p-60f : f);
+}
+// FP32 certificate of the box: true when box_certified(L1, D) holds for the bounds
+// D_k = cxf (|G0k| + |G1k|) + cyf (|G2k| + |G3k|), formed here in FP32 and rounded up
+// (truncated inputs, three roundings: relative error < 2^-21, covered by the factor
+// 1 + 2^-19), so that T, which grows with every D_k, is bounded above.  Components
+// of m and B of L1 below 2^-60 are taken as 0 in |m|^2 and |B|^2 (an error below
+// 2^-119 there, below 2^-77 rho c <= 2^-77 S in q0 and T, c > 0) and as 2^-60 in the
+// terms linear in them (bD, mD: an upper bound).  Each computed term then errs by
+// less than eps = 8 * 2^-23 of S, the sum of the magnitudes of every term of q0,
+// T and scale, so q0_32 - T_32 > 2^-14 S_32 implies q0 - T > (2^-14 - 3 eps) S >
+// 1e-12 scale, and the FP64 certificate (error about 1e-15 S) holds too.  The
+// density condition rho - 1e-13 >= (1e-12 + D0)(1 + 1e-10) follows from rho_32 >=
+// 1.0001 (1e-12 + D0_32 + 1e-13).  S_32 > 2^-100 keeps the absolute errors of
+// products below the normal FP32 range negligible; an overflow makes S_32 infinite.
+__device__ __forceinline__ bool box_cert32(const double *L1, const double (*Gf)[8], double cxf, double cyf,
+                                           double c13) {
+  bool ok = true;
+  float L[8], La[8], D[8];   // L: for the squares (small m, B flushed); La: |L|, small ones as 2^-60
+  L[0] = trunc_f32<false>(L1[0], ok);
+  L[7] = trunc_f32<false>(L1[7], ok);
+#pragma unroll
+  for (int k = 1; k < 7; ++k) {
+    L[k] = trunc_f32<true>(L1[k], ok);
+    La[k] = abs_f32_bound(L1[k], ok);
+  }
+  const float cx = trunc_f32<false>(cxf, ok), cy = trunc_f32<false>(cyf, ok), c = trunc_f32<false>(c13, ok);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float gx = abs_f32_bound(Gf[0][k], ok) + abs_f32_bound(Gf[1][k], ok);
+    const float gy = abs_f32_bound(Gf[2][k], ok) + abs_f32_bound(Gf[3][k], ok);
+    D[k] = fmaf(cx, gx, cy * gy) * (1.0f + 0x1p-19f);
+  }
+  const float rho = L[0], E = L[7];
+  const float bb = fmaf(L[4], L[4], fmaf(L[5], L[5], L[6] * L[6]));
+  const float mm = fmaf(L[1], L[1], fmaf(L[2], L[2], L[3] * L[3]));
+  const float eb = fmaf(0.5f, bb, c);
+  const float q0 = fmaf(-rho, eb, fmaf(rho, E, -0.5f * mm));
+  const float bD = fmaf(La[4], D[4], fmaf(La[5], D[5], La[6] * D[6]));
+  const float mD = fmaf(La[1], D[1], fmaf(La[2], D[2], La[3] * D[3]));
+  const float DB2 = fmaf(D[4], D[4], fmaf(D[5], D[5], D[6] * D[6]));
+  const float DM2 = fmaf(D[1], D[1], fmaf(D[2], D[2], D[3] * D[3]));
+  const float ar = fabsf(rho);
+  const float T1 = fmaf(fabsf(E - eb), D[0], fmaf(ar, D[7], fmaf(ar, bD, mD)));
+  const float T2 = fmaf(D[0], D[7], fmaf(0.5f, DM2, fmaf(0.5f * ar, DB2, D[0] * bD)));
+  const float T3 = 0.5f * D[0] * DB2;
+  const float T = T1 + T2 + T3;
+  const float S = fmaf(ar, fabsf(E), fmaf(0.5f, mm, fmaf(ar, eb, fmaf(fabsf(E) + eb, D[0], T))));
+  return ok && c > 0.0f && S > 0x1p-100f && q0 - T > 0x1p-14f * S && rho >= 1.0001f * (1e-12f + D[0] + 1e-13f);
+}
+
+// The FP64 bounds D and certificate for a cell that box_cert32 left undecided (not
+// inlined: the rare case; Lim1 by value, the face values G reloaded)
+__device__ __noinline__ bool box_cert64(const AfDev &d, const AfGrid &g, int i, int j, int ip, int jp, double l0,
+                                        double l1, double l2, double l3, double l4, double l5, double l6, double l7,
+                                        double cxf, double cyf) {
+  const WV FX = wview(d.fx, g), FY = wview(d.fy, g);
+  const double L1[8] = {l0, l1, l2, l3, l4, l5, l6, l7};
+  double D[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    D[k] = fma(cxf, absd(FX(i, j, QF_G + k)) + absd(FX(ip, j, QF_G + k)),
+               mul_i(cyf, absd(FY(i, j, QF_G + k)) + absd(FY(i, jp, QF_G + k))));
+  return box_certified(L1, D, g);
+}
+
 // Sec. 3.2 step (1) for one cell: theta_ij and Lim1, with the floors eps_rho, eps_p.
 __device__ __forceinline__ void cell_source_limit(const double *Ullf, const double *dS, double dtts, const AfGrid &g,
                                                   double *L1, int &srclim, double &th_out, double &eps_rho,
@@ -1317,12 +1390,9 @@ __device__ __forceinline__ void b_cells(const AfDev &d, const AfGrid &g, const i
           for (int k = 0; k < 8; ++k) L1[k] = fma(-dtts, dS[k], Ullf[k]);
           fast = clear_of_floor(L1, g);
         }
-        if (fast) {
-          double D[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) D[k] = fma(cxf, absd(Gf[0][k]) + absd(Gf[1][k]), mul_i(cyf, absd(Gf[2][k]) + absd(Gf[3][k])));
-          fast = box_certified(L1, D, g);
-        }
+        if (fast)
+          fast = box_cert32(L1, Gf, cxf, cyf, g.c13) ||
+                 box_cert64(d, g, i, j, ip, jp, L1[0], L1[1], L1[2], L1[3], L1[4], L1[5], L1[6], L1[7], cxf, cyf);
         bool listed = false;
         if (d.frz) {
         } else if (fast) {
