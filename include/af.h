@@ -338,10 +338,18 @@ void af_destroy(af_ctx *ctx);
  * arrays, in stream order: op 0 out = 1/x, op 1 out = x/y, op 2 out = sqrt(x),
  * op 3 out = x + y and op 4 out = x * y on the integer pipes (bitwise the IEEE
  * round-to-nearest sum and product), and the integer-pipe compares as 1.0 / 0.0:
- * op 5 x >= y, op 6 x >= y and op 7 x > y for a constant y > 0, op 8 x >= 0.
- * y is read by ops 1 and 3..7.  Used by the tests to bound the helpers' error
- * against the CUDA operators.  AF_EINVAL for an op outside 0..8 or a null x or
- * out (or y where it is read). */
+ * op 5 x >= y, op 6 x >= y and op 7 x > y for a constant y > 0, op 8 x >= 0;
+ * and the FP32 certificates as 1.0 (certified) / 0.0 (undecided): op 9, x = n
+ * states of 8 conserved values, y[0] = c: q = rho E - |m|^2/2 - rho (|B|^2/2 + c)
+ * >= 0; op 10, x = n cases of 40 values (Lim1, then the face values G of the
+ * left, right, lower and upper faces, 8 each), y = (dt/dx, dt/dy, c): the Sec. 3.2
+ * box certificate.  n is the number of results: out holds n doubles, x holds n
+ * (8n for op 9, 40n for op 10), y holds n for ops 1 and 3..7, 1 for op 9 and 3
+ * for op 10 and is not read by ops 0, 2 and 8.  The sizes cannot be checked here:
+ * buffers shorter than that are read or written out of bounds.  Used by the tests
+ * to bound the helpers' error against the CUDA operators and to check the
+ * certificates.  AF_EINVAL for an op outside 0..10, n < 0 or a null x or out (or y
+ * where it is read). */
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream);
 
 /* ---- Batched ensembles (not in the paper: many independent runs at once) ----

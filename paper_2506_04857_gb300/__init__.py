@@ -614,9 +614,31 @@ def af_destroy(ctx) -> None:
         _lib().af_destroy(ctx)
 
 
+# values of x per result and of y (per result, or in all) that each af_math_check op reads
+_MATH_X_PER = {9: 8, 10: 40}
+_MATH_Y = {1: "n", 3: "n", 4: "n", 5: "n", 6: "n", 7: "n", 9: 1, 10: 3}
+
+
 def af_math_check(op: int, x, y, out, stream=None) -> None:
+    """n = out.numel() results of the FP64 helpers or certificates (see af.h); every
+    buffer is checked here, since the C entry point cannot see their extents."""
+    import torch
+    if op not in range(11):
+        raise ValueError("af_math_check: op %d outside 0..10" % op)
+    n = out.numel()
+    need = {"x": (x, n * _MATH_X_PER.get(op, 1)), "out": (out, n)}
+    ny = _MATH_Y.get(op)
+    if ny is not None:
+        if y is None:
+            raise ValueError("af_math_check: op %d reads y" % op)
+        need["y"] = (y, n if ny == "n" else ny)
+    for name, (t, size) in need.items():
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and t.device == out.device):
+            raise ValueError("af_math_check: %s must be a contiguous CUDA float64 tensor on out's device" % name)
+        if t.numel() < size:
+            raise ValueError("af_math_check: %s holds %d values, op %d reads %d" % (name, t.numel(), op, size))
     handle = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-    rc = _lib().af_math_check(op, x.data_ptr(), None if y is None else y.data_ptr(), out.data_ptr(), x.numel(), handle)
+    rc = _lib().af_math_check(op, x.data_ptr(), None if ny is None else y.data_ptr(), out.data_ptr(), n, handle)
     if rc != AF_OK:
         raise AFError(rc, "af_math_check failed")
 

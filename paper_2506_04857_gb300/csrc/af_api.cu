@@ -1123,7 +1123,7 @@ void af_destroy(af_ctx *c) {
 }
 
 int af_math_check(int op, const double *x, const double *y, double *out, long long n, void *stream) {
-  if (op < 0 || op > 8 || !x || !out || (op != 0 && op != 2 && op != 8 && !y) || n < 0) return AF_EINVAL;
+  if (op < 0 || op > 10 || !x || !out || (op != 0 && op != 2 && op != 8 && !y) || n < 0) return AF_EINVAL;
   af_launch_math_check(op, x, y, out, n, (cudaStream_t)stream);
   return cudaGetLastError() == cudaSuccess ? AF_OK : AF_ECUDA;
 }

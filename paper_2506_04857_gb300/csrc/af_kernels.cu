@@ -88,16 +88,16 @@ __device__ __forceinline__ float trunc_f32(double x, bool &ok) {
   const unsigned fb = ((((hi & 0x7fffffffu) - (896u << 20)) << 3) | ((unsigned)b >> 29)) | (hi & 0x80000000u);
   return zero ? 0.0f : __uint_as_float(fb);
 }
-// True when q(U) = rho E - |m|^2/2 - rho (|B|^2/2 + c), c > 0, is certainly >= 0, from
+// True when q(U) = rho E - |m|^2/2 - rho (|B|^2/2 + c), c >= 0, is certainly > 0, from
 // q and the sum S of the magnitudes of its terms evaluated in FP32 on the truncated
 // inputs: each term then carries a relative error below 8 * 2^-23 and the combination
 // two more roundings, so |q32 - q| < 10 * 2^-23 S < 1.3e-6 S.  Components of m and B
 // below 2^-60 are taken as 0: they enter squared, |m|^2/2 then errs by < 2^-119 and
-// rho |B|^2/2 by < rho 2^-119 < 2^-77 rho c, both < 2^-19 S since S >= rho c and
-// S32 > 2^-100 is required (which also keeps negligible the absolute error of a
-// product of three inputs below the normal FP32 range).  So q32 > 2^-16 S32 implies
-// q > 0 (and the FP64 qform > 0, whose error is about 1e-15 S).  An overflow makes
-// S32 infinite.  False means undecided: the FP64 form decides.
+// rho |B|^2/2 by < rho 2^-119; with S >= rho (|E| + c), |E| + c > 2^-96 and S > 2^-96
+// required, both stay below 2^-22 S (which also keeps negligible the absolute error
+// of a product of three inputs below the normal FP32 range).  So q32 > 2^-16 S32
+// implies q > 0 (and the FP64 qform > 0, whose error is about 1e-15 S).  An overflow
+// makes S32 infinite.  False means undecided: the FP64 form decides.
 __device__ __forceinline__ bool qform_cert32(const double *U, double c) {
   bool ok = true;
   float f[8];
@@ -111,7 +111,7 @@ __device__ __forceinline__ bool qform_cert32(const double *U, double c) {
   const float t = fmaf(0.5f, b2, cf);
   const float q = fmaf(-f[0], t, fmaf(f[0], f[7], -0.5f * m2));
   const float S = fmaf(fabsf(f[0]), fabsf(f[7]), fmaf(0.5f, m2, fabsf(f[0]) * fabsf(t)));
-  return ok && cf > 0.0f && S > 0x1p-100f && q > 0x1p-16f * S;
+  return ok && fabsf(f[7]) + cf > 0x1p-96f && S > 0x1p-96f && q > 0x1p-16f * S;
 }
 // qform(U, c) >= 0 in FP64, in a function that is not inlined (values by value): an
 // inlined one is evaluated whether or not the FP32 certificate decided
@@ -119,6 +119,13 @@ __device__ __noinline__ bool qform_ge0(double u0, double u1, double u2, double u
                                        double u7, double c) {
   const double U[8] = {u0, u1, u2, u3, u4, u5, u6, u7};
   return ge_zero(qform(U, c));
+}
+// qform(U, 0) > 0 and finite in FP64 (not inlined, as above)
+__device__ __noinline__ bool qform_gt0(double u0, double u1, double u2, double u3, double u4, double u5, double u6,
+                                       double u7) {
+  const double U[8] = {u0, u1, u2, u3, u4, u5, u6, u7};
+  const double q = qform(U, 0.0);
+  return (long long)bits(q) > 0 && finite_bits(q);
 }
 // rho >= 1e-13 and p >= 1e-13 (so every limiter of Sec. 3 leaves the state alone)
 __device__ __forceinline__ bool clear_of_floor(const double *U, const AfGrid &g) {
@@ -1522,10 +1529,10 @@ __device__ __forceinline__ void b_final(const AfDev &d, const AfGrid &g, const i
     limited_value(d, g, i, j, th, dt, fe);
     // rho > 0 and p > 0 and all finite, on the integer pipe: for finite doubles
     // x > 0 exactly when the bit pattern, read as a signed integer, is > 0
-    const double q = qform(fe, 0.0);
-    bool ok = (long long)bits(fe[0]) > 0 && (long long)bits(q) > 0 && finite_bits(q);
+    bool ok = (long long)bits(fe[0]) > 0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) ok = ok && finite_bits(fe[k]);
+    ok = ok && (qform_cert32(fe, 0.0) || qform_gt0(fe[0], fe[1], fe[2], fe[3], fe[4], fe[5], fe[6], fe[7]));
     if (!ok && !d.frz) {
       const int slot = atomicAdd(&d.st->nrepair, 1);
       if (slot < AF_MAX_REPAIR) d.st->repair[slot] = j * g.nx + i;
@@ -1959,7 +1966,14 @@ __global__ void k_math_check(int op, const double *x, const double *y, double *o
   else if (op == 5) out[t] = ge_i(x[t], y[t]) ? 1.0 : 0.0;
   else if (op == 6) out[t] = ge_pos(x[t], y[t]) ? 1.0 : 0.0;
   else if (op == 7) out[t] = gt_pos(x[t], y[t]) ? 1.0 : 0.0;
-  else out[t] = ge_zero(x[t]) ? 1.0 : 0.0;
+  else if (op == 8) out[t] = ge_zero(x[t]) ? 1.0 : 0.0;
+  else if (op == 9) out[t] = qform_cert32(x + 8 * t, y[0]) ? 1.0 : 0.0;   // x: n states of 8
+  else {                                                                  // x: n cases of 8 + 4 x 8
+    double Gf[4][8];
+    for (int q = 0; q < 4; ++q)
+      for (int k = 0; k < 8; ++k) Gf[q][k] = x[40 * t + 8 + 8 * q + k];
+    out[t] = box_cert32(x + 40 * t, Gf, y[0], y[1], y[2]) ? 1.0 : 0.0;
+  }
 }
 
 // FP64 FMA throughput probe: 8 independent register chains per thread.

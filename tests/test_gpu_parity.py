@@ -203,6 +203,102 @@ def test_integer_pipe_compares_are_ieee(op):
     assert bad.size == 0, [(a[k].hex(), b[k].hex(), bool(got[k]), bool(ref[k])) for k in bad[:5]]
 
 
+def test_math_check_refuses_short_buffers():
+    """The binding checks every buffer against the op's sizes before the launch."""
+    out = torch.empty(16, dtype=torch.float64, device="cuda")
+    cases = [(10, torch.zeros(16 * 40 - 1, dtype=torch.float64, device="cuda"), torch.zeros(3, dtype=torch.float64, device="cuda")),
+             (10, torch.zeros(16 * 40, dtype=torch.float64, device="cuda"), torch.zeros(2, dtype=torch.float64, device="cuda")),
+             (9, torch.zeros(16 * 8 - 1, dtype=torch.float64, device="cuda"), torch.zeros(1, dtype=torch.float64, device="cuda")),
+             (3, torch.zeros(16, dtype=torch.float64, device="cuda"), torch.zeros(15, dtype=torch.float64, device="cuda")),
+             (1, torch.zeros(16, dtype=torch.float64, device="cuda"), None),
+             (0, torch.zeros(16, dtype=torch.float32, device="cuda"), None),
+             (0, torch.zeros(16, dtype=torch.float64), None),
+             (11, torch.zeros(16, dtype=torch.float64, device="cuda"), None)]
+    for op, x, y in cases:
+        with pytest.raises(ValueError):
+            af.af_math_check(op, x, y, out)
+
+
+_C13 = 1e-13 / 0.4   # the pressure floor over gamma - 1 (gamma = 1.4)
+
+
+def _states(n, seed):
+    """Conserved states: ordinary admissible ones (family 0), states within 1e-3 of the
+    pressure floor (1), strongly magnetised ones (2), ones with tiny or zero momentum
+    and field components (3) and ones with negative pressure (4)."""
+    rng = np.random.default_rng(seed)
+    fam = rng.integers(0, 5, n)
+    rho = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), n))
+    v = rng.normal(0.0, 3.0, (3, n))
+    B = rng.normal(0.0, 30.0, (3, n))
+    p = np.exp(rng.uniform(np.log(1e-3), np.log(1e3), n))
+    p = np.where(fam == 1, 0.4 * _C13 * (1.0 + rng.uniform(-1e-3, 1e-3, n)), p)
+    B = np.where(fam == 2, B * 30.0, B)
+    tiny = (fam == 3) & (rng.integers(0, 2, (3, n)) == 0)
+    v = np.where(tiny, rng.normal(0.0, 1e-25, (3, n)) * rng.integers(0, 2, (3, n)), v)
+    B = np.where(tiny, rng.normal(0.0, 1e-25, (3, n)), B)
+    p = np.where(fam == 4, -p * 1e-3, p)
+    m = rho * v
+    E = p / 0.4 + 0.5 * rho * (v * v).sum(0) + 0.5 * (B * B).sum(0)
+    U = np.stack([rho, m[0], m[1], m[2], B[0], B[1], B[2], E], axis=1)
+    return U, fam
+
+
+def _q(U, c):
+    """q = rho E - |m|^2/2 - rho (|B|^2/2 + c) in extended precision."""
+    U = U.astype(np.longdouble)
+    return (U[..., 0] * U[..., 7] - 0.5 * (U[..., 1:4] ** 2).sum(-1)
+            - U[..., 0] * (0.5 * (U[..., 4:7] ** 2).sum(-1) + c))
+
+
+@pytest.mark.parametrize("c", [_C13, 0.0])
+def test_fp32_admissibility_certificate_is_sound(c):
+    """The FP32 certificate of q > 0 (which lets the kernels skip the FP64 test)
+    never certifies a state whose q is not positive, and decides ordinary states."""
+    U, fam = _states(1 << 18, 31)
+    out = torch.empty(U.shape[0], dtype=torch.float64, device="cuda")
+    af.af_math_check(9, torch.from_numpy(U.reshape(-1)).cuda(), torch.tensor([c], dtype=torch.float64).cuda(), out)
+    cert = out.cpu().numpy() == 1.0
+    q = _q(U, c)
+    assert np.all(q[cert] > 0), U[cert & (q <= 0)][:3]
+    # decided wherever q is not tiny against the magnitudes of its terms (the
+    # certificate's margin is 2^-16 of their sum; very low beta states fall to FP64)
+    S = U[:, 0] * np.abs(U[:, 7]) + 0.5 * (U[:, 1:4] ** 2).sum(1) + U[:, 0] * (0.5 * (U[:, 4:7] ** 2).sum(1) + c)
+    clear = (fam == 0) & (q.astype(np.float64) > 1e-4 * S)
+    assert clear.sum() > 1000 and cert[clear].mean() > 0.99
+    assert cert[fam == 3].mean() > 0.5   # tiny components do not block the certificate
+    assert not cert[fam == 4].any()
+
+
+@pytest.mark.parametrize("scale", [1e-9, 1e-4, 1e-2, 0.3])
+def test_fp32_box_certificate_is_sound(scale):
+    """The FP32 certificate of the Sec. 3.2 box: where it certifies, every point of the
+    box |V_k - Lim1_k| <= D_k (D_k = dt/dx (|G_Lk| + |G_Rk|) + dt/dy (|G_Dk| + |G_Uk|))
+    sampled, its 16 sign vertices included, has rho >= 1e-13 and q >= 0."""
+    n = 1 << 14
+    L, fam = _states(n, 40)
+    rng = np.random.default_rng(41)
+    G = L[:, None, :] * rng.normal(0.0, scale, (n, 4, 8))
+    G = np.where(rng.integers(0, 4, (n, 4, 8)) == 0, 0.0, G)
+    cx, cy = 0.07, 0.05
+    x = np.concatenate([L, G.reshape(n, 32)], axis=1)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    af.af_math_check(10, torch.from_numpy(np.ascontiguousarray(x).reshape(-1)).cuda(),
+                     torch.tensor([cx, cy, _C13], dtype=torch.float64).cuda(), out)
+    cert = out.cpu().numpy() == 1.0
+    D = cx * (np.abs(G[:, 0]) + np.abs(G[:, 1])) + cy * (np.abs(G[:, 2]) + np.abs(G[:, 3]))
+    idx = np.flatnonzero(cert)
+    signs = np.array([[1 if (s >> k) & 1 else -1 for k in range(8)] for s in range(256)], dtype=np.float64)
+    for t in idx[:2000]:
+        V = L[t] + np.concatenate([signs, rng.uniform(-1, 1, (256, 8))]) * D[t]
+        assert np.all(V[:, 0] >= 1e-13) and np.all(_q(V, _C13) >= 0), (L[t], D[t])
+    if scale <= 1e-4:
+        S = L[:, 0] * np.abs(L[:, 7]) + 0.5 * (L[:, 1:4] ** 2).sum(1) + L[:, 0] * (0.5 * (L[:, 4:7] ** 2).sum(1) + _C13)
+        clear = (fam == 0) & (_q(L, _C13).astype(np.float64) > 1e-3 * S)
+        assert clear.sum() > 100 and cert[clear].mean() > 0.99
+    assert not cert[fam == 4].any()
+
+
 @pytest.mark.parametrize("bc,nx,ny", [(ai.PERIODIC, 16, 12), (ai.OUTFLOW, 13, 9), (ai.PERIODIC, 37, 29)])
 def test_rhs_parity(bc, nx, ny):
     pb = ai.random_smooth(nx, ny, seed=21, amp=0.2, bc=bc)
