@@ -52,6 +52,8 @@ WORKLOADS = {
                 "outflow, kappa=1", lambda: ai.blast1d(1 << 22)),
     "divb2048": ("divergence measures (Example 4.4) of the 2048x2048 low-beta blast after 3 steps",
                  lambda: ai.blast(2048)),
+    "divb512": ("divergence measures (Example 4.4) of the 512x512 low-beta blast after 3 steps (profiling size)",
+                lambda: ai.blast(512)),
     "lattice2048": ("rarefaction lattice 2048x2048 periodic (v = 6 (sgn sin 128 pi x, sgn sin 128 pi y), rho = 1, "
                     "p = 0.4, B = (0, 0.5, 0), gamma = 1.4), kappa=1: every positivity limiter and the Newton "
                     "solve act in each stage", lambda: ai.rarefaction_lattice(2048, periods=64)),
@@ -76,6 +78,9 @@ ALGO_FLOPS = {
 }
 # Flops per cell of the two divergence measures (af_divb), same counter.
 ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
+# Executed FP64 arithmetic per cell of one af_divb call (k_divb; the one-block sum is
+# negligible), from the capture named in "source"; filled in below EXEC_FP64.
+EXEC_FP64_DIVB = {}
 # Executed FP64 arithmetic per cell-stage of each stage kernel: DADD, DMUL and DFMA
 # thread instructions (ncu sm__sass_thread_inst_executed_op_{dadd,dmul,dfma}_pred_on.sum)
 # of one captured step, divided by the cell-stages of that step.  Flops = DADD + DMUL +
@@ -93,50 +98,52 @@ ALGO_FLOPS_DIVB = {"blast_low_beta": 414.0}
 # k_points_slow and k_cells_slow (the box and the Newton pass), the names af_timing
 # reports them under.
 EXEC_FP64 = {
-    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
-        "k_pointdata": {"dadd": 93.04, "dmul": 18.02, "dfma": 242.19, "pipe": 357.23, "dram_bytes": 1115.4, "int_mul": 124.09, "int_add": 0.00},
-        "k_points": {"dadd": 155.22, "dmul": 11.02, "dfma": 249.44, "pipe": 425.68, "dram_bytes": 1498.4, "int_mul": 40.06, "int_add": 0.00},
-        "k_points_slow": {"dadd": 0.15, "dmul": 0.22, "dfma": 0.48, "pipe": 0.88, "dram_bytes": 1.9, "int_mul": 0.02, "int_add": 0.00},
-        "k_faces": {"dadd": 74.11, "dmul": 5.95, "dfma": 56.41, "pipe": 141.48, "dram_bytes": 744.1, "int_mul": 44.08, "int_add": 0.00},
-        "k_cells": {"dadd": 80.00, "dmul": 7.00, "dfma": 171.01, "pipe": 265.01, "dram_bytes": 1172.7, "int_mul": 51.00, "int_add": 0.00},
-        "k_cells_slow": {"dadd": 0.06, "dmul": 0.18, "dfma": 0.21, "pipe": 0.55, "dram_bytes": 0.8, "int_mul": 0.00, "int_add": 0.00},
-        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 329.2, "int_mul": 8.33, "int_add": 16.00},
+    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+        "k_pointdata": {"dadd": 93.04, "dmul": 0.01, "dfma": 183.15, "pipe": 276.19, "dram_bytes": 1119.0, "int_mul": 142.10, "int_add": 0.00},
+        "k_points": {"dadd": 155.22, "dmul": 8.01, "dfma": 222.38, "pipe": 385.60, "dram_bytes": 1946.1, "int_mul": 43.07, "int_add": 0.00},
+        "k_points_slow": {"dadd": 0.14, "dmul": 0.19, "dfma": 0.39, "pipe": 0.74, "dram_bytes": 1.9, "int_mul": 0.05, "int_add": 0.00},
+        "k_faces": {"dadd": 74.11, "dmul": 5.95, "dfma": 52.36, "pipe": 134.39, "dram_bytes": 744.0, "int_mul": 44.08, "int_add": 0.00},
+        "k_cells": {"dadd": 58.01, "dmul": 3.00, "dfma": 122.02, "pipe": 183.03, "dram_bytes": 1224.2, "int_mul": 55.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 0.06, "dmul": 0.18, "dfma": 0.20, "pipe": 0.54, "dram_bytes": 0.8, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 329.5, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
-        "k_pointdata": {"dadd": 93.00, "dmul": 18.00, "dfma": 242.00, "pipe": 357.00, "dram_bytes": 943.8, "int_mul": 124.00, "int_add": 0.00},
-        "k_points": {"dadd": 156.00, "dmul": 11.00, "dfma": 259.00, "pipe": 436.00, "dram_bytes": 1411.1, "int_mul": 42.00, "int_add": 0.00},
+    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+        "k_pointdata": {"dadd": 93.00, "dmul": 0.00, "dfma": 183.00, "pipe": 276.00, "dram_bytes": 948.2, "int_mul": 142.00, "int_add": 0.00},
+        "k_points": {"dadd": 156.00, "dmul": 8.00, "dfma": 228.00, "pipe": 392.00, "dram_bytes": 1803.4, "int_mul": 45.00, "int_add": 0.00},
         "k_points_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
-        "k_faces": {"dadd": 74.00, "dmul": 0.00, "dfma": 82.00, "pipe": 159.00, "dram_bytes": 637.1, "int_mul": 46.00, "int_add": 0.00},
-        "k_cells": {"dadd": 80.00, "dmul": 7.00, "dfma": 171.00, "pipe": 265.00, "dram_bytes": 1031.7, "int_mul": 51.00, "int_add": 0.00},
+        "k_faces": {"dadd": 74.00, "dmul": 0.00, "dfma": 74.00, "pipe": 148.00, "dram_bytes": 637.8, "int_mul": 46.00, "int_add": 0.00},
+        "k_cells": {"dadd": 58.00, "dmul": 3.00, "dfma": 122.00, "pipe": 183.00, "dram_bytes": 1073.7, "int_mul": 55.00, "int_add": 0.00},
         "k_cells_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.3, "int_mul": 0.00, "int_add": 0.00},
-        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 277.4, "int_mul": 8.33, "int_add": 16.00},
+        "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 277.4, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
-        "k_pointdata": {"dadd": 93.05, "dmul": 18.01, "dfma": 242.23, "pipe": 357.27, "dram_bytes": 1094.3, "int_mul": 124.13, "int_add": 0.00},
-        "k_points": {"dadd": 189.44, "dmul": 11.94, "dfma": 249.44, "pipe": 460.84, "dram_bytes": 1625.3, "int_mul": 39.14, "int_add": 0.00},
-        "k_points_slow": {"dadd": 0.02, "dmul": 0.03, "dfma": 0.06, "pipe": 0.11, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
-        "k_faces": {"dadd": 83.13, "dmul": 6.02, "dfma": 56.16, "pipe": 150.39, "dram_bytes": 724.0, "int_mul": 44.08, "int_add": 0.00},
-        "k_cells": {"dadd": 80.52, "dmul": 7.00, "dfma": 171.01, "pipe": 265.53, "dram_bytes": 1135.7, "int_mul": 51.00, "int_add": 0.00},
-        "k_cells_slow": {"dadd": 0.03, "dmul": 0.09, "dfma": 0.11, "pipe": 0.28, "dram_bytes": 0.1, "int_mul": 0.00, "int_add": 0.00},
-        "k_final": {"dadd": 0.00, "dmul": 2.00, "dfma": 28.33, "pipe": 31.33, "dram_bytes": 321.9, "int_mul": 8.33, "int_add": 16.00},
+    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+        "k_pointdata": {"dadd": 93.05, "dmul": 0.00, "dfma": 183.17, "pipe": 276.21, "dram_bytes": 1098.4, "int_mul": 142.14, "int_add": 0.00},
+        "k_points": {"dadd": 189.44, "dmul": 8.27, "dfma": 222.40, "pipe": 420.13, "dram_bytes": 2399.5, "int_mul": 42.81, "int_add": 0.00},
+        "k_points_slow": {"dadd": 0.02, "dmul": 0.02, "dfma": 0.05, "pipe": 0.10, "dram_bytes": 0.2, "int_mul": 0.01, "int_add": 0.00},
+        "k_faces": {"dadd": 83.13, "dmul": 6.02, "dfma": 52.13, "pipe": 143.30, "dram_bytes": 723.8, "int_mul": 44.08, "int_add": 0.00},
+        "k_cells": {"dadd": 58.52, "dmul": 3.00, "dfma": 122.01, "pipe": 183.54, "dram_bytes": 1212.2, "int_mul": 55.00, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 0.03, "dmul": 0.09, "dfma": 0.10, "pipe": 0.27, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 322.2, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "22b961f5388f35b67a61d2221f58a5f3a9603849", "kernels": {
-        "k_pointdata": {"dadd": 93.50, "dmul": 20.24, "dfma": 246.10, "pipe": 364.30, "dram_bytes": 940.1, "int_mul": 124.00, "int_add": 0.00},
-        "k_points": {"dadd": 156.00, "dmul": 11.00, "dfma": 256.81, "pipe": 433.34, "dram_bytes": 1474.0, "int_mul": 39.81, "int_add": 0.00},
-        "k_points_slow": {"dadd": 53.51, "dmul": 80.96, "dfma": 172.99, "pipe": 319.01, "dram_bytes": 507.1, "int_mul": 6.84, "int_add": 0.00},
-        "k_faces": {"dadd": 74.00, "dmul": 0.01, "dfma": 82.00, "pipe": 159.00, "dram_bytes": 637.2, "int_mul": 46.00, "int_add": 0.00},
-        "k_cells": {"dadd": 81.36, "dmul": 8.59, "dfma": 179.16, "pipe": 276.52, "dram_bytes": 1032.2, "int_mul": 51.00, "int_add": 0.00},
-        "k_cells_slow": {"dadd": 44.31, "dmul": 58.33, "dfma": 240.91, "pipe": 358.34, "dram_bytes": 321.5, "int_mul": 0.00, "int_add": 0.00},
-        "k_final": {"dadd": 0.00, "dmul": 4.86, "dfma": 31.19, "pipe": 37.05, "dram_bytes": 277.8, "int_mul": 8.33, "int_add": 13.14},
+    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+        "k_pointdata": {"dadd": 93.50, "dmul": 1.87, "dfma": 187.23, "pipe": 283.05, "dram_bytes": 942.7, "int_mul": 142.37, "int_add": 0.00},
+        "k_points": {"dadd": 156.00, "dmul": 8.00, "dfma": 228.80, "pipe": 392.77, "dram_bytes": 1865.1, "int_mul": 42.81, "int_add": 0.00},
+        "k_points_slow": {"dadd": 49.23, "dmul": 68.69, "dfma": 141.61, "pipe": 271.05, "dram_bytes": 529.2, "int_mul": 19.11, "int_add": 0.00},
+        "k_faces": {"dadd": 74.00, "dmul": 0.57, "dfma": 75.13, "pipe": 149.66, "dram_bytes": 637.8, "int_mul": 45.44, "int_add": 0.00},
+        "k_cells": {"dadd": 64.34, "dmul": 4.36, "dfma": 136.73, "pipe": 206.08, "dram_bytes": 1092.5, "int_mul": 55.23, "int_add": 0.00},
+        "k_cells_slow": {"dadd": 44.31, "dmul": 54.71, "dfma": 233.66, "pipe": 347.47, "dram_bytes": 321.6, "int_mul": 3.62, "int_add": 0.00},
+        "k_final": {"dadd": 0.00, "dmul": 2.86, "dfma": 24.20, "pipe": 27.05, "dram_bytes": 277.8, "int_mul": 10.33, "int_add": 13.14},
     }},
-    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "34657efad9e053a3c26205343469505cf2570de2", "kernels": {
-        "k1_pointdata": {"dadd": 31.00, "dmul": 14.00, "dfma": 145.00, "pipe": 192.00, "dram_bytes": 667.6, "int_mul": 76.00, "int_add": 0.00},
-        "k1_points": {"dadd": 41.00, "dmul": 9.33, "dfma": 68.33, "pipe": 122.67, "dram_bytes": 430.6, "int_mul": 9.00, "int_add": 0.00},
-        "k1_faces": {"dadd": 30.00, "dmul": 20.00, "dfma": 21.00, "pipe": 75.00, "dram_bytes": 359.0, "int_mul": 4.00, "int_add": 0.00},
-        "k1_cells": {"dadd": 23.00, "dmul": 21.00, "dfma": 40.00, "pipe": 89.00, "dram_bytes": 290.5, "int_mul": 10.00, "int_add": 0.00},
-        "k1_final": {"dadd": 0.00, "dmul": 14.33, "dfma": 28.33, "pipe": 45.67, "dram_bytes": 252.6, "int_mul": 3.00, "int_add": 0.00},
+    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "0b72b8c35d8ea36709257e4b6f41eb3f5b365ff4", "kernels": {
+        "k1_pointdata": {"dadd": 31.00, "dmul": 8.00, "dfma": 106.00, "pipe": 145.00, "dram_bytes": 667.9, "int_mul": 82.00, "int_add": 0.00},
+        "k1_points": {"dadd": 41.00, "dmul": 9.33, "dfma": 55.33, "pipe": 107.67, "dram_bytes": 430.6, "int_mul": 9.00, "int_add": 0.00},
+        "k1_faces": {"dadd": 30.00, "dmul": 20.00, "dfma": 19.00, "pipe": 72.00, "dram_bytes": 358.9, "int_mul": 4.00, "int_add": 0.00},
+        "k1_cells": {"dadd": 23.00, "dmul": 19.00, "dfma": 40.00, "pipe": 85.00, "dram_bytes": 290.4, "int_mul": 12.00, "int_add": 0.00},
+        "k1_final": {"dadd": 0.00, "dmul": 14.33, "dfma": 28.33, "pipe": 45.67, "dram_bytes": 252.5, "int_mul": 3.00, "int_add": 0.00},
     }},
 }
+EXEC_FP64_DIVB["blast_low_beta"] = {"source": "profiles/divb_blast512.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0",
+                                     "dadd": 67.99, "dmul": 19.01, "dfma": 57.03, "pipe": 143.98}
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 / SM / cycle), i.e. 4 flops per SM-cycle.
@@ -375,7 +382,7 @@ def cpu_unit(key, pb, w):
             st[0], _ = oracle.step1(sub, st[0])
         return (run, sub.n * 3, "FP64 AF-MHD 1D cell-stage updates/s", "cell-stage updates/s",
                 "the same blast on %d cells, one SSP-RK3 step per call" % sub.n)
-    if key == "divb2048":
+    if key.startswith("divb"):
         sub, d = cpu_sample_problem("blast", pb, w)
         V = ai.dofs(sub)
         return (lambda: oracle.divb(sub, V), sub.nx * sub.ny, "FP64 divergence-measure cell evaluations/s",
@@ -881,13 +888,23 @@ def divb_bench(args, desc):
     cells = pb.nx * pb.ny
     value = cells * calls * world / (ms * 1e-3)
     peak, peak_src = fp64_peak(torch, local, clk)
-    fl = ALGO_FLOPS_DIVB[pb.name]
-    achieved = fl * cells / (ms / calls * 1e-3) * 1e-12
     state_bytes = cells * 32 * 8   # the four classes, read once per call
-    roofline = {"bound": "alu", "kernel": "k_divb + k_divb_sum (one call)", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic_flops_per_cell": fl,
+    lit = ALGO_FLOPS_DIVB[pb.name]
+    ex = EXEC_FP64_DIVB.get(pb.name)
+    roofline = {"bound": "alu", "kernel": "k_divb + k_divb_sum (one call)", "peak": peak, "unit": "TFLOP/s",
+                "traffic": None, "peak_source": peak_src, "literal_flops_per_cell": lit,
+                "literal_note": "the formulas counted as written (oracle counting build); context only, "
+                                "not divided by the peak",
                 "hbm_bound_cells_per_s": measured_peaks().get("hbm_gbs", 6775.6) * 1e9 / (32 * 8)}
+    if ex is not None:   # executed FP64-pipe flops per cell, as for the stage kernels
+        fl = ex["dadd"] + ex["dmul"] + 2.0 * ex["dfma"]
+        achieved = fl * cells / (ms / calls * 1e-3) * 1e-12
+        stale = kernel_digest(KERNEL_FILES_2D) != ex["digest"]
+        roofline.update({"achieved": achieved, "frac": achieved / peak, "executed_flops_per_cell": fl,
+                         "int_pipe_flops_per_cell": ex.get("int_mul", 0.0), "executed_counts": ex["source"],
+                         "counts_stale": stale})
+    else:
+        roofline.update({"achieved": None, "frac": None})
     # end to end: host state in, the two measures out
     host = [torch.from_numpy(u).pin_memory() for u in s.get_state(device=False)]
     t0 = time.perf_counter()
@@ -940,7 +957,7 @@ def main():
         return adjoint_bench(args, desc)
     if key == "blast1d" and args.impl == "ours":
         return oned_bench(args, desc)
-    if key == "divb2048" and args.impl == "ours":
+    if key.startswith("divb") and args.impl == "ours":
         return divb_bench(args, desc)
     pb = make()
     if args.impl == "reference":
