@@ -6,13 +6,15 @@
 // FP64 instruction count down:
 //   * rcp/ddiv/dsqrt: an FP32 hardware seed (rcp.approx / rsqrt.approx on the
 //     double's leading bits, converted with integer bit operations) refined by
-//     Newton-Raphson iterations in FP64 (the classical Newton reciprocal and
-//     Heron square-root iterations, e.g. P. Markstein, IBM J. Res. Dev. 34(1),
-//     1990).  Each costs 4-5 FP64 instructions and is accurate to about one
-//     ulp; outside the FP32 exponent range they fall back to the exact
-//     operators.
-//   * maxnn/minnn/absd: min/max/abs of doubles on the integer pipe (valid for
-//     non-negative, non-NaN operands where stated).
+//     one Newton-Raphson step in FP32 on the double split into two floats and
+//     one in FP64 (the classical Newton reciprocal and Heron square-root
+//     iterations, e.g. P. Markstein, IBM J. Res. Dev. 34(1), 1990).  Each costs
+//     2 FP64 instructions and is within one ulp; outside 2^-63 <= |x| < 2^78
+//     they take two FP64 steps (4 instructions), outside the FP32 exponent
+//     range the exact operators.
+//   * maxnn/minnn/absd and the compares ge_pos/gt_pos/ge_zero/ge_i: on the
+//     integer pipe, through an opaque move of the bit pattern (valid for
+//     non-negative, non-NaN operands where stated; the compares for every input).
 //   * mul_i/add_i: correctly rounded binary64 product and sum computed with
 //     integer instructions only, for code that is bound by the FP64 pipe while
 //     the integer pipes idle (GB300 has 2 FP64 lanes per SM against 64 integer
