@@ -98,7 +98,7 @@ EXEC_FP64_DIVB = {}
 # k_points_slow and k_cells_slow (the box and the Newton pass), the names af_timing
 # reports them under.
 EXEC_FP64 = {
-    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+    "blast_low_beta": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "7013560c17a537ed1abec9766d30c1192bfdcd19", "kernels": {
         "k_pointdata": {"dadd": 93.04, "dmul": 0.01, "dfma": 183.15, "pipe": 276.19, "dram_bytes": 1119.0, "int_mul": 142.10, "int_add": 0.00},
         "k_points": {"dadd": 155.22, "dmul": 8.01, "dfma": 222.38, "pipe": 385.60, "dram_bytes": 1946.1, "int_mul": 43.07, "int_add": 0.00},
         "k_points_slow": {"dadd": 0.14, "dmul": 0.19, "dfma": 0.39, "pipe": 0.74, "dram_bytes": 1.9, "int_mul": 0.05, "int_add": 0.00},
@@ -107,7 +107,7 @@ EXEC_FP64 = {
         "k_cells_slow": {"dadd": 0.06, "dmul": 0.18, "dfma": 0.20, "pipe": 0.54, "dram_bytes": 0.8, "int_mul": 0.00, "int_add": 0.00},
         "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 329.5, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+    "orszag_tang": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "7013560c17a537ed1abec9766d30c1192bfdcd19", "kernels": {
         "k_pointdata": {"dadd": 93.00, "dmul": 0.00, "dfma": 183.00, "pipe": 276.00, "dram_bytes": 948.2, "int_mul": 142.00, "int_add": 0.00},
         "k_points": {"dadd": 156.00, "dmul": 8.00, "dfma": 228.00, "pipe": 392.00, "dram_bytes": 1803.4, "int_mul": 45.00, "int_add": 0.00},
         "k_points_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
@@ -116,7 +116,7 @@ EXEC_FP64 = {
         "k_cells_slow": {"dadd": 0.00, "dmul": 0.00, "dfma": 0.00, "pipe": 0.00, "dram_bytes": 0.3, "int_mul": 0.00, "int_add": 0.00},
         "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 277.4, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+    "jets": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "7013560c17a537ed1abec9766d30c1192bfdcd19", "kernels": {
         "k_pointdata": {"dadd": 93.05, "dmul": 0.00, "dfma": 183.17, "pipe": 276.21, "dram_bytes": 1098.4, "int_mul": 142.14, "int_add": 0.00},
         "k_points": {"dadd": 189.44, "dmul": 8.27, "dfma": 222.40, "pipe": 420.13, "dram_bytes": 2399.5, "int_mul": 42.81, "int_add": 0.00},
         "k_points_slow": {"dadd": 0.02, "dmul": 0.02, "dfma": 0.05, "pipe": 0.10, "dram_bytes": 0.2, "int_mul": 0.01, "int_add": 0.00},
@@ -125,7 +125,7 @@ EXEC_FP64 = {
         "k_cells_slow": {"dadd": 0.03, "dmul": 0.09, "dfma": 0.10, "pipe": 0.27, "dram_bytes": 0.2, "int_mul": 0.00, "int_add": 0.00},
         "k_final": {"dadd": 0.00, "dmul": 0.00, "dfma": 21.33, "pipe": 21.33, "dram_bytes": 322.2, "int_mul": 10.33, "int_add": 16.00},
     }},
-    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0", "kernels": {
+    "rarefaction_lattice": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "7013560c17a537ed1abec9766d30c1192bfdcd19", "kernels": {
         "k_pointdata": {"dadd": 93.50, "dmul": 1.87, "dfma": 187.23, "pipe": 283.05, "dram_bytes": 942.7, "int_mul": 142.37, "int_add": 0.00},
         "k_points": {"dadd": 156.00, "dmul": 8.00, "dfma": 228.80, "pipe": 392.77, "dram_bytes": 1865.1, "int_mul": 42.81, "int_add": 0.00},
         "k_points_slow": {"dadd": 49.23, "dmul": 68.69, "dfma": 141.61, "pipe": 271.05, "dram_bytes": 529.2, "int_mul": 19.11, "int_add": 0.00},
@@ -134,7 +134,7 @@ EXEC_FP64 = {
         "k_cells_slow": {"dadd": 44.31, "dmul": 54.71, "dfma": 233.66, "pipe": 347.47, "dram_bytes": 321.6, "int_mul": 3.62, "int_add": 0.00},
         "k_final": {"dadd": 0.00, "dmul": 2.86, "dfma": 24.20, "pipe": 27.05, "dram_bytes": 277.8, "int_mul": 10.33, "int_add": 13.14},
     }},
-    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "0b72b8c35d8ea36709257e4b6f41eb3f5b365ff4", "kernels": {
+    "blast1d": {"source": "profiles/fp64ops_stage_kernels.md", "digest": "4087f8d8a892e78b360362b148be29e2a165c8b4", "kernels": {
         "k1_pointdata": {"dadd": 31.00, "dmul": 8.00, "dfma": 106.00, "pipe": 145.00, "dram_bytes": 667.9, "int_mul": 82.00, "int_add": 0.00},
         "k1_points": {"dadd": 41.00, "dmul": 9.33, "dfma": 55.33, "pipe": 107.67, "dram_bytes": 430.6, "int_mul": 9.00, "int_add": 0.00},
         "k1_faces": {"dadd": 30.00, "dmul": 20.00, "dfma": 19.00, "pipe": 72.00, "dram_bytes": 358.9, "int_mul": 4.00, "int_add": 0.00},
@@ -142,7 +142,7 @@ EXEC_FP64 = {
         "k1_final": {"dadd": 0.00, "dmul": 14.33, "dfma": 28.33, "pipe": 45.67, "dram_bytes": 252.5, "int_mul": 3.00, "int_add": 0.00},
     }},
 }
-EXEC_FP64_DIVB["blast_low_beta"] = {"source": "profiles/divb_blast512.md", "digest": "f6bec1deb278221f2fcb3b2831df7b42a6f500b0",
+EXEC_FP64_DIVB["blast_low_beta"] = {"source": "profiles/divb_blast512.md", "digest": "7013560c17a537ed1abec9766d30c1192bfdcd19",
                                      "dadd": 67.99, "dmul": 19.01, "dfma": 57.03, "pipe": 143.98}
 # FP64 roofline from unit counts and clock: the GB300 SM retires 2 DFMA thread
 # instructions per cycle (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
