@@ -187,6 +187,19 @@ __device__ __forceinline__ void b1_faces(const AfDev &d, const AfGrid &g, int f)
 
 // P4 (1D): per cell, U^LLF = U^{Lim,1}, the anti-diffusive fluxes H_L, H_R and
 // Lambda_L, Lambda_R (or the unlimited update without PP)
+// The FP64 bounds D_k = |dt/dx G_L,k| + |dt/dx G_R,k| and box certificate of 1D cell i
+// for the states box_cert32 leaves undecided (not inlined; Lim1 by value, G reloaded)
+__device__ __noinline__ bool box_cert64_1d(const AfDev &d, const AfGrid &g, int i, int ip, double l0, double l1,
+                                           double l2, double l3, double l4, double l5, double l6, double l7,
+                                           double cxf) {
+  const WV FX = wview(d.fx, g);
+  const double L1[8] = {l0, l1, l2, l3, l4, l5, l6, l7};
+  double D[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) D[k] = absd(cxf * FX(i, 0, QF_G + k)) + absd(-cxf * FX(ip, 0, QF_G + k));
+  return box_certified(L1, D, g);
+}
+
 __device__ __forceinline__ void b1_cells(const AfDev &d, const AfGrid &g, int i, double a, double b) {
   const size_t PS = (size_t)g.nxa;
   int nlam = 0, ncfl = 0;
@@ -196,7 +209,7 @@ __device__ __forceinline__ void b1_cells(const AfDev &d, const AfGrid &g, int i,
     const int ip = mface(i + 1, g.nx, g.bc);
     const WV FX = wview(d.fx, g);
     const SV Ub = sview(d.us[0], g, 0);
-    double Ullf[8], H[4][8];
+    double Ullf[8], H[4][8], Gf[4][8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const double fl = FX(i, 0, QF_FLLF + k), fr = FX(ip, 0, QF_FLLF + k);
@@ -206,6 +219,9 @@ __device__ __forceinline__ void b1_cells(const AfDev &d, const AfGrid &g, int i,
       H[1][k] = -cxf * gr;
       H[2][k] = 0.0;
       H[3][k] = 0.0;
+      Gf[0][k] = gl;
+      Gf[1][k] = gr;
+      Gf[2][k] = Gf[3][k] = 0.0;
     }
     const size_t cs0 = (size_t)g.nx;
     if (!g.pp_on) {
@@ -219,13 +235,12 @@ __device__ __forceinline__ void b1_cells(const AfDev &d, const AfGrid &g, int i,
       if (dt * ((FX(i, 0, QF_AL) + FX(ip, 0, QF_AL)) * g.rdx) > 1.0 + 1e-12) ncfl = 1;   // Lemma 3.1 (count only)
       double Lam[4];
       // fast path: where the box provably needs no limiting, Lambda = 1 exactly
-      bool fast = Ullf[0] >= 1e-13 && qform(Ullf, g.c13) >= 0.0;
-      if (fast) {
-        double D[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) D[k] = absd(H[0][k]) + absd(H[1][k]);
-        fast = box_certified(Ullf, D, g);
-      }
+      // (the FP32 certificates of the 2D cell pass, with the lower and upper face values 0;
+      // the FP64 forms only for the states they leave undecided)
+      bool fast = clear_of_floor(Ullf, g);
+      if (fast)
+        fast = box_cert32(Ullf, Gf, cxf, 0.0, g.c13) ||
+               box_cert64_1d(d, g, i, ip, Ullf[0], Ullf[1], Ullf[2], Ullf[3], Ullf[4], Ullf[5], Ullf[6], Ullf[7], cxf);
       if (fast) {
         Lam[0] = Lam[1] = 1.0;
       } else {
